@@ -1,0 +1,228 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) multigrid pressure Poisson solver.
+ *
+ * The solver computes the pressure p of the projection step of an
+ * incompressible VOF multiphase flow solver (paper §2: Eq. (1) div u = 0 and
+ * Eq. (2) with the pressure force -grad p / rho), i.e. the variable-coefficient
+ * Poisson problem
+ *
+ *        -div( (1/rho) grad p ) = b        on a uniform cell-centred grid,
+ *
+ * with homogeneous Neumann walls, density rho mixed from phase volume
+ * fractions by Eq. (5), and a geometric multigrid V-cycle as the solver (the
+ * multigrid pressure solver of §4.3.2).  Discretisation, fixed here because the
+ * paper states it nowhere:
+ *
+ *   cells    (i,j,k), spacing h, linear index (k*ny + j)*nx + i (x fastest);
+ *            a cell array has nx*ny*nz elements, shape (nz, ny, nx).
+ *   faces    bx: shape (nz, ny, nx+1), entry i is the face between cells i-1
+ *            and i; by: (nz, ny+1, nx); bz: (nz+1, ny, nx).  The first and last
+ *            face along each axis are walls: their values are ignored on input
+ *            (zero flux) and written as 0 on output.
+ *   beta     face coefficient = 1 / harmonic mean of the two cell densities
+ *            (= (1/rho_L + 1/rho_R) / 2).
+ *   operator (A p)_c = (1/h^2) sum_{interior faces f of c} beta_f (p_c - p_nb(f)).
+ *            A is symmetric positive semidefinite; its null space is the constants.
+ *   solution the zero-mean p with A p = b - mean(b).
+ *   V-cycle  red-black Gauss-Seidel (red = (i+j+k) even; pre sweeps red then
+ *            black, post sweeps black then red), residual, 8:1 restriction
+ *            (mean of the 8 children), prolongation (cell-centred trilinear, or
+ *            constant), face coarsening (a coarse face = mean of the 4 fine
+ *            faces tiling it, operator spacing doubled), and an exact dense
+ *            solve e = A_c^+ (r - mean r) on the coarsest level.  Levels halve
+ *            every dimension while all are even and the largest exceeds
+ *            opts.coarsest.
+ *   FP64     plain FP64 V-cycles on p until |b~ - A p| / |b~| <= rtol.
+ *   MIXED    FP64 defect correction: r = b~ - A p in FP64, one FP32 V-cycle
+ *            on r, p += correction in FP64, zero mean; same stopping rule.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers (CUDA global memory of the device the
+ *     handle was created on), owned by the caller, contiguous, in the layouts
+ *     above; the library keeps no reference to them after the call returns.
+ *     Unless a parameter says otherwise they are double (FP64).
+ *   - Work is queued on the CUDA stream given to mg_create.  Entry points that
+ *     need a scalar result on the host (mg_solve, mg_adjoint, the norm outputs)
+ *     synchronise that stream; the others return once the work is queued.
+ *   - All device memory the handle needs is allocated in mg_create; no other
+ *     entry point allocates device memory.
+ *   - Return value: MG_OK (0) or a negative MG_ERR_* code; no exception or
+ *     signal crosses the ABI.  mg_last_error() gives a message for the last
+ *     failure on that handle.  After MG_ERR_CUDA the handle should be destroyed.
+ *   - A handle is not thread safe: calls on one handle must not overlap.
+ */
+#ifndef MG_POISSON_H
+#define MG_POISSON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MG_OK = 0,
+    MG_ERR_ARG = -1,           /* bad argument: null pointer, size, option */
+    MG_ERR_DENSITY = -2,       /* a density or face coefficient is not finite and > 0 */
+    MG_ERR_NOT_CONVERGED = -3, /* max_cycles reached before rtol */
+    MG_ERR_DIVERGED = -4,      /* residual became non-finite or grew without bound */
+    MG_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+    MG_ERR_OOM = -6,           /* device memory allocation failed (mg_create only) */
+    MG_ERR_STATE = -7          /* call order: e.g. solve before coefficients were set */
+};
+
+enum { MG_FP64 = 0, MG_MIXED = 1 };
+enum { MG_PROLONG_TRILINEAR = 0, MG_PROLONG_CONSTANT = 1 };
+enum { MG_F64 = 0, MG_F32 = 1 }; /* element type of component-level arrays */
+
+#define MG_MAX_LEVELS 24
+#define MG_MAX_COARSE 1024 /* largest coarsest-level cell count (dense solve) */
+#define MG_HIST_LEN 256
+
+typedef struct mg_handle mg_handle;
+
+typedef struct {
+    int nx, ny, nz;   /* cells per dimension, each >= 1, nx*ny*nz >= 2 */
+    double h;         /* grid spacing, > 0 */
+    int precision;    /* MG_FP64 or MG_MIXED */
+    int pre, post;    /* RBGS sweeps before / after the coarse correction (>= 0) */
+    int coarsest;     /* stop coarsening once the largest dimension is <= this (>= 2) */
+    int prolong;      /* MG_PROLONG_TRILINEAR or MG_PROLONG_CONSTANT */
+    double rtol;      /* relative residual tolerance, |b~ - A p|_2 / |b~|_2 */
+    int max_cycles;   /* V-cycles (FP64) or outer iterations (MIXED), >= 0 */
+    int warm_start;   /* 1: mg_solve starts from the p passed in; 0: from p = 0 */
+} mg_opts;
+
+typedef struct {
+    int status;                     /* same as the return value */
+    int cycles;                     /* V-cycles run (one per outer iteration in MIXED) */
+    double relres;                  /* final relative residual */
+    double relres_hist[MG_HIST_LEN];/* relres after c cycles, c = 0..min(cycles, HIST-1) */
+    double ms;                      /* device time of the call (CUDA events) */
+} mg_stats;
+
+/* Defaults: 2/2 sweeps, coarsest 4, trilinear, rtol 1e-10, 200 cycles, FP64, cold start. */
+void mg_default_opts(mg_opts *opts);
+
+/* Create a solver for one grid.  `stream` is a cudaStream_t (NULL = legacy
+ * default stream) on the current device.  Allocates every device buffer the
+ * handle will use (hierarchy, scratch, coarse inverse): nothing is allocated
+ * later.  On failure *out is NULL and the code says why (MG_ERR_ARG: opts;
+ * MG_ERR_OOM; MG_ERR_CUDA). */
+int mg_create(const mg_opts *opts, void *stream, mg_handle **out);
+
+/* Free the handle and all its device memory (synchronises its stream). NULL is a no-op. */
+int mg_destroy(mg_handle *h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char *mg_last_error(const mg_handle *h);
+
+/* Number of multigrid levels, and the (nx, ny, nz) of level l (0 = finest). */
+int mg_num_levels(const mg_handle *h);
+int mg_level_dims(const mg_handle *h, int level, int *dims3);
+
+/* Eq. (5): rho = sum_{q<nfrac} rho_q f_q + rho_{nfrac} (1 - sum_{q<nfrac} f_q).
+ * frac_dev: host array of nfrac (1..4) device pointers to cell arrays;
+ * rho_phase: host array of nfrac+1 phase densities; rho_dev: output cell array. */
+int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac_dev,
+                              const double *rho_phase, double *rho_dev);
+
+/* Set the operator from a cell density field (device, cell array): face
+ * coefficients 1/harmonic-mean(rho), every coarse level, and the coarse
+ * inverse.  Checks that rho is finite and > 0 everywhere (MG_ERR_DENSITY
+ * otherwise; the previous operator is then no longer valid).  Synchronises. */
+int mg_set_density(mg_handle *h, const double *rho_dev);
+
+/* Set the operator from face coefficients beta (device, face layouts above;
+ * wall entries ignored).  Interior entries must be finite and > 0
+ * (MG_ERR_DENSITY).  Synchronises. */
+int mg_set_face_coeffs(mg_handle *h, const double *bx, const double *by, const double *bz);
+
+/* Copy the FP64 face coefficients of level l into caller arrays in the face
+ * layouts of that level's dimensions (walls written as 0). */
+int mg_get_level_faces(mg_handle *h, int level, double *bx, double *by, double *bz);
+
+/* CSF face quantity for a surface-tension RHS term: on interior faces
+ * csf_f = (kappa_L + kappa_R)/2 * (f_R - f_L) / h, walls 0.  f, kappa: cells. */
+int mg_csf_faces(mg_handle *h, const double *f, const double *kappa, double *csfx, double *csfy,
+                 double *csfz);
+
+/* RHS assembly b = b0 + D u + sigma * D(beta * csf), D the cell divergence
+ * (D u)_c = sum_faces (+u on the high face, -u on the low face) / h over
+ * interior faces.  Each term is optional: b0 (cell array) may be NULL; u* are
+ * face arrays or all NULL; csf* are face arrays or all NULL.  beta = the
+ * handle's current fine face coefficients (needed only when csf is given).
+ * b: output cell array; it may be the same array as b0. */
+int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, const double *uz,
+           const double *csfx, const double *csfy, const double *csfz, double sigma, double *b);
+
+/* Solve A p = b - mean(b) with mean(p) = 0 to opts.rtol.  b: cell array (not
+ * modified); p: cell array, output (and the initial guess if warm_start).
+ * stats may be NULL.  Returns MG_OK, MG_ERR_NOT_CONVERGED (p holds the last
+ * iterate, zero mean) or MG_ERR_DIVERGED.  Synchronises. */
+int mg_solve(mg_handle *h, const double *b, double *p, mg_stats *stats);
+
+/* Adjoint of mg_solve for a loss L with dL/dp = w.  Solves A lam = w - mean(w)
+ * (zero-mean lam = dL/db) with the same method and tolerance, then forms
+ *   dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R)/h^2 + sigma csf_f (lam_L - lam_R)/h
+ * on every interior face (FP32 outputs gbx/gby/gbz in the face layouts, walls
+ * 0) and dL/dsigma = sum_f beta_f csf_f (lam_L - lam_R)/h, where the forward
+ * RHS was b = D u + sigma D(beta csf).  p is the forward solution.  The csf
+ * arrays may be NULL (no surface term: the sigma terms vanish and *dLdsigma
+ * is set to 0).  gbx/gby/gbz and dLdsigma may be NULL to skip them.  The
+ * operator must be the one p was solved with.  Synchronises. */
+int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, float *gbx,
+               float *gby, float *gbz, const double *csfx, const double *csfy, const double *csfz,
+               double sigma, double *dLdsigma, mg_stats *stats);
+
+/* ---- component steps of the V-cycle on level `level` --------------------------
+ * For callers that assemble their own cycles, and for step-by-step checking.
+ * dtype MG_F64 uses the FP64 coefficients, MG_F32 the FP32 copies (MIXED
+ * handles only); arrays are then double or float cell arrays of that level.
+ * Physical scaling: level l has spacing h * 2^l. */
+
+/* y = A_l x */
+int mg_apply(mg_handle *h, int level, int dtype, const void *x, void *y);
+
+/* `sweeps` full red-black Gauss-Seidel sweeps on x in place for A_l x = b;
+ * order 0 = red then black (pre-smoothing), 1 = black then red (post). */
+int mg_smooth(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps, int order);
+
+/* r = b - A_l x, and (if norm2 != NULL) |r|_2 on the host (synchronises). */
+int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b, void *r,
+                double *norm2);
+
+/* bc (level+1) = mean of the 8 children of (b - A_l x). */
+int mg_residual_restrict(mg_handle *h, int level, int dtype, const void *x, const void *b,
+                         void *bc);
+
+/* x (level) += P ec (ec on level+1), with the handle's prolongation kind. */
+int mg_prolong_correct(mg_handle *h, int level, int dtype, const void *ec, void *x);
+
+/* e = A_c^+ (r - mean r) on the coarsest level (FP64 arithmetic for both dtypes). */
+int mg_coarse_solve(mg_handle *h, int dtype, const void *r, void *e);
+
+/* ---- instrumentation ------------------------------------------------------------
+ * With profiling on, the library records a CUDA event pair around every launch
+ * of a level-0 kernel class below (on the handle's stream) and accumulates the
+ * elapsed device time per class.  It measures the kernels inside real solves;
+ * it adds two event records per timed launch and nothing else. */
+enum {
+    MG_PROF_SMOOTH = 0,         /* finest-level red-black Gauss-Seidel sweeps */
+    MG_PROF_RESID_RESTRICT = 1, /* finest-level residual + restriction */
+    MG_PROF_PROLONG = 2,        /* prolongation + correction into the finest level */
+    MG_PROF_COARSE = 3,         /* dense coarse solve when the finest level is the coarsest */
+    MG_PROF_FINE_RESIDUAL = 4,  /* FP64 residual / norm pass of the outer loop */
+    MG_PROF_UPDATE = 5,         /* MIXED solution update */
+    MG_PROF_ADJOINT_GRAD = 6,   /* fused adjoint gradient kernel */
+    MG_PROF_NCLASS = 7
+};
+
+/* Turn timing on (1) or off (0); either way the accumulated totals are reset. */
+int mg_profile(mg_handle *h, int enable);
+
+/* Launches timed and their total device milliseconds for one class. */
+int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_POISSON_H */

@@ -1,0 +1,220 @@
+// Fine-level FP64 passes and deterministic reductions: RHS mean and norm,
+// the FP64 residual of the outer loop (with its norm, the mean of p and the
+// scaled FP32 copy that feeds the inner V-cycle), the solution update, and the
+// fused adjoint gradient kernel.
+//
+// Every reduction runs on a grid whose size depends only on n; each block
+// writes one partial (warp shuffles in a fixed pattern), and one block sums
+// the partials in index order, so results are bitwise reproducible.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+int reduce_blocks(i64 n) {
+    i64 b = (n + kReduceThreads - 1) / kReduceThreads;
+    const i64 cap = 152 * 8;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// reduce (a, b) over the block; thread 0 writes them to out[0], out[1]
+__device__ __forceinline__ void block_sum2(double a, double b, double *out) {
+    __shared__ double sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            out[0] = a;
+            out[1] = b;
+        }
+    }
+}
+
+__global__ void k_final(const double *__restrict__ partials, int nb, double *out) {
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        a += partials[2 * q];
+        b += partials[2 * q + 1];
+    }
+    block_sum2(a, b, out);
+}
+
+template <typename T>
+__global__ void k_sum_sumsq(i64 n, const T *__restrict__ x, double *partials) {
+    double a = 0.0, b = 0.0;
+    for (i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (i64)gridDim.x * blockDim.x) {
+        double v = (double)x[m];
+        a += v;
+        b += v * v;
+    }
+    block_sum2(a, b, partials + 2 * blockIdx.x);
+}
+
+__global__ void k_sub_mean(i64 n, const double *__restrict__ b, const double *__restrict__ sum,
+                           double *b64, double *partials) {
+    double mean = sum[0] / (double)n;
+    double q = 0.0;
+    for (i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (i64)gridDim.x * blockDim.x) {
+        double v = b[m] - mean;
+        b64[m] = v;
+        q += v * v;
+    }
+    block_sum2(q, 0.0, partials + 2 * blockIdx.x);
+}
+
+// r = b - ih2 * sum_f beta_f (p_c - p_nb); partials: (sum r^2, sum p)
+__global__ void k_fine_residual(Dims d, double ih2, const double *__restrict__ fx,
+                                const double *__restrict__ fy, const double *__restrict__ fz,
+                                const double *__restrict__ b, const double *__restrict__ p,
+                                float *r32, double scale, double *partials) {
+    double q = 0.0, sp = 0.0;
+    for (i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x; c < d.n; c += (i64)gridDim.x * blockDim.x) {
+        int i = (int)(c % d.nx);
+        i64 row = c / d.nx;
+        int j = (int)(row % d.ny), k = (int)(row / d.ny);
+        double pc = p[c];
+        double s = 0.0;
+        if (i > 0) s += fx[c] * (pc - p[c - 1]);
+        if (i < d.nx - 1) s += fx[c + 1] * (pc - p[c + 1]);
+        if (j > 0) s += fy[c] * (pc - p[c - d.nx]);
+        if (j < d.ny - 1) s += fy[c + d.nx] * (pc - p[c + d.nx]);
+        if (k > 0) s += fz[c] * (pc - p[c - d.nxy]);
+        if (k < d.nz - 1) s += fz[c + d.nxy] * (pc - p[c + d.nxy]);
+        double r = b[c] - s * ih2;
+        if (r32) r32[c] = (float)(r * scale);
+        q += r * r;
+        sp += pc;
+    }
+    block_sum2(q, sp, partials + 2 * blockIdx.x);
+}
+
+__global__ void k_update(i64 n, double *p, const float *__restrict__ e, double alpha, double shift) {
+    i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) p[m] = (p[m] - shift) + alpha * (double)e[m];
+}
+
+__global__ void k_add_const(i64 n, double *p, double c) {
+    i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) p[m] += c;
+}
+
+// dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R) ih2 + sigma csf_f (lam_L - lam_R) ih on the low
+// faces of each cell (walls 0); partial sums of beta_f csf_f (lam_L - lam_R) ih (= dL/dsigma)
+__global__ void k_adjoint_grad(Dims d, double ih, double ih2, const double *__restrict__ lam,
+                               const double *__restrict__ p, const double *__restrict__ fx,
+                               const double *__restrict__ fy, const double *__restrict__ fz,
+                               const double *__restrict__ csx, const double *__restrict__ csy,
+                               const double *__restrict__ csz, double sigma, float *gx, float *gy,
+                               float *gz, double *partials) {
+    double ds = 0.0;
+    for (i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x; c < d.n; c += (i64)gridDim.x * blockDim.x) {
+        int i = (int)(c % d.nx);
+        i64 row = c / d.nx;
+        int j = (int)(row % d.ny), k = (int)(row / d.ny);
+        i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
+        i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
+        double lc = lam[c], pc = p[c];
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        if (i > 0) {
+            double dl = lam[c - 1] - lc;
+            g0 = -dl * (p[c - 1] - pc) * ih2;
+            if (csx) {
+                g0 += sigma * csx[ax] * dl * ih;
+                ds += fx[c] * csx[ax] * dl * ih;
+            }
+        }
+        if (j > 0) {
+            double dl = lam[c - d.nx] - lc;
+            g1 = -dl * (p[c - d.nx] - pc) * ih2;
+            if (csy) {
+                g1 += sigma * csy[ay] * dl * ih;
+                ds += fy[c] * csy[ay] * dl * ih;
+            }
+        }
+        if (k > 0) {
+            double dl = lam[c - d.nxy] - lc;
+            g2 = -dl * (p[c - d.nxy] - pc) * ih2;
+            if (csz) {
+                g2 += sigma * csz[c] * dl * ih;
+                ds += fz[c] * csz[c] * dl * ih;
+            }
+        }
+        if (gx) {
+            gx[ax] = (float)g0;
+            gy[ay] = (float)g1;
+            gz[c] = (float)g2;
+            if (i == d.nx - 1) gx[ax + 1] = 0.f;
+            if (j == d.ny - 1) gy[ay + d.nx] = 0.f;
+            if (k == d.nz - 1) gz[c + d.nxy] = 0.f;
+        }
+    }
+    block_sum2(ds, 0.0, partials + 2 * blockIdx.x);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out) {
+    int nb = reduce_blocks(n);
+    k_sum_sumsq<T><<<nb, kReduceThreads, 0, s>>>(n, x, partials);
+    k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+template void launch_sum_sumsq<double>(cudaStream_t, i64, const double *, double *, double *);
+template void launch_sum_sumsq<float>(cudaStream_t, i64, const float *, double *, double *);
+
+void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
+                     double *partials, double *out) {
+    int nb = reduce_blocks(n);
+    k_sub_mean<<<nb, kReduceThreads, 0, s>>>(n, b, sum, b64, partials);
+    k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+
+void launch_fine_residual(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+                          const double *fz, const double *b, const double *p, float *r32,
+                          double scale, double *partials, double *out) {
+    int nb = reduce_blocks(d.n);
+    k_fine_residual<<<nb, kReduceThreads, 0, s>>>(d, ih2, fx, fy, fz, b, p, r32, scale, partials);
+    k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+
+void launch_update(cudaStream_t s, i64 n, double *p, const float *e32, double alpha, double shift) {
+    k_update<<<blocks_for(n), kThreads, 0, s>>>(n, p, e32, alpha, shift);
+}
+
+void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {
+    k_add_const<<<blocks_for(n), kThreads, 0, s>>>(n, p, c);
+}
+
+void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, const double *p,
+                         const double *fx, const double *fy, const double *fz, const double *csfx,
+                         const double *csfy, const double *csfz, double sigma, float *gx,
+                         float *gy, float *gz, double *partials, double *out) {
+    int nb = reduce_blocks(d.n);
+    k_adjoint_grad<<<nb, kReduceThreads, 0, s>>>(d, 1.0 / h, 1.0 / (h * h), lam, p, fx, fy, fz,
+                                                 csfx, csfy, csfz, sigma, gx, gy, gz, partials);
+    k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+
+}  // namespace mg

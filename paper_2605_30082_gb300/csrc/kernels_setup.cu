@@ -1,0 +1,332 @@
+// Set-up kernels: density mixing (Eq. (5)), face coefficients, coarsening,
+// inverse diagonals, precision copies, CSF faces, RHS assembly and the dense
+// coarse-level inverse.  All FP64, one thread per cell (these run once per
+// density field, not inside the V-cycle).
+#include "mg_internal.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+struct FracArgs {
+    const double *f[4];
+    double rho[5];
+    int nfrac;
+};
+
+__global__ void k_density(i64 n, FracArgs a, double *rho) {
+    i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double r = 0.0, rest = 1.0;
+    for (int q = 0; q < a.nfrac; ++q) {
+        double f = a.f[q][m];
+        r += a.rho[q] * f;
+        rest -= f;
+    }
+    rho[m] = r + a.rho[a.nfrac] * rest;
+}
+
+__device__ __forceinline__ bool good_positive(double v) { return v > 0.0 && v <= 1.79e308; }
+
+// beta between densities a and b: 1 / harmonic mean = (a + b) / (2 a b)
+__device__ __forceinline__ double inv_harmonic(double a, double b) { return (a + b) / (2.0 * a * b); }
+
+__global__ void k_faces_from_rho(Dims d, const double *__restrict__ rho, double *fx, double *fy,
+                                 double *fz, unsigned *err) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    double rc = rho[c];
+    if (!good_positive(rc)) atomicOr(err, 1u);
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    if (i > 0) vx = inv_harmonic(rho[c - 1], rc);
+    if (j > 0) vy = inv_harmonic(rho[c - d.nx], rc);
+    if (k > 0) vz = inv_harmonic(rho[c - d.nxy], rc);
+    fx[c] = vx;
+    fy[c] = vy;
+    fz[c] = vz;
+}
+
+__global__ void k_faces_from_api(Dims d, const double *__restrict__ bx, const double *__restrict__ by,
+                                 const double *__restrict__ bz, double *fx, double *fy, double *fz,
+                                 unsigned *err) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    if (i > 0) vx = bx[((i64)k * d.ny + j) * (d.nx + 1) + i];
+    if (j > 0) vy = by[((i64)k * (d.ny + 1) + j) * d.nx + i];
+    if (k > 0) vz = bz[c];  // (nz+1, ny, nx): plane k starts at k*nxy
+    if ((i > 0 && !good_positive(vx)) || (j > 0 && !good_positive(vy)) ||
+        (k > 0 && !good_positive(vz)))
+        atomicOr(err, 1u);
+    fx[c] = vx;
+    fy[c] = vy;
+    fz[c] = vz;
+}
+
+__global__ void k_faces_to_api(Dims d, const double *__restrict__ fx, const double *__restrict__ fy,
+                               const double *__restrict__ fz, double *bx, double *by, double *bz) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
+    i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
+    bx[ax] = i > 0 ? fx[c] : 0.0;
+    by[ay] = j > 0 ? fy[c] : 0.0;
+    bz[c] = k > 0 ? fz[c] : 0.0;
+    if (i == d.nx - 1) bx[ax + 1] = 0.0;
+    if (j == d.ny - 1) by[ay + d.nx] = 0.0;
+    if (k == d.nz - 1) bz[c + d.nxy] = 0.0;
+}
+
+__global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *__restrict__ fy,
+                          const double *__restrict__ fz, double *invd64, float *invd32) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    // order x-, x+, y-, y+, z-, z+ (low faces of i=0 etc. are stored as 0)
+    double s = fx[c];
+    if (i < d.nx - 1) s += fx[c + 1];
+    s += fy[c];
+    if (j < d.ny - 1) s += fy[c + d.nx];
+    s += fz[c];
+    if (k < d.nz - 1) s += fz[c + d.nxy];
+    double inv = 1.0 / s;
+    if (invd64) invd64[c] = inv;
+    if (invd32) invd32[c] = (float)inv;
+}
+
+// coarse low face = mean of the 4 fine low faces that tile it
+__global__ void k_coarsen(Dims f, Dims cd, const double *__restrict__ ffx,
+                          const double *__restrict__ ffy, const double *__restrict__ ffz,
+                          double *cfx, double *cfy, double *cfz) {
+    i64 C = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (C >= cd.n) return;
+    int I = (int)(C % cd.nx);
+    int J = (int)((C / cd.nx) % cd.ny);
+    int K = (int)(C / cd.nxy);
+    i64 base = ((i64)(2 * K) * f.ny + 2 * J) * f.nx + 2 * I;  // child (0,0,0)
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b) sx += ffx[base + c * f.nxy + b * f.nx];
+    for (int c = 0; c < 2; ++c)
+        for (int a = 0; a < 2; ++a) sy += ffy[base + c * f.nxy + a];
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) sz += ffz[base + b * f.nx + a];
+    cfx[C] = sx / 4.0;
+    cfy[C] = sy / 4.0;
+    cfz[C] = sz / 4.0;
+}
+
+__global__ void k_to_f32(i64 n, const double *__restrict__ src, float *dst) {
+    i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) dst[m] = (float)src[m];
+}
+
+__global__ void k_csf_faces(Dims d, double ih, const double *__restrict__ f,
+                            const double *__restrict__ kap, double *cx, double *cy, double *cz) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
+    i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
+    double fc = f[c], kc = kap[c];
+    cx[ax] = i > 0 ? 0.5 * (kap[c - 1] + kc) * (fc - f[c - 1]) * ih : 0.0;
+    cy[ay] = j > 0 ? 0.5 * (kap[c - d.nx] + kc) * (fc - f[c - d.nx]) * ih : 0.0;
+    cz[c] = k > 0 ? 0.5 * (kap[c - d.nxy] + kc) * (fc - f[c - d.nxy]) * ih : 0.0;
+    if (i == d.nx - 1) cx[ax + 1] = 0.0;
+    if (j == d.ny - 1) cy[ay + d.nx] = 0.0;
+    if (k == d.nz - 1) cz[c + d.nxy] = 0.0;
+}
+
+// b = b0 + D u + sigma D(beta csf); D over interior faces, (+high - low)/h; terms optional
+__global__ void k_rhs(Dims d, double ih, const double *b0, const double *__restrict__ ux,
+                      const double *__restrict__ uy, const double *__restrict__ uz,
+                      const double *__restrict__ fx, const double *__restrict__ fy,
+                      const double *__restrict__ fz, const double *__restrict__ csx,
+                      const double *__restrict__ csy, const double *__restrict__ csz, double sigma,
+                      double *b) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
+    i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
+    double v = b0 ? b0[c] : 0.0;
+    if (ux) {
+        double s = 0.0;
+        if (i > 0) s -= ux[ax];
+        if (i < d.nx - 1) s += ux[ax + 1];
+        if (j > 0) s -= uy[ay];
+        if (j < d.ny - 1) s += uy[ay + d.nx];
+        if (k > 0) s -= uz[c];
+        if (k < d.nz - 1) s += uz[c + d.nxy];
+        v += s * ih;
+    }
+    if (csx) {
+        double t = 0.0;
+        if (i > 0) t -= fx[c] * csx[ax];
+        if (i < d.nx - 1) t += fx[c + 1] * csx[ax + 1];
+        if (j > 0) t -= fy[c] * csy[ay];
+        if (j < d.ny - 1) t += fy[c + d.nx] * csy[ay + d.nx];
+        if (k > 0) t -= fz[c] * csz[c];
+        if (k < d.nz - 1) t += fz[c + d.nxy] * csz[c + d.nxy];
+        v += sigma * (t * ih);
+    }
+    b[c] = v;
+}
+
+// ---- dense coarse inverse -----------------------------------------------------------
+// M (row-major nc x nc) = A_c; one thread per row
+__global__ void k_coarse_assemble(Dims d, double ih2, const double *__restrict__ fx,
+                                  const double *__restrict__ fy, const double *__restrict__ fz,
+                                  double *M) {
+    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    int i = (int)(c % d.nx);
+    int j = (int)((c / d.nx) % d.ny);
+    int k = (int)(c / d.nxy);
+    double *row = M + c * d.n;
+    for (i64 q = 0; q < d.n; ++q) row[q] = 0.0;
+    double diag = 0.0, v;
+    if (i > 0) { v = fx[c] * ih2; row[c - 1] -= v; diag += v; }
+    if (i < d.nx - 1) { v = fx[c + 1] * ih2; row[c + 1] -= v; diag += v; }
+    if (j > 0) { v = fy[c] * ih2; row[c - d.nx] -= v; diag += v; }
+    if (j < d.ny - 1) { v = fy[c + d.nx] * ih2; row[c + d.nx] -= v; diag += v; }
+    if (k > 0) { v = fz[c] * ih2; row[c - d.nxy] -= v; diag += v; }
+    if (k < d.nz - 1) { v = fz[c + d.nxy] * ih2; row[c + d.nxy] -= v; diag += v; }
+    row[c] = diag;
+}
+
+// scal[0] = c = mean(diag)/nc; adds c to every entry; scal[1] = 1/M[0][0]
+__global__ void k_coarse_shift(int nc, double *M, double *scal) {
+    __shared__ double red[1024];
+    double t = 0.0;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) t += M[(i64)q * nc + q];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double cshift = red[0] / nc / nc;
+    __syncthreads();
+    for (i64 q = threadIdx.x; q < (i64)nc * nc; q += blockDim.x) M[q] += cshift;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        scal[0] = cshift;
+        scal[1] = 1.0 / M[0];
+    }
+}
+
+// One Gauss-Jordan sweep on pivot k, out of place.  scal[1] holds 1/pivot;
+// the thread owning the next pivot stores its reciprocal in scal[2] (swapped by the host).
+__global__ void k_gj_step(int nc, int k, const double *__restrict__ A, double *B,
+                          const double *__restrict__ rpiv_in, double *rpiv_out) {
+    i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (i64)nc * nc) return;
+    int i = (int)(e / nc), j = (int)(e % nc);
+    double rp = *rpiv_in;
+    double v;
+    if (i == k && j == k) v = rp;
+    else if (i == k) v = A[(i64)k * nc + j] * rp;
+    else if (j == k) v = -A[(i64)i * nc + k] * rp;
+    else v = A[e] - A[(i64)i * nc + k] * (A[(i64)k * nc + j] * rp);
+    B[e] = v;
+    if (i == k + 1 && j == k + 1 && rpiv_out) *rpiv_out = 1.0 / v;
+}
+
+__global__ void k_pinv_finish(int nc, double *M, const double *__restrict__ scal) {
+    i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (i64)nc * nc) return;
+    M[e] -= 1.0 / (scal[0] * (double)nc * (double)nc);
+}
+
+}  // namespace
+
+void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
+                    const double *rho_phase, double *rho) {
+    FracArgs a;
+    a.nfrac = nfrac;
+    for (int q = 0; q < 4; ++q) a.f[q] = q < nfrac ? frac[q] : nullptr;
+    for (int q = 0; q < 5; ++q) a.rho[q] = q <= nfrac ? rho_phase[q] : 0.0;
+    k_density<<<blocks_for(n), kThreads, 0, s>>>(n, a, rho);
+}
+
+void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *fx, double *fy,
+                           double *fz, unsigned *err) {
+    k_faces_from_rho<<<blocks_for(d.n), kThreads, 0, s>>>(d, rho, fx, fy, fz, err);
+}
+
+void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const double *by,
+                           const double *bz, double *fx, double *fy, double *fz, unsigned *err) {
+    k_faces_from_api<<<blocks_for(d.n), kThreads, 0, s>>>(d, bx, by, bz, fx, fy, fz, err);
+}
+
+void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double *fy,
+                         const double *fz, double *bx, double *by, double *bz) {
+    k_faces_to_api<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, bx, by, bz);
+}
+
+void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
+                    double *invd64, float *invd32) {
+    k_invdiag<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, invd64, invd32);
+}
+
+void launch_coarsen(cudaStream_t s, Dims fine, const double *ffx, const double *ffy,
+                    const double *ffz, double *cfx, double *cfy, double *cfz) {
+    Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
+    k_coarsen<<<blocks_for(cd.n), kThreads, 0, s>>>(fine, cd, ffx, ffy, ffz, cfx, cfy, cfz);
+}
+
+void launch_to_f32(cudaStream_t s, i64 n, const double *src, float *dst) {
+    k_to_f32<<<blocks_for(n), kThreads, 0, s>>>(n, src, dst);
+}
+
+void launch_csf_faces(cudaStream_t s, Dims d, double h, const double *f, const double *kappa,
+                      double *cx, double *cy, double *cz) {
+    k_csf_faces<<<blocks_for(d.n), kThreads, 0, s>>>(d, 1.0 / h, f, kappa, cx, cy, cz);
+}
+
+void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double *ux, const double *uy,
+                const double *uz, const double *fx, const double *fy, const double *fz,
+                const double *csfx, const double *csfy, const double *csfz, double sigma,
+                double *b) {
+    k_rhs<<<blocks_for(d.n), kThreads, 0, s>>>(d, 1.0 / h, b0, ux, uy, uz, fx, fy, fz, csfx, csfy,
+                                               csfz, sigma, b);
+}
+
+void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+                            const double *fz, double *M, double *scal) {
+    k_coarse_assemble<<<blocks_for(d.n), kThreads, 0, s>>>(d, ih2, fx, fy, fz, M);
+    k_coarse_shift<<<1, 1024, 0, s>>>((int)d.n, M, scal);
+}
+
+void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mout, double *scal) {
+    // reciprocal pivots alternate between scal[1] and scal[2]
+    const double *rin = scal + 1 + (k & 1);
+    double *rout = (k + 1 < nc) ? scal + 1 + ((k + 1) & 1) : nullptr;
+    k_gj_step<<<blocks_for((i64)nc * nc), kThreads, 0, s>>>(nc, k, Min, Mout, rin, rout);
+}
+
+void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal) {
+    k_pinv_finish<<<blocks_for((i64)nc * nc), kThreads, 0, s>>>(nc, M, scal);
+}
+
+}  // namespace mg

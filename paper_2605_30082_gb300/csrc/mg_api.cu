@@ -1,0 +1,677 @@
+// Host side of the C ABI declared in include/mg.h: the handle, its one-arena
+// device allocation, the V-cycle driver, the FP64 and mixed-precision outer
+// loops, the adjoint, and the component entry points.
+//
+// Memory: every device buffer of a handle is carved out of one cudaMalloc made
+// in mg_create (a pool in the sense of the paper's §4.2: allocation happens
+// once, never inside a solve).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mg_internal.cuh"
+
+using mg::Coef;
+using mg::Dims;
+using mg::i64;
+
+namespace {
+
+struct Level {
+    Dims d;
+    double h, h2, ih2;
+    double *fx64, *fy64, *fz64, *invd64;
+    float *fx32, *fy32, *fz32, *invd32;
+    double *x64, *b64;  // FP64 path, levels >= 1
+    float *x32, *b32;   // MIXED inner cycle, all levels (level 0: e and scaled r)
+};
+
+constexpr int kProfEvents = 8192;
+
+}  // namespace
+
+struct mg_handle {
+    mg_opts o;
+    cudaStream_t s;
+    int nlev;
+    Level lv[MG_MAX_LEVELS];
+    int nc;
+    double *pinv, *gj_tmp, *scal;
+    double *bt;        // zero-mean fine RHS
+    double *partials;  // reduction partials
+    double *red;       // device reduction results (16 doubles)
+    double *hred;      // pinned host copy of red
+    unsigned *err;     // device error word
+    void *arena;
+    size_t arena_bytes;
+    int have_op;
+    cudaEvent_t ev0, ev1;
+    // optional per-class timing of level-0 kernels (events recorded around launches)
+    int prof_on;
+    cudaEvent_t *pev;
+    int pev_used;
+    int pev_cls[kProfEvents / 2];
+    long long prof_count[MG_PROF_NCLASS];
+    double prof_ms[MG_PROF_NCLASS];
+    char msg[512];
+};
+
+namespace {
+
+int fail(mg_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define MG_CUDA(h, call)                                                                        \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail((h), MG_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                    \
+    } while (0)
+
+int check_launch(mg_handle *h, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(h, MG_ERR_CUDA, "kernel launch in %s failed: %s", where, cudaGetErrorString(e));
+    return MG_OK;
+}
+
+int num_levels(int nx, int ny, int nz, int coarsest) {
+    int nl = 1;
+    while (nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
+        int mx = nx > ny ? nx : ny;
+        mx = mx > nz ? mx : nz;
+        if (mx <= coarsest) break;
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        ++nl;
+    }
+    return nl;
+}
+
+template <typename T>
+Coef<T> coef(const Level &L);
+template <>
+Coef<double> coef<double>(const Level &L) {
+    return Coef<double>{L.fx64, L.fy64, L.fz64, L.invd64};
+}
+template <>
+Coef<float> coef<float>(const Level &L) {
+    return Coef<float>{L.fx32, L.fy32, L.fz32, L.invd32};
+}
+template <typename T>
+T *lvl_x(Level &L);
+template <>
+double *lvl_x<double>(Level &L) { return L.x64; }
+template <>
+float *lvl_x<float>(Level &L) { return L.x32; }
+template <typename T>
+T *lvl_b(Level &L);
+template <>
+double *lvl_b<double>(Level &L) { return L.b64; }
+template <>
+float *lvl_b<float>(Level &L) { return L.b32; }
+
+// ---- optional timing of level-0 kernels ------------------------------------------
+void prof_begin(mg_handle *h, int cls) {
+    if (!h->prof_on || h->pev_used + 2 > kProfEvents) return;
+    h->pev_cls[h->pev_used / 2] = cls;
+    cudaEventRecord(h->pev[h->pev_used], h->s);
+}
+void prof_end(mg_handle *h) {
+    if (!h->prof_on || h->pev_used + 2 > kProfEvents) return;
+    cudaEventRecord(h->pev[h->pev_used + 1], h->s);
+    h->pev_used += 2;
+}
+// called after a stream synchronisation: fold recorded pairs into the totals
+void prof_collect(mg_handle *h) {
+    if (!h->prof_on) return;
+    for (int q = 0; q + 1 < h->pev_used; q += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->pev[q], h->pev[q + 1]) == cudaSuccess) {
+            int cls = h->pev_cls[q / 2];
+            h->prof_count[cls] += 1;
+            h->prof_ms[cls] += ms;
+        }
+    }
+    h->pev_used = 0;
+}
+
+// ---- the V-cycle --------------------------------------------------------------------
+template <typename T>
+void smooth(mg_handle *h, int l, T *x, const T *b, int sweeps, int order) {
+    Level &L = h->lv[l];
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int half = 0; half < 2; ++half) {
+            int colour = order ? 1 - half : half;
+            if (l == 0) prof_begin(h, MG_PROF_SMOOTH);
+            mg::launch_rbgs_half<T>(h->s, L.d, L.h2, coef<T>(L), b, x, colour);
+            if (l == 0) prof_end(h);
+        }
+    }
+}
+
+template <typename T>
+void vcycle(mg_handle *h, int l, const T *b, T *x) {
+    Level &L = h->lv[l];
+    if (l == h->nlev - 1) {
+        if (l == 0) prof_begin(h, MG_PROF_COARSE);
+        mg::launch_coarse_matvec<T>(h->s, h->nc, h->pinv, b, x);
+        if (l == 0) prof_end(h);
+        return;
+    }
+    Level &C = h->lv[l + 1];
+    smooth<T>(h, l, x, b, h->o.pre, 0);
+    if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
+    mg::launch_resid_restrict<T>(h->s, L.d, L.ih2, coef<T>(L), b, x, lvl_b<T>(C));
+    if (l == 0) prof_end(h);
+    if (l + 1 < h->nlev - 1) cudaMemsetAsync(lvl_x<T>(C), 0, sizeof(T) * (size_t)C.d.n, h->s);
+    vcycle<T>(h, l + 1, lvl_b<T>(C), lvl_x<T>(C));
+    if (l == 0) prof_begin(h, MG_PROF_PROLONG);
+    mg::launch_prolong<T>(h->s, C.d, lvl_x<T>(C), x, h->o.prolong);
+    if (l == 0) prof_end(h);
+    smooth<T>(h, l, x, b, h->o.post, 1);
+}
+
+// ---- set-up of the operator hierarchy -------------------------------------------------
+int finish_operator(mg_handle *h) {
+    cudaStream_t s = h->s;
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+        Level &F = h->lv[l], &C = h->lv[l + 1];
+        mg::launch_coarsen(s, F.d, F.fx64, F.fy64, F.fz64, C.fx64, C.fy64, C.fz64);
+    }
+    bool mixed = h->o.precision == MG_MIXED;
+    for (int l = 0; l < h->nlev; ++l) {
+        Level &L = h->lv[l];
+        mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, mixed ? L.invd32 : nullptr);
+        if (mixed) {
+            mg::launch_to_f32(s, L.d.n, L.fx64, L.fx32);
+            mg::launch_to_f32(s, L.d.n, L.fy64, L.fy32);
+            mg::launch_to_f32(s, L.d.n, L.fz64, L.fz32);
+        }
+    }
+    // dense pseudo-inverse of the coarsest operator
+    Level &C = h->lv[h->nlev - 1];
+    double *A = h->pinv, *B = h->gj_tmp;
+    mg::launch_coarse_assemble(s, C.d, C.ih2, C.fx64, C.fy64, C.fz64, A, h->scal);
+    for (int k = 0; k < h->nc; ++k) {
+        mg::launch_gj_step(s, h->nc, k, A, B, h->scal);
+        double *t = A;
+        A = B;
+        B = t;
+    }
+    if (A != h->pinv) MG_CUDA(h, cudaMemcpyAsync(h->pinv, A, sizeof(double) * (size_t)h->nc * h->nc,
+                                                 cudaMemcpyDeviceToDevice, s));
+    mg::launch_pinv_finish(s, h->nc, h->pinv, h->scal);
+    int st = check_launch(h, "operator set-up");
+    if (st) return st;
+    unsigned herr = 0;
+    MG_CUDA(h, cudaMemcpyAsync(&herr, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(h, cudaStreamSynchronize(s));
+    if (herr) {
+        h->have_op = 0;
+        return fail(h, MG_ERR_DENSITY, "density / face coefficients must be finite and > 0");
+    }
+    h->have_op = 1;
+    return MG_OK;
+}
+
+// ---- one solve A x = b - mean(b), zero-mean x -------------------------------------------
+int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st) {
+    cudaStream_t s = h->s;
+    Level &F = h->lv[0];
+    const i64 n = F.d.n;
+    int hist_n = 0;
+    double hist[MG_HIST_LEN];
+    MG_CUDA(h, cudaEventRecord(h->ev0, s));
+    // b~ = b - mean(b), |b~|
+    mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red);
+    mg::launch_sub_mean(s, n, b, h->red, h->bt, h->partials, h->red + 2);
+    MG_CUDA(h, cudaMemcpyAsync(h->hred, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(h, cudaStreamSynchronize(s));
+    int rc = check_launch(h, "rhs preparation");
+    if (rc) return rc;
+    const double nb = std::sqrt(h->hred[2]);
+    if (!std::isfinite(nb)) return fail(h, MG_ERR_ARG, "right-hand side is not finite");
+    int status = MG_OK;
+    int cycles = 0;
+    double rr = 0.0;
+    if (nb == 0.0) {
+        MG_CUDA(h, cudaMemsetAsync(p, 0, sizeof(double) * (size_t)n, s));
+        hist[hist_n++] = 0.0;
+    } else {
+        if (warm) {
+            mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 4);
+            MG_CUDA(h, cudaMemcpyAsync(h->hred + 4, h->red + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+            MG_CUDA(h, cudaStreamSynchronize(s));
+            mg::launch_add_const(s, n, p, -h->hred[4] / (double)n);
+        } else {
+            MG_CUDA(h, cudaMemsetAsync(p, 0, sizeof(double) * (size_t)n, s));
+        }
+        const bool mixed = h->o.precision == MG_MIXED;
+        double scale = 1.0 / nb;  // r32 = scale * r (scale = 1 / previous residual norm)
+        auto residual = [&](bool write32) -> int {
+            prof_begin(h, MG_PROF_FINE_RESIDUAL);
+            mg::launch_fine_residual(s, F.d, F.ih2, F.fx64, F.fy64, F.fz64, h->bt, p,
+                                     write32 ? F.b32 : nullptr, scale, h->partials, h->red + 6);
+            prof_end(h);
+            MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->red + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            MG_CUDA(h, cudaStreamSynchronize(s));
+            prof_collect(h);
+            return check_launch(h, "fine residual");
+        };
+        rc = residual(mixed);
+        if (rc) return rc;
+        double rn = std::sqrt(h->hred[6]);
+        double mu = h->hred[7] / (double)n;
+        rr = rn / nb;
+        hist[hist_n++] = rr;
+        status = MG_ERR_NOT_CONVERGED;
+        if (rr <= h->o.rtol) status = MG_OK;
+        for (int c = 1; c <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++c) {
+            if (mixed) {
+                MG_CUDA(h, cudaMemsetAsync(F.x32, 0, sizeof(float) * (size_t)n, s));
+                vcycle<float>(h, 0, F.b32, F.x32);
+                prof_begin(h, MG_PROF_UPDATE);
+                mg::launch_update(s, n, p, F.x32, 1.0 / scale, mu);
+                prof_end(h);
+                scale = 1.0 / rn;
+            } else {
+                vcycle<double>(h, 0, h->bt, p);
+            }
+            rc = residual(mixed);
+            if (rc) return rc;
+            rn = std::sqrt(h->hred[6]);
+            double mu_new = h->hred[7] / (double)n;
+            if (!mixed) mg::launch_add_const(s, n, p, -mu_new);  // FP64 path: zero mean each cycle
+            mu = mixed ? mu_new : 0.0;
+            rr = rn / nb;
+            cycles = c;
+            if (hist_n < MG_HIST_LEN) hist[hist_n++] = rr;
+            if (!std::isfinite(rr) || rr > 1e12) {
+                status = MG_ERR_DIVERGED;
+                break;
+            }
+            if (rr <= h->o.rtol) status = MG_OK;
+        }
+        if (mu != 0.0) mg::launch_add_const(s, n, p, -mu);  // final zero-mean gauge
+    }
+    MG_CUDA(h, cudaEventRecord(h->ev1, s));
+    MG_CUDA(h, cudaEventSynchronize(h->ev1));
+    rc = check_launch(h, "solve");
+    if (rc) return rc;
+    if (st) {
+        st->status = status;
+        st->cycles = cycles;
+        st->relres = rr;
+        for (int q = 0; q < MG_HIST_LEN; ++q) st->relres_hist[q] = q < hist_n ? hist[q] : 0.0;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        st->ms = ms;
+    }
+    if (status == MG_ERR_NOT_CONVERGED)
+        fail(h, status, "not converged: relres %.3e after %d cycles (rtol %.3e)", rr, cycles, h->o.rtol);
+    if (status == MG_ERR_DIVERGED) fail(h, status, "diverged: relres %.3e at cycle %d", rr, cycles);
+    return status;
+}
+
+int check_level(mg_handle *h, int level, int dtype, bool need_coarser) {
+    if (!h) return MG_ERR_ARG;
+    if (level < 0 || level >= h->nlev || (need_coarser && level >= h->nlev - 1))
+        return fail(h, MG_ERR_ARG, "level %d out of range (levels: %d)", level, h->nlev);
+    if (dtype != MG_F64 && dtype != MG_F32) return fail(h, MG_ERR_ARG, "dtype must be MG_F64 or MG_F32");
+    if (dtype == MG_F32 && h->o.precision != MG_MIXED)
+        return fail(h, MG_ERR_ARG, "MG_F32 components need a MG_MIXED handle");
+    if (!h->have_op) return fail(h, MG_ERR_STATE, "coefficients not set");
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_opts(mg_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nx = o->ny = o->nz = 32;
+    o->h = 1.0 / 32;
+    o->precision = MG_FP64;
+    o->pre = o->post = 2;
+    o->coarsest = 4;
+    o->prolong = MG_PROLONG_TRILINEAR;
+    o->rtol = 1e-10;
+    o->max_cycles = 200;
+    o->warm_start = 0;
+}
+
+int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (!o) return MG_ERR_ARG;
+    if (o->nx < 1 || o->ny < 1 || o->nz < 1 || (i64)o->nx * o->ny * o->nz < 2 ||
+        (i64)o->nx * o->ny * o->nz > (i64)2000000000 || !(o->h > 0.0) || !std::isfinite(o->h) ||
+        (o->precision != MG_FP64 && o->precision != MG_MIXED) || o->pre < 0 || o->post < 0 ||
+        o->pre > 64 || o->post > 64 || o->coarsest < 2 ||
+        (o->prolong != MG_PROLONG_TRILINEAR && o->prolong != MG_PROLONG_CONSTANT) || !(o->rtol >= 0.0) ||
+        o->max_cycles < 0)
+        return MG_ERR_ARG;
+    int nl = num_levels(o->nx, o->ny, o->nz, o->coarsest);
+    if (nl > MG_MAX_LEVELS) return MG_ERR_ARG;
+    i64 nc = (i64)(o->nx >> (nl - 1)) * (o->ny >> (nl - 1)) * (o->nz >> (nl - 1));
+    if (nc > MG_MAX_COARSE) return MG_ERR_ARG;
+
+    mg_handle *h = new (std::nothrow) mg_handle();
+    if (!h) return MG_ERR_OOM;
+    h->o = *o;
+    h->s = (cudaStream_t)stream;
+    h->nlev = nl;
+    h->nc = (int)nc;
+    const bool mixed = o->precision == MG_MIXED;
+
+    // plan the arena: (pointer slot, bytes) pairs, each rounded up to 256 B
+    struct Slot {
+        void **p;
+        size_t bytes;
+    };
+    Slot slots[16 * MG_MAX_LEVELS + 16];
+    int ns = 0;
+    auto add = [&](void **p, size_t bytes) { slots[ns++] = Slot{p, (bytes + 255) & ~(size_t)255}; };
+    for (int l = 0; l < nl; ++l) {
+        Level &L = h->lv[l];
+        L.d = mg::make_dims(o->nx >> l, o->ny >> l, o->nz >> l);
+        L.h = std::ldexp(o->h, l);
+        L.h2 = L.h * L.h;
+        L.ih2 = 1.0 / L.h2;
+        size_t n = (size_t)L.d.n;
+        add((void **)&L.fx64, 8 * n);
+        add((void **)&L.fy64, 8 * n);
+        add((void **)&L.fz64, 8 * n);
+        add((void **)&L.invd64, 8 * n);
+        if (mixed) {
+            add((void **)&L.fx32, 4 * n);
+            add((void **)&L.fy32, 4 * n);
+            add((void **)&L.fz32, 4 * n);
+            add((void **)&L.invd32, 4 * n);
+            add((void **)&L.x32, 4 * n);
+            add((void **)&L.b32, 4 * n);
+        } else if (l > 0) {
+            add((void **)&L.x64, 8 * n);
+            add((void **)&L.b64, 8 * n);
+        }
+    }
+    add((void **)&h->pinv, 8 * (size_t)nc * nc);
+    add((void **)&h->gj_tmp, 8 * (size_t)nc * nc);
+    add((void **)&h->scal, 8 * 4);
+    add((void **)&h->bt, 8 * (size_t)h->lv[0].d.n);
+    add((void **)&h->partials, 16 * (size_t)mg::reduce_blocks(h->lv[0].d.n));
+    add((void **)&h->red, 8 * 16);
+    add((void **)&h->err, 256);
+    size_t total = 0;
+    for (int q = 0; q < ns; ++q) total += slots[q].bytes;
+    cudaError_t e = cudaMalloc(&h->arena, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    h->arena_bytes = total;
+    char *cur = (char *)h->arena;
+    for (int q = 0; q < ns; ++q) {
+        *slots[q].p = cur;
+        cur += slots[q].bytes;
+    }
+    if (cudaMallocHost((void **)&h->hred, 16 * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->arena);
+        delete h;
+        return MG_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(h->err, 0, 256, h->s) != cudaSuccess) {
+        mg_destroy(h);
+        return MG_ERR_CUDA;
+    }
+    h->msg[0] = 0;
+    *out = h;
+    return MG_OK;
+}
+
+int mg_destroy(mg_handle *h) {
+    if (!h) return MG_OK;
+    cudaStreamSynchronize(h->s);
+    if (h->pev) {
+        for (int q = 0; q < kProfEvents; ++q) cudaEventDestroy(h->pev[q]);
+        delete[] h->pev;
+    }
+    cudaEventDestroy(h->ev0);
+    cudaEventDestroy(h->ev1);
+    cudaFreeHost(h->hred);
+    cudaFree(h->arena);
+    delete h;
+    return MG_OK;
+}
+
+const char *mg_last_error(const mg_handle *h) { return h ? h->msg : "null handle"; }
+
+int mg_num_levels(const mg_handle *h) { return h ? h->nlev : MG_ERR_ARG; }
+
+int mg_level_dims(const mg_handle *h, int level, int *dims3) {
+    if (!h || !dims3 || level < 0 || level >= h->nlev) return MG_ERR_ARG;
+    dims3[0] = h->lv[level].d.nx;
+    dims3[1] = h->lv[level].d.ny;
+    dims3[2] = h->lv[level].d.nz;
+    return MG_OK;
+}
+
+int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac_dev,
+                              const double *rho_phase, double *rho_dev) {
+    if (!h) return MG_ERR_ARG;
+    if (nfrac < 1 || nfrac > 4 || !frac_dev || !rho_phase || !rho_dev)
+        return fail(h, MG_ERR_ARG, "mg_density_from_fractions: 1..4 fractions and non-null arrays");
+    for (int q = 0; q < nfrac; ++q)
+        if (!frac_dev[q]) return fail(h, MG_ERR_ARG, "fraction %d is NULL", q);
+    mg::launch_density(h->s, h->lv[0].d.n, nfrac, frac_dev, rho_phase, rho_dev);
+    return check_launch(h, "mg_density_from_fractions");
+}
+
+int mg_set_density(mg_handle *h, const double *rho) {
+    if (!h) return MG_ERR_ARG;
+    if (!rho) return fail(h, MG_ERR_ARG, "rho is NULL");
+    h->have_op = 0;
+    MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
+    Level &F = h->lv[0];
+    mg::launch_faces_from_rho(h->s, F.d, rho, F.fx64, F.fy64, F.fz64, h->err);
+    return finish_operator(h);
+}
+
+int mg_set_face_coeffs(mg_handle *h, const double *bx, const double *by, const double *bz) {
+    if (!h) return MG_ERR_ARG;
+    if (!bx || !by || !bz) return fail(h, MG_ERR_ARG, "face arrays must be non-null");
+    h->have_op = 0;
+    MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
+    Level &F = h->lv[0];
+    mg::launch_faces_from_api(h->s, F.d, bx, by, bz, F.fx64, F.fy64, F.fz64, h->err);
+    return finish_operator(h);
+}
+
+int mg_get_level_faces(mg_handle *h, int level, double *bx, double *by, double *bz) {
+    int rc = check_level(h, level, MG_F64, false);
+    if (rc) return rc;
+    if (!bx || !by || !bz) return fail(h, MG_ERR_ARG, "face arrays must be non-null");
+    Level &L = h->lv[level];
+    mg::launch_faces_to_api(h->s, L.d, L.fx64, L.fy64, L.fz64, bx, by, bz);
+    return check_launch(h, "mg_get_level_faces");
+}
+
+int mg_csf_faces(mg_handle *h, const double *f, const double *kappa, double *cx, double *cy,
+                 double *cz) {
+    if (!h) return MG_ERR_ARG;
+    if (!f || !kappa || !cx || !cy || !cz) return fail(h, MG_ERR_ARG, "mg_csf_faces: null array");
+    mg::launch_csf_faces(h->s, h->lv[0].d, h->o.h, f, kappa, cx, cy, cz);
+    return check_launch(h, "mg_csf_faces");
+}
+
+int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, const double *uz,
+           const double *csfx, const double *csfy, const double *csfz, double sigma, double *b) {
+    if (!h) return MG_ERR_ARG;
+    if (!b) return fail(h, MG_ERR_ARG, "mg_rhs: b is NULL");
+    bool u = ux || uy || uz;
+    if (u && !(ux && uy && uz)) return fail(h, MG_ERR_ARG, "mg_rhs: give all three velocity arrays or none");
+    bool csf = csfx || csfy || csfz;
+    if (csf && !(csfx && csfy && csfz)) return fail(h, MG_ERR_ARG, "mg_rhs: give all three csf arrays or none");
+    if (csf && !h->have_op) return fail(h, MG_ERR_STATE, "mg_rhs: the surface term needs coefficients set");
+    if (!std::isfinite(sigma)) return fail(h, MG_ERR_ARG, "mg_rhs: sigma not finite");
+    Level &F = h->lv[0];
+    mg::launch_rhs(h->s, F.d, h->o.h, b0, u ? ux : nullptr, uy, uz, F.fx64, F.fy64, F.fz64,
+                   csf ? csfx : nullptr, csf ? csfy : nullptr, csf ? csfz : nullptr, sigma, b);
+    return check_launch(h, "mg_rhs");
+}
+
+int mg_solve(mg_handle *h, const double *b, double *p, mg_stats *st) {
+    if (!h) return MG_ERR_ARG;
+    if (!b || !p) return fail(h, MG_ERR_ARG, "mg_solve: null array");
+    if (!h->have_op) return fail(h, MG_ERR_STATE, "mg_solve: coefficients not set");
+    h->msg[0] = 0;
+    return solve_impl(h, b, p, h->o.warm_start, st);
+}
+
+int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, float *gbx, float *gby,
+               float *gbz, const double *csfx, const double *csfy, const double *csfz, double sigma,
+               double *dLdsigma, mg_stats *st) {
+    if (!h) return MG_ERR_ARG;
+    if (!w || !p || !lam) return fail(h, MG_ERR_ARG, "mg_adjoint: w, p, lam must be non-null");
+    bool g = gbx || gby || gbz;
+    if (g && !(gbx && gby && gbz)) return fail(h, MG_ERR_ARG, "mg_adjoint: give all three gradients or none");
+    bool csf = csfx || csfy || csfz;
+    if (csf && !(csfx && csfy && csfz)) return fail(h, MG_ERR_ARG, "mg_adjoint: give all three csf arrays or none");
+    if (!h->have_op) return fail(h, MG_ERR_STATE, "mg_adjoint: coefficients not set");
+    h->msg[0] = 0;
+    int rc = solve_impl(h, w, lam, 0, st);
+    if (rc != MG_OK) return rc;
+    Level &F = h->lv[0];
+    if (g || dLdsigma) {
+        prof_begin(h, MG_PROF_ADJOINT_GRAD);
+        mg::launch_adjoint_grad(h->s, F.d, h->o.h, lam, p, F.fx64, F.fy64, F.fz64,
+                                csf ? csfx : nullptr, csf ? csfy : nullptr, csf ? csfz : nullptr,
+                                sigma, gbx, gby, gbz, h->partials, h->red + 8);
+        prof_end(h);
+        MG_CUDA(h, cudaMemcpyAsync(h->hred + 8, h->red + 8, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        MG_CUDA(h, cudaStreamSynchronize(h->s));
+        prof_collect(h);
+        rc = check_launch(h, "adjoint gradient");
+        if (rc) return rc;
+        if (dLdsigma) *dLdsigma = csf ? h->hred[8] : 0.0;
+    }
+    return MG_OK;
+}
+
+int mg_apply(mg_handle *h, int level, int dtype, const void *x, void *y) {
+    int rc = check_level(h, level, dtype, false);
+    if (rc) return rc;
+    if (!x || !y) return fail(h, MG_ERR_ARG, "mg_apply: null array");
+    Level &L = h->lv[level];
+    if (dtype == MG_F64) mg::launch_apply<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)x, (double *)y);
+    else mg::launch_apply<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)x, (float *)y);
+    return check_launch(h, "mg_apply");
+}
+
+int mg_smooth(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps, int order) {
+    int rc = check_level(h, level, dtype, false);
+    if (rc) return rc;
+    if (!x || !b || sweeps < 0) return fail(h, MG_ERR_ARG, "mg_smooth: bad argument");
+    if (dtype == MG_F64) smooth<double>(h, level, (double *)x, (const double *)b, sweeps, order);
+    else smooth<float>(h, level, (float *)x, (const float *)b, sweeps, order);
+    return check_launch(h, "mg_smooth");
+}
+
+int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b, void *r,
+                double *norm2) {
+    int rc = check_level(h, level, dtype, false);
+    if (rc) return rc;
+    if (!x || !b || !r) return fail(h, MG_ERR_ARG, "mg_residual: null array");
+    Level &L = h->lv[level];
+    if (dtype == MG_F64) {
+        mg::launch_residual<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x, (double *)r);
+        if (norm2) mg::launch_sum_sumsq<double>(h->s, L.d.n, (const double *)r, h->partials, h->red + 10);
+    } else {
+        mg::launch_residual<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)b, (const float *)x, (float *)r);
+        if (norm2) mg::launch_sum_sumsq<float>(h->s, L.d.n, (const float *)r, h->partials, h->red + 10);
+    }
+    rc = check_launch(h, "mg_residual");
+    if (rc) return rc;
+    if (norm2) {
+        MG_CUDA(h, cudaMemcpyAsync(h->hred + 10, h->red + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        MG_CUDA(h, cudaStreamSynchronize(h->s));
+        *norm2 = std::sqrt(h->hred[11]);
+    }
+    return MG_OK;
+}
+
+int mg_residual_restrict(mg_handle *h, int level, int dtype, const void *x, const void *b, void *bc) {
+    int rc = check_level(h, level, dtype, true);
+    if (rc) return rc;
+    if (!x || !b || !bc) return fail(h, MG_ERR_ARG, "mg_residual_restrict: null array");
+    Level &L = h->lv[level];
+    if (dtype == MG_F64)
+        mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x, (double *)bc);
+    else
+        mg::launch_resid_restrict<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)b, (const float *)x, (float *)bc);
+    return check_launch(h, "mg_residual_restrict");
+}
+
+int mg_prolong_correct(mg_handle *h, int level, int dtype, const void *ec, void *x) {
+    int rc = check_level(h, level, dtype, true);
+    if (rc) return rc;
+    if (!ec || !x) return fail(h, MG_ERR_ARG, "mg_prolong_correct: null array");
+    Level &C = h->lv[level + 1];
+    if (dtype == MG_F64) mg::launch_prolong<double>(h->s, C.d, (const double *)ec, (double *)x, h->o.prolong);
+    else mg::launch_prolong<float>(h->s, C.d, (const float *)ec, (float *)x, h->o.prolong);
+    return check_launch(h, "mg_prolong_correct");
+}
+
+int mg_coarse_solve(mg_handle *h, int dtype, const void *r, void *e) {
+    int rc = check_level(h, h ? h->nlev - 1 : 0, dtype, false);
+    if (rc) return rc;
+    if (!r || !e) return fail(h, MG_ERR_ARG, "mg_coarse_solve: null array");
+    if (dtype == MG_F64) mg::launch_coarse_matvec<double>(h->s, h->nc, h->pinv, (const double *)r, (double *)e);
+    else mg::launch_coarse_matvec<float>(h->s, h->nc, h->pinv, (const float *)r, (float *)e);
+    return check_launch(h, "mg_coarse_solve");
+}
+
+int mg_profile(mg_handle *h, int enable) {
+    if (!h) return MG_ERR_ARG;
+    MG_CUDA(h, cudaStreamSynchronize(h->s));
+    if (enable && !h->pev) {
+        h->pev = new (std::nothrow) cudaEvent_t[kProfEvents];
+        if (!h->pev) return fail(h, MG_ERR_OOM, "profile events");
+        for (int q = 0; q < kProfEvents; ++q) MG_CUDA(h, cudaEventCreate(&h->pev[q]));
+    }
+    h->prof_on = enable ? 1 : 0;
+    h->pev_used = 0;
+    for (int c = 0; c < MG_PROF_NCLASS; ++c) {
+        h->prof_count[c] = 0;
+        h->prof_ms[c] = 0.0;
+    }
+    return MG_OK;
+}
+
+int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms) {
+    if (!h || cls < 0 || cls >= MG_PROF_NCLASS) return MG_ERR_ARG;
+    MG_CUDA(h, cudaStreamSynchronize(h->s));
+    prof_collect(h);
+    if (launches) *launches = h->prof_count[cls];
+    if (ms) *ms = h->prof_ms[cls];
+    return MG_OK;
+}
+
+}  // extern "C"

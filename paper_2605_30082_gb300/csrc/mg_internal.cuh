@@ -1,0 +1,105 @@
+// Internal declarations of the GB300 multigrid Poisson library (not part of the ABI).
+//
+// Storage inside the library.  Every per-level array is a cell array of the
+// level's shape (nz, ny, nx), x fastest.  Face coefficients are kept as three
+// cell arrays of LOW faces: fx[c] is the coefficient of the face between cell
+// c and its x-1 neighbour (0 for i = 0, the wall); the high face of c is the
+// low face of its x+1 neighbour, or the wall (0) when i = nx-1.  The ABI's
+// (n+1)-long face layouts are converted on entry and exit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+typedef long long i64;
+
+struct Dims {
+    int nx, ny, nz;
+    i64 nxy, n;
+};
+
+inline Dims make_dims(int nx, int ny, int nz) {
+    Dims d;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.nxy = (i64)nx * ny;
+    d.n = d.nxy * nz;
+    return d;
+}
+
+template <typename T>
+struct Coef {
+    const T *fx, *fy, *fz;  // low-face coefficients
+    const T *invd;          // 1 / sum of the cell's interior face coefficients
+};
+
+// number of blocks used by every deterministic reduction over n elements
+int reduce_blocks(i64 n);
+constexpr int kReduceThreads = 256;
+
+// ---- setup kernels (FP64) -------------------------------------------------------
+void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
+                    const double *rho_phase, double *rho);
+void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *fx, double *fy,
+                           double *fz, unsigned *err);
+void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const double *by,
+                           const double *bz, double *fx, double *fy, double *fz, unsigned *err);
+void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double *fy,
+                         const double *fz, double *bx, double *by, double *bz);
+void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
+                    double *invd64, float *invd32);
+void launch_coarsen(cudaStream_t s, Dims fine, const double *ffx, const double *ffy,
+                    const double *ffz, double *cfx, double *cfy, double *cfz);
+void launch_to_f32(cudaStream_t s, i64 n, const double *src, float *dst);
+void launch_csf_faces(cudaStream_t s, Dims d, double h, const double *f, const double *kappa,
+                      double *cx, double *cy, double *cz);
+void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double *ux, const double *uy,
+                const double *uz, const double *fx, const double *fy, const double *fz,
+                const double *csfx, const double *csfy, const double *csfz, double sigma,
+                double *b);
+// dense coarse inverse (Gauss-Jordan on A_c + c 1 1^T, then minus 1/(c n^2))
+void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+                            const double *fz, double *M, double *scal);
+void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mout, double *scal);
+void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
+
+// ---- V-cycle kernels --------------------------------------------------------------
+template <typename T>
+void launch_rbgs_half(cudaStream_t s, Dims d, double h2, Coef<T> c, const T *b, T *p, int colour);
+template <typename T>
+void launch_apply(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *x, T *y);
+template <typename T>
+void launch_residual(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *b, const T *x, T *r);
+template <typename T>
+void launch_resid_restrict(cudaStream_t s, Dims fine, double ih2, Coef<T> c, const T *b,
+                           const T *x, T *bc);
+template <typename T>
+void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind);
+template <typename T>
+void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r, T *e);
+
+// ---- reductions, fine-level FP64 passes, adjoint -----------------------------------
+// partials: reduce_blocks(n) x 2 doubles; out: 2 doubles (deterministic order)
+template <typename T>
+void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out);
+// b64 = b - out_mean[0]/n, with sum of squares of b64 into out[0]
+void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
+                     double *partials, double *out);
+// fine FP64 residual r = b - A p: out[0] = sum r^2, out[1] = sum p; optional r32 = scale * r
+void launch_fine_residual(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+                          const double *fz, const double *b, const double *p, float *r32,
+                          double scale, double *partials, double *out);
+// p = p - shift + alpha * e32   (shift a host scalar)
+void launch_update(cudaStream_t s, i64 n, double *p, const float *e32, double alpha, double shift);
+void launch_add_const(cudaStream_t s, i64 n, double *p, double c);
+void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, const double *p,
+                         const double *fx, const double *fy, const double *fz, const double *csfx,
+                         const double *csfy, const double *csfz, double sigma, float *gx,
+                         float *gy, float *gz, double *partials, double *out);
+
+}  // namespace mg

@@ -1,0 +1,198 @@
+"""Step-by-step parity of the CUDA kernels with the FP64 oracle (through the C ABI).
+
+Grids span several thread blocks with ragged tails in every direction; each
+multigrid level of each grid is checked.  FP64 kernels must agree with the
+oracle to rounding (1e-13 relative L2); FP32 kernels, run on the FP32 copies
+of the coefficients, to 2e-6 (a few units of FP32 rounding, amplified by at
+most the stencil's 7 terms).
+"""
+import numpy as np
+import pytest
+import torch
+
+import dropfilm as D
+import oracle as O
+from paper_2605_30082_gb300 import MG_ERR_DENSITY, MG_ERR_STATE, MgError, Solver
+from paper_2605_30082_gb300 import _lib as L
+
+from _helpers import RHO_PHASE, dev, dropfilm_case, host, random_rho, rel
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(72, 40, 24), (40, 24, 56), (32, 32, 32)]
+TOL = {torch.float64: 1e-13, torch.float32: 2e-6}
+
+
+def make(dims, precision, seed=3, prolong="trilinear", coarsest=4):
+    nx, ny, nz = dims
+    h = 1.0 / 64
+    s = Solver(dims, h=h, precision=precision, coarsest=coarsest, prolong=prolong)
+    rho = random_rho(dims, seed)
+    s.set_density(dev(rho))
+    M = O.Multigrid(O.faces_from_density(rho), h, coarsest=coarsest,
+                    prolong=O.TRILINEAR if prolong == "trilinear" else O.CONSTANT)
+    return s, M
+
+
+def rnd(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_levels_and_faces_match_oracle(dims):
+    s, M = make(dims, "fp64")
+    assert s.num_levels == M.nlevels
+    for l in range(M.nlevels):
+        assert s.level_dims(l) == M.level_dims(l)
+        for g, o in zip(s.level_faces(l), M.level_faces(l)):
+            assert rel(host(g), o) < 1e-15
+
+
+def test_density_from_fractions_and_face_round_trip():
+    n = 24
+    fd, ff = D.fractions_ramp(D.scaled_geometry(n))
+    s = Solver((n, n, n), precision="fp64")
+    rho = s.density_from_fractions([fd.cuda(), ff.cuda()], RHO_PHASE)
+    rho_o = O.density([fd.numpy(), ff.numpy()], RHO_PHASE)
+    assert np.abs(host(rho) - rho_o).max() <= 1e-15 * rho_o.max()
+    faces = O.faces_from_density(rho_o)
+    s.set_face_coeffs(*(dev(f) for f in faces))
+    for g, o in zip(s.level_faces(0), faces):
+        assert rel(host(g), o) == 0.0
+    # wall entries are ignored on input and written back as zero
+    bad = [f.copy() for f in faces]
+    bad[0][:, :, 0] = -5.0
+    bad[2][-1] = np.nan
+    s.set_face_coeffs(*(dev(f) for f in bad))
+    for g, o in zip(s.level_faces(0), faces):
+        assert rel(host(g), o) == 0.0
+
+
+def test_csf_faces_and_rhs_match_oracle():
+    c = dropfilm_case(32)
+    h = c["h"]
+    s = Solver((32, 32, 32), precision="fp64")
+    s.set_density(dev(c["rho"]))
+    kappa = D.curvature_band(c["fd"], c["geom"])
+    csf = s.csf_faces(c["fd"].cuda(), kappa.cuda())
+    csf_o = O.csf_faces(c["fd"].numpy(), kappa.numpy(), h)
+    for g, o in zip(csf, csf_o):
+        assert rel(host(g), o) < 1e-14
+    u = tuple(a.cuda() for a in c["u"])
+    b = s.rhs(u=u)
+    assert rel(host(b), c["b"]) < 1e-14
+    b0 = rnd((32, 32, 32), 1)
+    b2 = s.rhs(u=u, csf=csf, sigma=0.03, b0=dev(b0))
+    want = b0 + O.rhs([a.numpy() for a in c["u"]], c["faces"], h, csf=csf_o, sigma=0.03)
+    assert rel(host(b2), want) < 1e-14
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_apply_smooth_residual_match_oracle(dims, dtype):
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed")
+    tol = TOL[dtype]
+    for l in range(M.nlevels):
+        nx, ny, nz = M.level_dims(l)
+        H = s.h * 2**l
+        faces = M.level_faces(l)
+        if dtype == torch.float32:  # the oracle sees the same FP32-rounded coefficients
+            faces = tuple(f.astype(np.float32).astype(np.float64) for f in faces)
+        x = rnd((nz, ny, nx), 10 + l).astype(np.float32 if dtype == torch.float32 else np.float64)
+        b = rnd((nz, ny, nx), 20 + l).astype(x.dtype)
+        xg, bg = dev(x, dtype), dev(b, dtype)
+        y = torch.empty_like(xg)
+        assert L.mg_apply(s._h, l, xg, y) == 0
+        assert rel(host(y), O.apply(faces, x, H)) < tol
+        r = torch.empty_like(xg)
+        st, nrm = L.mg_residual(s._h, l, xg, bg, r, want_norm=True)
+        r_o = O.residual(faces, b, x, H)
+        assert st == 0 and rel(host(r), r_o) < tol
+        assert abs(nrm - np.linalg.norm(r_o)) <= 10 * tol * np.linalg.norm(r_o)
+        for sweeps, order in ((1, 0), (1, 1), (2, 0)):
+            xs = xg.clone()
+            assert L.mg_smooth(s._h, l, xs, bg, sweeps, order) == 0
+            assert rel(host(xs), O.rbgs(faces, b, x, H, sweeps, order)) < tol
+        # after one pre sweep (red then black) the black rows are solved exactly
+        xs = xg.clone()
+        L.mg_smooth(s._h, l, xs, bg, 1, 0)
+        k, j, i = np.meshgrid(range(nz), range(ny), range(nx), indexing="ij")
+        black = (i + j + k) % 2 == 1
+        rb = O.residual(faces, b, host(xs), H)
+        assert np.abs(rb[black]).max() <= 50 * tol * np.abs(O.apply(faces, host(xs), H)).max()
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("prolong", ["trilinear", "constant"])
+def test_transfers_match_oracle(dims, dtype, prolong):
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed", prolong=prolong)
+    tol = TOL[dtype]
+    kind = O.TRILINEAR if prolong == "trilinear" else O.CONSTANT
+    for l in range(M.nlevels - 1):
+        nx, ny, nz = M.level_dims(l)
+        cx, cy, cz = M.level_dims(l + 1)
+        H = s.h * 2**l
+        faces = M.level_faces(l)
+        if dtype == torch.float32:
+            faces = tuple(f.astype(np.float32).astype(np.float64) for f in faces)
+        npd = np.float32 if dtype == torch.float32 else np.float64
+        x = rnd((nz, ny, nx), 30 + l).astype(npd)
+        b = rnd((nz, ny, nx), 40 + l).astype(npd)
+        bc = torch.empty((cz, cy, cx), dtype=dtype, device="cuda")
+        assert L.mg_residual_restrict(s._h, l, dev(x, dtype), dev(b, dtype), bc) == 0
+        assert rel(host(bc), O.restrict(O.residual(faces, b, x, H))) < tol
+        ec = rnd((cz, cy, cx), 50 + l).astype(npd)
+        xg = dev(x, dtype)
+        assert L.mg_prolong_correct(s._h, l, dev(ec, dtype), xg) == 0
+        assert rel(host(xg), O.prolong_correct(ec, x, kind)) < tol
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_coarse_solve_matches_oracle(dims, dtype):
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed")
+    l = M.nlevels - 1
+    nx, ny, nz = M.level_dims(l)
+    H = s.h * 2**l
+    npd = np.float32 if dtype == torch.float32 else np.float64
+    r = rnd((nz, ny, nx), 60).astype(npd)
+    e = torch.empty((nz, ny, nx), dtype=dtype, device="cuda")
+    assert L.mg_coarse_solve(s._h, dev(r, dtype), e) == 0
+    want = O.coarse_solve(M.level_faces(l), r.astype(np.float64), H)
+    assert rel(host(e), want) < (1e-11 if dtype == torch.float64 else 1e-6)
+
+
+def test_single_level_grid_is_a_dense_solve():
+    dims = (8, 6, 4)
+    s, M = make(dims, "fp64", coarsest=8)
+    assert s.num_levels == 1 and M.nlevels == 1
+    b = rnd((4, 6, 8), 70)
+    p = s.solve(dev(b))
+    assert s.last_stats.cycles == 1
+    want, _, _ = M.solve_exact(b)
+    assert rel(host(p), want) < 1e-11
+
+
+def test_density_errors_are_reported_not_faulted():
+    n = 16
+    s = Solver((n, n, n), precision="mixed", coarsest=8)
+    rho = np.full((n, n, n), 1.0)
+    rho[3, 4, 5] = 0.0
+    with pytest.raises(MgError) as ei:
+        s.set_density(dev(rho))
+    assert ei.value.code == MG_ERR_DENSITY
+    with pytest.raises(MgError) as ei:
+        s.solve(dev(np.ones((n, n, n))))
+    assert ei.value.code == MG_ERR_STATE
+    rho[3, 4, 5] = np.nan
+    with pytest.raises(MgError):
+        s.set_density(dev(rho))
+    faces = list(O.faces_from_density(np.ones((n, n, n))))
+    faces[1][2, 3, 4] = -1.0
+    with pytest.raises(MgError) as ei:
+        s.set_face_coeffs(*(dev(f) for f in faces))
+    assert ei.value.code == MG_ERR_DENSITY
+    rho[3, 4, 5] = 2.0
+    s.set_density(dev(rho))  # recovers
+    s.solve(dev(rnd((n, n, n), 1)))

@@ -1,0 +1,126 @@
+"""End-to-end parity of mg_solve with the FP64 oracle, and its error paths.
+
+Reference values:
+  O-iter  : the oracle's own V-cycle solve stopped at the same tolerance;
+            the GPU FP64 path runs the same algorithm and must reproduce it
+            (same cycle count, residual history, p to 1e-12).
+  O-exact : the oracle's V-cycles run to stagnation (relative residual
+            ~1e-15), i.e. the zero-mean discrete solution p*.  Both GPU
+            precisions must reach it to relative L2 <= 1e-9 at rtol 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_30082_gb300 import MG_ERR_ARG, MG_ERR_NOT_CONVERGED, MgError, Solver
+
+from _helpers import dev, dropfilm_case, host, random_rho, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c32():
+    c = dropfilm_case(32, subcell=True)
+    for coarsest in (4, 8):
+        M = O.Multigrid(c["faces"], c["h"], coarsest=coarsest)
+        c[f"iter{coarsest}"] = M.solve(c["b"], rtol=1e-10)
+        c[f"exact{coarsest}"] = M.solve_exact(c["b"])[0]
+    return c
+
+
+def test_fp64_reproduces_oracle_iteration_32cubed(c32):
+    s = Solver((32, 32, 32), h=c32["h"], precision="fp64", coarsest=4)
+    s.set_density(dev(c32["rho"]))
+    p = s.solve(dev(c32["b"]))
+    st = s.last_stats
+    p_o, st_o, nc_o, rr_o, hist_o = c32["iter4"]
+    assert st.cycles == nc_o
+    assert np.allclose(st.history(), hist_o, rtol=1e-6, atol=0)
+    assert rel(host(p), p_o) < 1e-12
+    assert rel(host(p), c32["exact4"]) < 1e-9
+    assert abs(host(p).mean()) < 1e-14 * np.abs(host(p)).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solution_matches_exact_32cubed(c32, prec):
+    s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8)
+    s.set_density(dev(c32["rho"]))
+    p = s.solve(dev(c32["b"]))
+    assert s.last_stats.relres <= 1e-10
+    assert rel(host(p), c32["exact8"]) < 1e-9
+    nc_o = c32["iter8"][2]
+    assert abs(s.last_stats.cycles - nc_o) <= 2
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (64, 48, 32), (96, 40, 24)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ragged_grids_match_exact(dims, prec):
+    nx, ny, nz = dims
+    h = 1.0 / 64
+    rho = random_rho(dims, 5, lo=1.2, hi=998.0) if dims != (64, 64, 64) else dropfilm_case(64)["rho"]
+    faces = O.faces_from_density(rho)
+    b = np.random.default_rng(7).standard_normal((nz, ny, nx))
+    M = O.Multigrid(faces, h, coarsest=8)
+    exact = M.solve_exact(b)[0]
+    s = Solver(dims, h=h, precision=prec, coarsest=8, max_cycles=400)
+    s.set_density(dev(rho))
+    p = s.solve(dev(b))
+    assert s.last_stats.relres <= 1e-10
+    assert rel(host(p), exact) < 1e-9
+    if prec == "fp64":
+        p_o, _, nc_o, _, _ = M.solve(b, rtol=1e-10, max_cycles=400)
+        assert s.last_stats.cycles == nc_o and rel(host(p), p_o) < 1e-12
+
+
+def test_solve_is_deterministic(c32):
+    s = Solver((32, 32, 32), h=c32["h"], precision="mixed", coarsest=8)
+    s.set_density(dev(c32["rho"]))
+    b = dev(c32["b"])
+    p1 = s.solve(b).clone()
+    p2 = s.solve(b)
+    assert torch.equal(p1, p2)
+
+
+def test_edge_cases():
+    n = 16
+    s = Solver((n, n, n), precision="mixed", coarsest=8)
+    s.set_density(dev(random_rho((n, n, n), 9)))
+    for b in (np.zeros((n, n, n)), np.full((n, n, n), 2.5)):
+        p = s.solve(dev(b))
+        assert s.last_stats.cycles == 0 and not host(p).any()
+    b = dev(np.random.default_rng(3).standard_normal((n, n, n)))
+    p = s.solve(b)
+    # warm start from the solution: no cycle needed
+    s2 = Solver((n, n, n), precision="mixed", coarsest=8, warm_start=True)
+    s2.set_density(dev(random_rho((n, n, n), 9)))
+    p2 = s2.solve(b, p=p.clone())
+    assert s2.last_stats.cycles == 0 and rel(host(p2), host(p)) < 1e-12
+    # warm start from a shifted solution: the gauge is restored
+    p3 = s2.solve(b, p=p.clone() + 7.0)
+    assert s2.last_stats.cycles == 0 and rel(host(p3), host(p)) < 1e-12
+    # max_cycles exhausted: status returned, last iterate kept with zero mean
+    s3 = Solver((n, n, n), precision="fp64", coarsest=8, rtol=1e-30, max_cycles=2)
+    s3.set_density(dev(random_rho((n, n, n), 9)))
+    with pytest.raises(MgError) as ei:
+        s3.solve(b)
+    assert ei.value.code == MG_ERR_NOT_CONVERGED
+    p4 = s3.solve(b, raise_on_nonconvergence=False)
+    assert s3.last_stats.cycles == 2 and abs(host(p4).mean()) < 1e-14
+    # non-finite RHS
+    bad = np.ones((n, n, n))
+    bad[1, 2, 3] = np.inf
+    with pytest.raises(MgError) as ei:
+        s.solve(dev(bad))
+    assert ei.value.code == MG_ERR_ARG
+
+
+def test_wrong_shapes_and_devices_are_rejected():
+    s = Solver((16, 16, 16), precision="fp64")
+    with pytest.raises(ValueError):
+        s.set_density(torch.ones((16, 16, 15), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        s.set_density(torch.ones((16, 16, 16), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        s.set_density(torch.ones((16, 16, 16), dtype=torch.float64))
