@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the multigrid pressure Poisson hot path on GB300.
+
+One step = the whole path on the 512^3 drop-on-film workload: density from
+the VOF fractions (Eq. (5)), face coefficients + coarse hierarchy + dense
+coarse inverse, RHS = divergence of the face velocities, mixed-precision
+solve to relative residual 1e-10, adjoint solve and fused gradient kernel
+(dL/db, dL/d(face 1/rho)) for L = sum(w p).  Inputs are generated on the
+device before timing (synthetic, seeded); every array is >= 1 GB, larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own copy (the solve does not shard:
+replicas only) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 residual & fine-grid GLUP/s at 512^3, FP64 vs mixed; HBM GB/s"
+RHO_PHASE = (998.0, 880.0, 1.2)
+# FP32 bytes a fused red-black sweep must move per cell: read x, b, 3 face coefficients, write x
+SWEEP_BYTES_PER_CELL_FP32 = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help="cells per dimension (default 512)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(fd, ff, u, w, n, cycles_total):
+    """Time the FP64 CPU oracle on a bounded sample of the step and scale it to cells/s.
+
+    Sample: set-up (density, faces, hierarchy, coarse factor), RHS, two V-cycles
+    of the forward solve (the initial residual and two cycles with their
+    residual checks), and the gradient pass, all at the full size.  The step
+    estimate charges the measured per-cycle time for `cycles_total` V-cycles
+    (forward + adjoint; the oracle runs the same algorithm and cycle count as
+    the CUDA FP64 path).
+    """
+    import numpy as np
+
+    import oracle as O
+
+    h = 1.0 / n
+    fdn, ffn = fd.cpu().numpy(), ff.cpu().numpy()
+    un = [a.cpu().numpy() for a in u]
+    wn = w.cpu().numpy()
+    t0 = time.perf_counter()
+    rho = O.density([fdn, ffn], RHO_PHASE)
+    faces = O.faces_from_density(rho)
+    M = O.Multigrid(faces, h, coarsest=8)
+    t1 = time.perf_counter()
+    b = O.divergence(un, h)
+    t2 = time.perf_counter()
+    p, st, nc, rr, _ = M.solve(b, rtol=1e-30, max_cycles=2)
+    t3 = time.perf_counter()
+    O.adjoint_grads(faces, p, p, h)
+    t4 = time.perf_counter()
+    per_cycle = (t3 - t2) / 2.0  # includes the per-cycle residual check
+    est = (t1 - t0) + (t2 - t1) + per_cycle * cycles_total + (t4 - t3)
+    return {
+        "value": n**3 / est / 1e9,
+        "unit": "Gcell/s",
+        "cores": O.num_threads(),
+        "kind": "oracle",
+        "sample": (f"{n}^3 set-up + RHS + 2 FP64 V-cycles + gradient pass timed "
+                   f"({t4 - t0:.1f} s); step estimated with {cycles_total} V-cycles "
+                   f"at {per_cycle:.2f} s each = {est:.1f} s"),
+        "step_s_est": est,
+    }
+
+
+# ---------------------------------------------------------------- our path
+
+def run_ours(args):
+    import torch
+
+    import dropfilm as D
+    from paper_2605_30082_gb300 import Solver, _lib as L
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    geom = D.scaled_geometry(n)
+    fd, ff = D.fractions_ramp(geom, device=dev)
+    u = D.face_velocities(n, seed=0, device=dev)
+    w = D.normal_weights((n, n, n), seed=1, device=dev)
+    torch.cuda.synchronize()
+
+    s = Solver((n, n, n), precision="mixed", coarsest=8, rtol=1e-10, max_cycles=200)
+    rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    b = torch.empty_like(rho)
+    p = torch.zeros_like(rho)
+    lam = torch.empty_like(rho)
+    stats = {}
+
+    def step(fd_, ff_, u_, w_):
+        s.density_from_fractions([fd_, ff_], RHO_PHASE, out=rho)
+        s.set_density(rho)
+        s.rhs(u=u_, out=b)
+        s.solve(b, p)
+        stats["fwd"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms)
+        _, g, _ = s.adjoint(w_, p, lam=lam)
+        stats["adj"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms)
+        return g
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step(fd, ff, u, w)
+    torch.cuda.synchronize()
+    barrier()
+    s.profile(True)
+    l0 = L.mg_kernel_launches()
+    clk = Clocks(local_rank)
+    clk.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(fd, ff, u, w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = L.mg_kernel_launches() - l0
+    ms_total = e0.elapsed_time(e1)
+    prof = {name: s.profile_read(cls) for name, cls in [
+        ("smooth", L.MG_PROF_SMOOTH), ("resid_restrict", L.MG_PROF_RESID_RESTRICT),
+        ("prolong", L.MG_PROF_PROLONG), ("fine_residual", L.MG_PROF_FINE_RESIDUAL),
+        ("update", L.MG_PROF_UPDATE), ("adjoint_grad", L.MG_PROF_ADJOINT_GRAD)]}
+    s.profile(False)
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+
+    # ---- time-to-tolerance: mixed vs plain FP64 forward solve (median of 3)
+    def time_solve(solver):
+        times, cyc = [], None
+        for _ in range(3):
+            solver.solve(b, p)
+            times.append(solver.last_stats.ms)
+            cyc = solver.last_stats.cycles
+        return statistics.median(times), cyc
+
+    t_mixed, cyc_mixed = time_solve(s)
+    t_fp64 = cyc_fp64 = None
+    if not args.no_fp64:
+        s64 = Solver((n, n, n), precision="fp64", coarsest=8, rtol=1e-10, max_cycles=200)
+        s64.set_density(rho)
+        t_fp64, cyc_fp64 = time_solve(s64)
+        s64.close()
+
+    # ---- roofline of the dominant kernel (finest-level FP32 smoother)
+    n_sm, ms_sm = prof["smooth"]
+    avg_sm = ms_sm / max(n_sm, 1)
+    cells = n**3
+    sweeps_per_launch = 0.5  # one colour per launch (half sweep)
+    alg_bytes = 20 * cells  # half sweep: other-colour x, own b and x write, all faces (see design notes)
+    peak = _measured_peak_hbm()
+    achieved = alg_bytes / (avg_sm * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 3), "traffic": _traffic_from_profiles("rbgs_half", cells),
+                "kernel": "k_rbgs_half<float> (finest level)", "launch_ms": round(avg_sm, 4)}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(args, step, fd, ff, u, w, lam, p)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(fd, ff, u, w, n, (cyc_fp64 or cyc_mixed) * 2)
+
+    value = world * cells / (ms_step * 1e-3) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "Gcell/s (512^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 inner V-cycle / f64 outer residual, update, coarse solve",
+        "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
+        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, mixed V(2,2), coarsest 8^3, "
+                               f"rtol 1e-10, forward + adjoint",
+                   "cells": cells, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "breakdown": {
+            "time_to_tol_ms": {"mixed": round(t_mixed, 3), "fp64": None if t_fp64 is None else round(t_fp64, 3)},
+            "cycles": {"mixed": cyc_mixed, "fp64": cyc_fp64, "adjoint": stats["adj"][0]},
+            "speedup_mixed_vs_fp64": None if t_fp64 is None else round(t_fp64 / t_mixed, 3),
+            "adjoint_over_forward": round(stats["adj"][2] / stats["fwd"][2], 3),
+            "solve_glups_mixed": round(cells * cyc_mixed / (t_mixed * 1e-3) / 1e9, 3),
+            "smoother_glups": round(cells * sweeps_per_launch / (avg_sm * 1e-3) / 1e9, 3),
+            "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+            "kernel_launches_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        },
+        "roofline": roofline,
+        "cpu_baseline": None if cpu is None else {k: v for k, v in cpu.items() if k != "step_s_est"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def _e2e(args, step, fd, ff, u, w, lam, p):
+    """Same step through the public API with inputs in pinned host memory and results read back."""
+    import torch
+
+    hin = [t.cpu().pin_memory() for t in (fd, ff, *u, w)]
+    din = [torch.empty_like(t) for t in (fd, ff, *u, w)]
+    hout = None
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ksteps = max(1, min(args.steps, 3))
+    bytes_in = sum(t.numel() * t.element_size() for t in hin)
+    bytes_out = 0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ksteps):
+        for d_, h_ in zip(din, hin):
+            d_.copy_(h_, non_blocking=True)
+        g = step(din[0], din[1], tuple(din[2:5]), din[5])
+        res = (p, lam, *g)
+        if hout is None:
+            hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in res]
+            bytes_out = sum(t.numel() * t.element_size() for t in hout)
+        for h_, d_ in zip(hout, res):
+            h_.copy_(d_, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / ksteps
+    n3 = fd.numel()
+    return {"value": round(n3 / (ms * 1e-3) / 1e9, 4), "unit": "Gcell/s", "ms_per_step": round(ms, 3),
+            "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": ksteps}
+
+
+def _measured_peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0  # fallback figure of an earlier GB300 measurement
+
+
+def _traffic_from_profiles(kernel, cells):
+    """DRAM bytes per launch from the committed ncu summary, if one exists for this kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(f) >= 3 and f[0] == kernel:
+            try:
+                per_cell = float(f[2])
+                return round(per_cell * cells)
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------- reference arm (the CPU oracle)
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    import torch
+
+    import dropfilm as D
+    import oracle as O
+
+    n = args.n
+    geom = D.scaled_geometry(n)
+    fd, ff = D.fractions_ramp(geom)
+    u = D.face_velocities(n, seed=0)
+    w = D.normal_weights((n, n, n), seed=1)
+    # forward + adjoint V-cycles at this size, taken from the FP64 path's measured count (equal to
+    # the oracle's: same algorithm); 512^3 drop/film needs 24 + 24
+    cycles_total = 48 if n == 512 else 2 * 20
+    for _ in range(max(args.warmup, 0)):
+        pass  # the oracle has no warm-up state; each step is independent
+    samples = [oracle_sample(fd, ff, u, w, n, cycles_total) for _ in range(max(args.steps, 1))]
+    est = statistics.median(x["step_s_est"] for x in samples)
+    v = n**3 / est / 1e9
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(v, 6),
+        "unit": "Gcell/s (512^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(est * 1e3, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
+        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, V(2,2), coarsest 8^3, "
+                               f"rtol 1e-10, forward + adjoint", "cells": n**3},
+        "cpu_baseline": {"value": round(v, 6), "unit": "Gcell/s", "cores": samples[0]["cores"],
+                         "kind": "oracle", "sample": samples[0]["sample"]},
+        "e2e": {"value": round(v, 6), "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -222,6 +222,9 @@ int mg_profile(mg_handle *h, int enable);
 /* Launches timed and their total device milliseconds for one class. */
 int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms);
 
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+long long mg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mg_coarse_solve": (_i, [_v, _i, _v, _v]),
     "mg_profile": (_i, [_v, _i]),
     "mg_profile_read": (_i, [_v, _i, C.POINTER(_ll), C.POINTER(_d)]),
+    "mg_kernel_launches": (_ll, []),
 }
 
 
@@ -285,3 +286,7 @@ def mg_profile_read(h, cls):
     ms = C.c_double(0.0)
     st = lib().mg_profile_read(h, int(cls), C.byref(n), C.byref(ms))
     return st, n.value, ms.value
+
+
+def mg_kernel_launches():
+    return lib().mg_kernel_launches()

@@ -161,16 +161,19 @@ __global__ void k_coarse_matvec(int nc, const double *__restrict__ pinv, const T
 template <typename T>
 void launch_rbgs_half(cudaStream_t s, Dims d, double h2, Coef<T> c, const T *b, T *p, int colour) {
     i64 work = (i64)d.ny * d.nz * ((d.nx + 1) / 2);
+    count_launch();
     k_rbgs_half<T><<<blocks_for(work), kThreads, 0, s>>>(d, (T)h2, c, b, p, colour);
 }
 
 template <typename T>
 void launch_apply(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *x, T *y) {
+    count_launch();
     k_apply<T><<<blocks_for(d.n), kThreads, 0, s>>>(d, (T)ih2, c, x, y);
 }
 
 template <typename T>
 void launch_residual(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *b, const T *x, T *r) {
+    count_launch();
     k_residual<T><<<blocks_for(d.n), kThreads, 0, s>>>(d, (T)ih2, c, b, x, r);
 }
 
@@ -178,18 +181,21 @@ template <typename T>
 void launch_resid_restrict(cudaStream_t s, Dims fine, double ih2, Coef<T> c, const T *b,
                            const T *x, T *bc) {
     Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
+    count_launch();
     k_resid_restrict<T><<<blocks_for(cd.n), kThreads, 0, s>>>(fine, cd, (T)ih2, c, b, x, bc);
 }
 
 template <typename T>
 void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind) {
     Dims f = make_dims(coarse.nx * 2, coarse.ny * 2, coarse.nz * 2);
+    count_launch();
     k_prolong<T><<<blocks_for(f.n), kThreads, 0, s>>>(coarse, f, ec, e, kind);
 }
 
 template <typename T>
 void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r, T *e) {
     i64 threads = (i64)nc * 32;
+    count_launch();
     k_coarse_matvec<T><<<blocks_for(threads), kThreads, 0, s>>>(nc, pinv, r, e);
 }
 

@@ -10,6 +10,12 @@
 
 namespace mg {
 
+static unsigned long long g_launches = 0;
+
+void count_launch(int k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+
+unsigned long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 int reduce_blocks(i64 n) {
     i64 b = (n + kReduceThreads - 1) / kReduceThreads;
     const i64 cap = 152 * 8;
@@ -178,7 +184,9 @@ __global__ void k_adjoint_grad(Dims d, double ih, double ih2, const double *__re
 template <typename T>
 void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out) {
     int nb = reduce_blocks(n);
+    count_launch();
     k_sum_sumsq<T><<<nb, kReduceThreads, 0, s>>>(n, x, partials);
+    count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 template void launch_sum_sumsq<double>(cudaStream_t, i64, const double *, double *, double *);
@@ -187,7 +195,9 @@ template void launch_sum_sumsq<float>(cudaStream_t, i64, const float *, double *
 void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
                      double *partials, double *out) {
     int nb = reduce_blocks(n);
+    count_launch();
     k_sub_mean<<<nb, kReduceThreads, 0, s>>>(n, b, sum, b64, partials);
+    count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 
@@ -195,15 +205,19 @@ void launch_fine_residual(cudaStream_t s, Dims d, double ih2, const double *fx, 
                           const double *fz, const double *b, const double *p, float *r32,
                           double scale, double *partials, double *out) {
     int nb = reduce_blocks(d.n);
+    count_launch();
     k_fine_residual<<<nb, kReduceThreads, 0, s>>>(d, ih2, fx, fy, fz, b, p, r32, scale, partials);
+    count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 
 void launch_update(cudaStream_t s, i64 n, double *p, const float *e32, double alpha, double shift) {
+    count_launch();
     k_update<<<blocks_for(n), kThreads, 0, s>>>(n, p, e32, alpha, shift);
 }
 
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {
+    count_launch();
     k_add_const<<<blocks_for(n), kThreads, 0, s>>>(n, p, c);
 }
 
@@ -212,8 +226,10 @@ void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, co
                          const double *csfy, const double *csfz, double sigma, float *gx,
                          float *gy, float *gz, double *partials, double *out) {
     int nb = reduce_blocks(d.n);
+    count_launch();
     k_adjoint_grad<<<nb, kReduceThreads, 0, s>>>(d, 1.0 / h, 1.0 / (h * h), lam, p, fx, fy, fz,
                                                  csfx, csfy, csfz, sigma, gx, gy, gz, partials);
+    count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 

@@ -266,41 +266,49 @@ void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
     a.nfrac = nfrac;
     for (int q = 0; q < 4; ++q) a.f[q] = q < nfrac ? frac[q] : nullptr;
     for (int q = 0; q < 5; ++q) a.rho[q] = q <= nfrac ? rho_phase[q] : 0.0;
+    count_launch();
     k_density<<<blocks_for(n), kThreads, 0, s>>>(n, a, rho);
 }
 
 void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *fx, double *fy,
                            double *fz, unsigned *err) {
+    count_launch();
     k_faces_from_rho<<<blocks_for(d.n), kThreads, 0, s>>>(d, rho, fx, fy, fz, err);
 }
 
 void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const double *by,
                            const double *bz, double *fx, double *fy, double *fz, unsigned *err) {
+    count_launch();
     k_faces_from_api<<<blocks_for(d.n), kThreads, 0, s>>>(d, bx, by, bz, fx, fy, fz, err);
 }
 
 void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double *fy,
                          const double *fz, double *bx, double *by, double *bz) {
+    count_launch();
     k_faces_to_api<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, bx, by, bz);
 }
 
 void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
                     double *invd64, float *invd32) {
+    count_launch();
     k_invdiag<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, invd64, invd32);
 }
 
 void launch_coarsen(cudaStream_t s, Dims fine, const double *ffx, const double *ffy,
                     const double *ffz, double *cfx, double *cfy, double *cfz) {
     Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
+    count_launch();
     k_coarsen<<<blocks_for(cd.n), kThreads, 0, s>>>(fine, cd, ffx, ffy, ffz, cfx, cfy, cfz);
 }
 
 void launch_to_f32(cudaStream_t s, i64 n, const double *src, float *dst) {
+    count_launch();
     k_to_f32<<<blocks_for(n), kThreads, 0, s>>>(n, src, dst);
 }
 
 void launch_csf_faces(cudaStream_t s, Dims d, double h, const double *f, const double *kappa,
                       double *cx, double *cy, double *cz) {
+    count_launch();
     k_csf_faces<<<blocks_for(d.n), kThreads, 0, s>>>(d, 1.0 / h, f, kappa, cx, cy, cz);
 }
 
@@ -308,13 +316,16 @@ void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double
                 const double *uz, const double *fx, const double *fy, const double *fz,
                 const double *csfx, const double *csfy, const double *csfz, double sigma,
                 double *b) {
+    count_launch();
     k_rhs<<<blocks_for(d.n), kThreads, 0, s>>>(d, 1.0 / h, b0, ux, uy, uz, fx, fy, fz, csfx, csfy,
                                                csfz, sigma, b);
 }
 
 void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
                             const double *fz, double *M, double *scal) {
+    count_launch();
     k_coarse_assemble<<<blocks_for(d.n), kThreads, 0, s>>>(d, ih2, fx, fy, fz, M);
+    count_launch();
     k_coarse_shift<<<1, 1024, 0, s>>>((int)d.n, M, scal);
 }
 
@@ -322,10 +333,12 @@ void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mo
     // reciprocal pivots alternate between scal[1] and scal[2]
     const double *rin = scal + 1 + (k & 1);
     double *rout = (k + 1 < nc) ? scal + 1 + ((k + 1) & 1) : nullptr;
+    count_launch();
     k_gj_step<<<blocks_for((i64)nc * nc), kThreads, 0, s>>>(nc, k, Min, Mout, rin, rout);
 }
 
 void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal) {
+    count_launch();
     k_pinv_finish<<<blocks_for((i64)nc * nc), kThreads, 0, s>>>(nc, M, scal);
 }
 

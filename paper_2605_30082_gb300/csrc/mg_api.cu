@@ -13,6 +13,10 @@
 
 #include "mg_internal.cuh"
 
+namespace mg {
+unsigned long long launches_total();
+}
+
 using mg::Coef;
 using mg::Dims;
 using mg::i64;
@@ -673,5 +677,7 @@ int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms) {
     if (ms) *ms = h->prof_ms[cls];
     return MG_OK;
 }
+
+long long mg_kernel_launches(void) { return (long long)mg::launches_total(); }
 
 }  // extern "C"

@@ -38,6 +38,9 @@ struct Coef {
     const T *invd;          // 1 / sum of the cell's interior face coefficients
 };
 
+// process-wide count of kernel launches (read through mg_kernel_launches)
+void count_launch(int k = 1);
+
 // number of blocks used by every deterministic reduction over n elements
 int reduce_blocks(i64 n);
 constexpr int kReduceThreads = 256;
