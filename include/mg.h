@@ -225,6 +225,33 @@ int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 long long mg_kernel_launches(void);
 
+/* ---- allocation-free entry point ----------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory when they need a solve: code being recorded into a
+ * CUDA graph by stream capture (cudaMalloc is not allowed during capture),
+ * programs whose device memory belongs to another allocator (a framework's
+ * caching pool, where an extra cudaMalloc can fail or fragment the pool), and
+ * loops held to a fixed memory budget.
+ *
+ * e = A^+ (r - mean r): the exact zero-mean solution of the cell-centred
+ * Neumann operator above on a small grid, for face coefficients bx, by, bz in
+ * the face layouts (wall entries ignored; interior entries finite and > 0,
+ * else MG_ERR_DENSITY).  r, e: cell arrays.  All pointers are device
+ * pointers; `stream` is a cudaStream_t (NULL = legacy default stream).  The
+ * call builds the dense pseudo-inverse from scratch and applies it; it needs
+ * no handle and calls no cudaMalloc, cudaFree or other allocating routine.
+ * Working memory is one fixed array in this library's device image (about
+ * 4.2 MB, held on every GPU that loads the library until the process exits),
+ * so nx*ny*nz must be at most MG_NOALLOC_MAX_CELLS (MG_ERR_ARG otherwise).
+ * The first call on each device looks up that array's device address (with
+ * that device current); make it before any stream capture.  Every call uses
+ * the same array, which keeps the previous call's contents: calls that can
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Synchronises `stream` before returning. */
+#define MG_NOALLOC_MAX_CELLS 512
+int mg_dense_solve_noalloc(int nx, int ny, int nz, double h, const double *bx, const double *by,
+                           const double *bz, const double *r, double *e, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

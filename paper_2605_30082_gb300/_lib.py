@@ -22,6 +22,7 @@ MG_FP64, MG_MIXED = 0, 1
 MG_PROLONG_TRILINEAR, MG_PROLONG_CONSTANT = 0, 1
 MG_F64, MG_F32 = 0, 1
 MG_MAX_LEVELS, MG_MAX_COARSE, MG_HIST_LEN = 24, 1024, 256
+MG_NOALLOC_MAX_CELLS = 512
 (MG_PROF_SMOOTH, MG_PROF_RESID_RESTRICT, MG_PROF_PROLONG, MG_PROF_COARSE,
  MG_PROF_FINE_RESIDUAL, MG_PROF_UPDATE, MG_PROF_ADJOINT_GRAD, MG_PROF_NCLASS) = range(8)
 
@@ -75,6 +76,7 @@ SIGNATURES = {
     "mg_profile": (_i, [_v, _i]),
     "mg_profile_read": (_i, [_v, _i, C.POINTER(_ll), C.POINTER(_d)]),
     "mg_kernel_launches": (_ll, []),
+    "mg_dense_solve_noalloc": (_i, [_i, _i, _i, _d, _v, _v, _v, _v, _v, _v]),
 }
 
 
@@ -290,3 +292,16 @@ def mg_profile_read(h, cls):
 
 def mg_kernel_launches():
     return lib().mg_kernel_launches()
+
+
+def mg_dense_solve_noalloc(dims, h, bx, by, bz, r, e, stream=None):
+    """Allocation-free exact small-grid solve (see include/mg.h); returns the status."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    fs = face_shapes(dims)
+    cs = cell_shape(dims)
+    nx, ny, nz = dims
+    return lib().mg_dense_solve_noalloc(nx, ny, nz, float(h), _dev(bx, shape=fs[0], name="bx"),
+                                        _dev(by, shape=fs[1], name="by"), _dev(bz, shape=fs[2], name="bz"),
+                                        _dev(r, shape=cs, name="r"), _dev(e, shape=cs, name="e"),
+                                        C.c_void_p(stream.cuda_stream))
