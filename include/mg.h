@@ -183,8 +183,21 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
 int mg_apply(mg_handle *h, int level, int dtype, const void *x, void *y);
 
 /* `sweeps` full red-black Gauss-Seidel sweeps on x in place for A_l x = b;
- * order 0 = red then black (pre-smoothing), 1 = black then red (post). */
+ * order 0 = red then black (pre-smoothing), 1 = black then red (post).
+ * The smoothing components (this one and the two fused ones below) run in the
+ * handle's V-cycle precision: MG_F64 on MG_FP64 handles, MG_F32 on MG_MIXED. */
 int mg_smooth(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps, int order);
+
+/* The V-cycle's downward step, fused as the cycle runs it: x <- `sweeps` pre-smoothing
+ * sweeps (red then black) starting from x (from zero when x_is_zero; x's contents are
+ * then ignored), and bc (level+1) = mean of the 8 children of b - A_l x. */
+int mg_presmooth_restrict(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps,
+                          int x_is_zero, void *bc);
+
+/* The V-cycle's upward step, fused as the cycle runs it: x <- `sweeps`
+ * post-smoothing sweeps (black then red) of x + P ec (ec on level+1). */
+int mg_prolong_postsmooth(mg_handle *h, int level, int dtype, const void *ec, void *x, const void *b,
+                          int sweeps);
 
 /* r = b - A_l x, and (if norm2 != NULL) |r|_2 on the host (synchronises). */
 int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b, void *r,
@@ -206,9 +219,10 @@ int mg_coarse_solve(mg_handle *h, int dtype, const void *r, void *e);
  * elapsed device time per class.  It measures the kernels inside real solves;
  * it adds two event records per timed launch and nothing else. */
 enum {
-    MG_PROF_SMOOTH = 0,         /* finest-level red-black Gauss-Seidel sweeps */
-    MG_PROF_RESID_RESTRICT = 1, /* finest-level residual + restriction */
-    MG_PROF_PROLONG = 2,        /* prolongation + correction into the finest level */
+    MG_PROF_SMOOTH = 0,         /* finest-level fused sweep passes (with the restriction or
+                                   prolongation some of them carry) */
+    MG_PROF_RESID_RESTRICT = 1, /* finest-level standalone residual + restriction (pre = 0) */
+    MG_PROF_PROLONG = 2,        /* finest-level standalone prolongation + correction (post = 0) */
     MG_PROF_COARSE = 3,         /* dense coarse solve when the finest level is the coarsest */
     MG_PROF_FINE_RESIDUAL = 4,  /* FP64 residual / norm pass of the outer loop */
     MG_PROF_UPDATE = 5,         /* MIXED solution update */

@@ -69,6 +69,8 @@ SIGNATURES = {
     "mg_adjoint": (_i, [_v, _v, _v, _v, _v, _v, _v, _v, _v, _v, _d, C.POINTER(_d), C.POINTER(mg_stats)]),
     "mg_apply": (_i, [_v, _i, _i, _v, _v]),
     "mg_smooth": (_i, [_v, _i, _i, _v, _v, _i, _i]),
+    "mg_presmooth_restrict": (_i, [_v, _i, _i, _v, _v, _i, _i, _v]),
+    "mg_prolong_postsmooth": (_i, [_v, _i, _i, _v, _v, _v, _i]),
     "mg_residual": (_i, [_v, _i, _i, _v, _v, _v, C.POINTER(_d)]),
     "mg_residual_restrict": (_i, [_v, _i, _i, _v, _v, _v]),
     "mg_prolong_correct": (_i, [_v, _i, _i, _v, _v]),
@@ -247,6 +249,22 @@ def mg_smooth(h, level, x, b, sweeps, order=0):
     dt = _dtype_code(x)
     s = _lvl_shape(h, level)
     return lib().mg_smooth(h, level, dt, _dev(x, x.dtype, s, "x"), _dev(b, x.dtype, s, "b"), int(sweeps), int(order))
+
+
+def mg_presmooth_restrict(h, level, x, b, sweeps, bc, x_is_zero=False):
+    dt = _dtype_code(x)
+    s = _lvl_shape(h, level)
+    sc = _lvl_shape(h, level + 1)
+    return lib().mg_presmooth_restrict(h, level, dt, _dev(x, x.dtype, s, "x"), _dev(b, x.dtype, s, "b"),
+                                       int(sweeps), int(bool(x_is_zero)), _dev(bc, x.dtype, sc, "bc"))
+
+
+def mg_prolong_postsmooth(h, level, ec, x, b, sweeps):
+    dt = _dtype_code(x)
+    s = _lvl_shape(h, level)
+    sc = _lvl_shape(h, level + 1)
+    return lib().mg_prolong_postsmooth(h, level, dt, _dev(ec, x.dtype, sc, "ec"), _dev(x, x.dtype, s, "x"),
+                                       _dev(b, x.dtype, s, "b"), int(sweeps))
 
 
 def mg_residual(h, level, x, b, r, want_norm=False):

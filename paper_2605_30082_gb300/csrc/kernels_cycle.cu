@@ -1,12 +1,11 @@
-// V-cycle kernels on one level: red-black Gauss-Seidel half sweeps, operator
-// application, residual, fused residual + 8:1 restriction, prolongation +
-// correction, and the dense coarse solve.  Templated on the level's element
+// Unfused V-cycle kernels on one level: the FP64 red-black half sweep,
+// operator application, residual, residual + 8:1 restriction, prolongation +
+// correction, and the dense coarse solve.  (The FP32 sweeps, with restriction
+// or prolongation fused in, are the z-marching passes of kernels_pass.cu.)  Templated on the level's element
 // type (double for the FP64 path, float for the inner cycle of MIXED).
 //
 // Operator (cell-centred, homogeneous Neumann walls):
 //   (A x)_c = ih2 * sum_{interior faces f of c} beta_f (x_c - x_nb(f))
-// Red-black Gauss-Seidel half sweep of colour q ((i+j+k) % 2 == q):
-//   x_c = (h2 b_c + sum_f beta_f x_nb) / sum_f beta_f
 // Restriction: coarse b = mean of the 8 children of the fine residual.
 // Prolongation: cell-centred trilinear (weights 3/4, 1/4 per axis; at a wall
 // the missing coarse neighbour is replaced by the parent) or constant.
@@ -56,19 +55,23 @@ __device__ __forceinline__ T flux_sum(const Dims &d, int i, int j, int k, i64 c,
     return s;
 }
 
+// red-black Gauss-Seidel half sweep of colour q ((i+j+k) % 2 == q), in place:
+//   x_c = (h2 b_c + sum_f beta_f x_nb) * invd_c   (invd = 1 / sum_f beta_f)
+// one thread per cell of the colour; used by the FP64 V-cycle, whose cost is
+// FP64 arithmetic rather than bytes, so it keeps zero redundant work
 template <typename T>
 __global__ void k_rbgs_half(Dims d, T h2, Coef<T> cf, const T *__restrict__ b, T *x, int colour) {
-    int half = (d.nx + 1) >> 1;
-    i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    i64 rows = (i64)d.ny * d.nz;
+    const int half = (d.nx + 1) >> 1;
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 rows = (i64)d.ny * d.nz;
     if (t >= rows * half) return;
-    i64 row = t / half;
-    int m = (int)(t - row * half);
-    int j = (int)(row % d.ny), k = (int)(row / d.ny);
-    int i = 2 * m + ((colour + j + k) & 1);
+    const i64 row = t / half;
+    const int m = (int)(t - row * half);
+    const int j = (int)(row % d.ny), k = (int)(row / d.ny);
+    const int i = 2 * m + ((colour + j + k) & 1);
     if (i >= d.nx) return;
-    i64 c = row * d.nx + i;
-    T num = nb_sum(d, i, j, k, c, cf, x);
+    const i64 c = row * d.nx + i;
+    const T num = nb_sum(d, i, j, k, c, cf, x);
     x[c] = (h2 * b[c] + num) * cf.invd[c];
 }
 
@@ -158,11 +161,11 @@ __global__ void k_coarse_matvec(int nc, const double *__restrict__ pinv, const T
 
 }  // namespace
 
-template <typename T>
-void launch_rbgs_half(cudaStream_t s, Dims d, double h2, Coef<T> c, const T *b, T *p, int colour) {
-    i64 work = (i64)d.ny * d.nz * ((d.nx + 1) / 2);
+void launch_rbgs_half64(cudaStream_t s, Dims d, double h2, Coef<double> c, const double *b, double *p,
+                        int colour) {
+    const i64 work = (i64)d.ny * d.nz * ((d.nx + 1) / 2);
     count_launch();
-    k_rbgs_half<T><<<blocks_for(work), kThreads, 0, s>>>(d, (T)h2, c, b, p, colour);
+    k_rbgs_half<double><<<blocks_for(work), kThreads, 0, s>>>(d, h2, c, b, p, colour);
 }
 
 template <typename T>
@@ -200,7 +203,6 @@ void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r
 }
 
 #define MG_INSTANTIATE(T)                                                                        \
-    template void launch_rbgs_half<T>(cudaStream_t, Dims, double, Coef<T>, const T *, T *, int); \
     template void launch_apply<T>(cudaStream_t, Dims, double, Coef<T>, const T *, T *);          \
     template void launch_residual<T>(cudaStream_t, Dims, double, Coef<T>, const T *, const T *,  \
                                      T *);                                                       \

@@ -90,8 +90,74 @@ __global__ void k_sub_mean(i64 n, const double *__restrict__ b, const double *__
     block_sum2(q, 0.0, partials + 2 * blockIdx.x);
 }
 
+__device__ __forceinline__ i64 sto(const Lay &L, int x, int y, int z) {
+    const i64 row = (i64)z * L.ny + y;
+    if (!L.split) return row * L.nx + x;
+    return ((x + y + z) & 1) * L.half + row * L.hx + (x >> 1);
+}
+
+// FP64 -> FP32 by truncating the IEEE-754 fields with integer operations (the
+// binary64 layout: 1 sign, 11 exponent (bias 1023), 52 fraction bits; binary32:
+// 1, 8 (bias 127), 23).  Rounds toward zero; results below the FP32 normal range
+// become zero, above it infinity; NaN stays NaN.  Keeps the conversion off the
+// FP64 pipe, which GB300 runs at a small fraction of the FP32 rate.
+__device__ __forceinline__ float d2f_trunc(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) return __uint_as_float(sign);
+    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)e32 << 23) | frac);
+}
+
+// FP32 -> FP64 exactly with integer operations (FP32 subnormals become zero)
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned ed = (e == 0xffu) ? 0x7ffu : (e - 127u + 1023u);
+    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// h^2 r = h^2 b - (d p_c - sum_f beta_f p_nb), d = sum_f beta_f (8 FP64 operations per cell);
+// partials: (sum (h^2 r)^2 accumulated in FP32 per thread, sum p in FP64); r32 = s32 * h^2 r
+__global__ void k_fine_resid2(Dims d, Lay L, double h2, const double *__restrict__ fx,
+                              const double *__restrict__ fy, const double *__restrict__ fz,
+                              const double *__restrict__ dg, const double *__restrict__ b,
+                              const double *__restrict__ p, float *r32, float s32, double *partials) {
+    float q = 0.f;
+    double sp = 0.0;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const i64 nxy = d.nxy;
+    for (i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x; c < d.n; c += (i64)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const i64 row = c / nx;
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const double pc = p[c];
+        double acc = h2 * b[c];
+        if (i > 0) acc = fma(fx[c], p[c - 1], acc);
+        if (i < nx - 1) acc = fma(fx[c + 1], p[c + 1], acc);
+        if (j > 0) acc = fma(fy[c], p[c - nx], acc);
+        if (j < ny - 1) acc = fma(fy[c + nx], p[c + nx], acc);
+        if (k > 0) acc = fma(fz[c], p[c - nxy], acc);
+        if (k < nz - 1) acc = fma(fz[c + nxy], p[c + nxy], acc);
+        acc = fma(-dg[c], pc, acc);
+        const float rf = d2f_trunc(acc);
+        if (r32) r32[sto(L, i, j, k)] = rf * s32;
+        q = fmaf(rf, rf, q);
+        sp += pc;
+    }
+    block_sum2((double)q, sp, partials + 2 * blockIdx.x);
+}
+
 // r = b - ih2 * sum_f beta_f (p_c - p_nb); partials: (sum r^2, sum p)
-__global__ void k_fine_residual(Dims d, double ih2, const double *__restrict__ fx,
+__global__ void k_fine_residual(Dims d, Lay L, double ih2, const double *__restrict__ fx,
                                 const double *__restrict__ fy, const double *__restrict__ fz,
                                 const double *__restrict__ b, const double *__restrict__ p,
                                 float *r32, double scale, double *partials) {
@@ -109,16 +175,20 @@ __global__ void k_fine_residual(Dims d, double ih2, const double *__restrict__ f
         if (k > 0) s += fz[c] * (pc - p[c - d.nxy]);
         if (k < d.nz - 1) s += fz[c + d.nxy] * (pc - p[c + d.nxy]);
         double r = b[c] - s * ih2;
-        if (r32) r32[c] = (float)(r * scale);
+        if (r32) r32[sto(L, i, j, k)] = (float)(r * scale);
         q += r * r;
         sp += pc;
     }
     block_sum2(q, sp, partials + 2 * blockIdx.x);
 }
 
-__global__ void k_update(i64 n, double *p, const float *__restrict__ e, double alpha, double shift) {
-    i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < n) p[m] = (p[m] - shift) + alpha * (double)e[m];
+// p = (p - shift) + alpha e: 2 FP64 operations, the FP32 value widened exactly with integer operations
+__global__ void k_update(Dims d, Lay L, double *p, const float *__restrict__ e, double alpha, double shift) {
+    const i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= d.n) return;
+    const int i = (int)(m % d.nx);
+    const i64 row = m / d.nx;
+    p[m] = fma(alpha, f2d_exact(e[sto(L, i, (int)(row % d.ny), (int)(row / d.ny))]), p[m] - shift);
 }
 
 __global__ void k_add_const(i64 n, double *p, double c) {
@@ -201,19 +271,29 @@ void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, 
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 
-void launch_fine_residual(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const double *fx, const double *fy,
                           const double *fz, const double *b, const double *p, float *r32,
                           double scale, double *partials, double *out) {
     int nb = reduce_blocks(d.n);
     count_launch();
-    k_fine_residual<<<nb, kReduceThreads, 0, s>>>(d, ih2, fx, fy, fz, b, p, r32, scale, partials);
+    k_fine_residual<<<nb, kReduceThreads, 0, s>>>(d, L, ih2, fx, fy, fz, b, p, r32, scale, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
 
-void launch_update(cudaStream_t s, i64 n, double *p, const float *e32, double alpha, double shift) {
+void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
+                        const double *fz, const double *diag, const double *b, const double *p, float *r32,
+                        float s32, double *partials, double *out) {
+    int nb = reduce_blocks(d.n);
     count_launch();
-    k_update<<<blocks_for(n), kThreads, 0, s>>>(n, p, e32, alpha, shift);
+    k_fine_resid2<<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    count_launch();
+    k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+
+void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift) {
+    count_launch();
+    k_update<<<blocks_for(d.n), kThreads, 0, s>>>(d, L, p, e32, alpha, shift);
 }
 
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {

@@ -91,7 +91,7 @@ __global__ void k_faces_to_api(Dims d, const double *__restrict__ fx, const doub
 }
 
 __global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *__restrict__ fy,
-                          const double *__restrict__ fz, double *invd64, float *invd32) {
+                          const double *__restrict__ fz, double *invd64, double *diag) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
     int i = (int)(c % d.nx);
@@ -104,9 +104,8 @@ __global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *_
     if (j < d.ny - 1) s += fy[c + d.nx];
     s += fz[c];
     if (k < d.nz - 1) s += fz[c + d.nxy];
-    double inv = 1.0 / s;
-    if (invd64) invd64[c] = inv;
-    if (invd32) invd32[c] = (float)inv;
+    if (invd64) invd64[c] = 1.0 / s;
+    if (diag) diag[c] = s;
 }
 
 // coarse low face = mean of the 4 fine low faces that tile it
@@ -289,9 +288,9 @@ void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double 
 }
 
 void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
-                    double *invd64, float *invd32) {
+                    double *invd64, double *diag) {
     count_launch();
-    k_invdiag<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, invd64, invd32);
+    k_invdiag<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, invd64, diag);
 }
 
 void launch_coarsen(cudaStream_t s, Dims fine, const double *ffx, const double *ffy,

@@ -1,0 +1,569 @@
+// FP32 V-cycle kernels on colour-split levels.
+//
+// Storage: an FP32 level with even nx keeps every cell array colour-split: all
+// red cells ((x+y+z) even) first, then all black cells, each colour row by row
+// with the cell at x stored at k = x >> 1.  Levels with odd nx (possible only on
+// the coarsest level) keep the natural layout.  `sto` maps (x, y, z) to the
+// storage index in either case.
+//
+// For a cell of colour c at (k, y, z), x = 2k + p with p = (c + y + z) & 1, the six
+// neighbours all have the other colour and sit in the other half at
+//   x-1: k + p - 1,   x+1: k + p      (same row)
+//   y-1, y+1, z-1, z+1: k             (the rows above, below, before, after)
+// so a half sweep reads the other colour with unit-stride, vectorisable loads and
+// no shared memory: 4 B of the other colour's x, 8 B of 1/rho (both colours) or
+// 12 B of face coefficients, and 4 B of b per updated cell, plus the write.
+//
+// Coefficients: SFORM uses s = 1/rho per cell and beta_f = (s_c + s_nb)/2 (the
+// finest level when the operator came from a density); otherwise the low-face
+// arrays fx, fy, fz (beta of the face between a cell and its x-1, y-1, z-1
+// neighbour) stored in the same split layout.
+//
+// Two exact properties of red-black Gauss-Seidel shorten the V-cycle:
+//  - after the last pre-smoothing sweep (black last) every black row is solved,
+//    so the black residuals are zero and the restriction sums red residuals only;
+//  - the first post-smoothing sweep (black first) overwrites every black cell, so
+//    the coarse correction only needs to be added to the red cells.
+#include "mg_internal.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ i64 sto(const Lay &L, int x, int y, int z) {
+    const i64 row = (i64)z * L.ny + y;
+    if (!L.split) return row * L.nx + x;
+    return ((x + y + z) & 1) * L.half + row * L.hx + (x >> 1);
+}
+
+struct Coef32 {
+    const float *s;             // SFORM when non-null
+    const float *fx, *fy, *fz;  // face form otherwise
+};
+
+// ---- generic (scalar, any layout) stencil pieces --------------------------------------
+// sum_f beta_f x_nb and sum_f beta_f at cell (x, y, z), SFORM carries a factor 2
+__device__ __forceinline__ void stencil_any(const Lay &L, const Coef32 &cf, const float *__restrict__ xv,
+                                            int x, int y, int z, float &num, float &den) {
+    const i64 c = sto(L, x, y, z);
+    const bool hx0 = x > 0, hx1 = x < L.nx - 1, hy0 = y > 0, hy1 = y < L.ny - 1, hz0 = z > 0, hz1 = z < L.nz - 1;
+    const i64 n0 = hx0 ? sto(L, x - 1, y, z) : c, n1 = hx1 ? sto(L, x + 1, y, z) : c;
+    const i64 n2 = hy0 ? sto(L, x, y - 1, z) : c, n3 = hy1 ? sto(L, x, y + 1, z) : c;
+    const i64 n4 = hz0 ? sto(L, x, y, z - 1) : c, n5 = hz1 ? sto(L, x, y, z + 1) : c;
+    float w0, w1, w2, w3, w4, w5;
+    if (cf.s) {
+        const float sc = cf.s[c];
+        w0 = hx0 ? sc + cf.s[n0] : 0.f;
+        w1 = hx1 ? sc + cf.s[n1] : 0.f;
+        w2 = hy0 ? sc + cf.s[n2] : 0.f;
+        w3 = hy1 ? sc + cf.s[n3] : 0.f;
+        w4 = hz0 ? sc + cf.s[n4] : 0.f;
+        w5 = hz1 ? sc + cf.s[n5] : 0.f;
+    } else {
+        w0 = cf.fx[c];
+        w1 = hx1 ? cf.fx[n1] : 0.f;
+        w2 = cf.fy[c];
+        w3 = hy1 ? cf.fy[n3] : 0.f;
+        w4 = cf.fz[c];
+        w5 = hz1 ? cf.fz[n5] : 0.f;
+    }
+    float nm = w0 * xv[n0];
+    nm += w1 * xv[n1];
+    nm += w2 * xv[n2];
+    nm += w3 * xv[n3];
+    nm += w4 * xv[n4];
+    nm += w5 * xv[n5];
+    num = nm;
+    den = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
+}
+
+// half sweep of colour `col`, one thread per cell of that colour, any layout
+__global__ void k_half_any(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col,
+                           int from_zero) {
+    const int halfw = (L.nx + 1) >> 1;
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 rows = (i64)L.ny * L.nz;
+    if (t >= rows * halfw) return;
+    const i64 row = t / halfw;
+    const int m = (int)(t - row * halfw);
+    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    const int x = 2 * m + ((col + y + z) & 1);
+    if (x >= L.nx) return;
+    float num, den;
+    stencil_any(L, cf, xv, x, y, z, num, den);
+    if (from_zero) num = 0.f;
+    const float hh = cf.s ? 2.f * h2 : h2;
+    xv[sto(L, x, y, z)] = __fdividef(hh * b[sto(L, x, y, z)] + num, den);
+}
+
+// ---- vectorised half sweep on split levels (hx % 4 == 0) ---------------------------------
+// one thread updates 4 consecutive cells (k0..k0+3) of colour col in one row
+template <bool SFORM, bool FROM_ZERO>
+__global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col) {
+    const int hx = L.hx, kv = hx >> 2;
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 rows = (i64)L.ny * L.nz;
+    if (t >= rows * kv) return;
+    const i64 row = t / kv;
+    const int k0 = (int)(t - row * kv) << 2;
+    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    const int p = (col + y + z) & 1;  // x = 2k + p
+    const i64 own = col * L.half + row * hx + k0;
+    const i64 opp = (1 - col) * L.half + row * hx + k0;
+    const bool hy0 = y > 0, hy1 = y < L.ny - 1, hz0 = z > 0, hz1 = z < L.nz - 1;
+    const i64 dy = hx, dz = (i64)L.ny * hx;
+    // same-row other-colour window: xm[v] = O[k0+v+p-1], xp[v] = O[k0+v+p]
+    auto window = [&](const float *O, float (&m)[4], float (&q)[4]) {
+        const float4 c4 = *reinterpret_cast<const float4 *>(O + opp);
+        if (p) {
+            const float e = (k0 + 4 < hx) ? O[opp + 4] : 0.f;
+            m[0] = c4.x; m[1] = c4.y; m[2] = c4.z; m[3] = c4.w;
+            q[0] = c4.y; q[1] = c4.z; q[2] = c4.w; q[3] = e;
+        } else {
+            const float e = (k0 > 0) ? O[opp - 1] : 0.f;
+            m[0] = e; m[1] = c4.x; m[2] = c4.y; m[3] = c4.z;
+            q[0] = c4.x; q[1] = c4.y; q[2] = c4.z; q[3] = c4.w;
+        }
+    };
+    auto ld4 = [&](const float *A, i64 off, bool ok, float (&v)[4]) {
+        if (ok) {
+            const float4 c4 = *reinterpret_cast<const float4 *>(A + off);
+            v[0] = c4.x; v[1] = c4.y; v[2] = c4.z; v[3] = c4.w;
+        } else {
+            v[0] = v[1] = v[2] = v[3] = 0.f;
+        }
+    };
+    // wall masks along x: the first cell of a row has no x-1 when p == 0, the last no x+1 when p == 1
+    const bool xw0 = (p == 0 && k0 == 0), xw1 = (p == 1 && k0 + 4 == hx);
+    float xm[4], xp[4], ym[4], yp[4], zm[4], zp[4];
+    if (!FROM_ZERO) {
+        window(xv, xm, xp);
+        ld4(xv, opp - dy, hy0, ym);
+        ld4(xv, opp + dy, hy1, yp);
+        ld4(xv, opp - dz, hz0, zm);
+        ld4(xv, opp + dz, hz1, zp);
+    }
+    float w0[4], w1[4], w2[4], w3[4], w4[4], w5[4];
+    if (SFORM) {
+        float sc[4], sm_[4], sp_[4], s2[4], s3[4], s4[4], s5[4];
+        ld4(cf.s, own, true, sc);
+        window(cf.s, sm_, sp_);
+        ld4(cf.s, opp - dy, hy0, s2);
+        ld4(cf.s, opp + dy, hy1, s3);
+        ld4(cf.s, opp - dz, hz0, s4);
+        ld4(cf.s, opp + dz, hz1, s5);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            w0[v] = (v == 0 && xw0) ? 0.f : sc[v] + sm_[v];
+            w1[v] = (v == 3 && xw1) ? 0.f : sc[v] + sp_[v];
+            w2[v] = hy0 ? sc[v] + s2[v] : 0.f;
+            w3[v] = hy1 ? sc[v] + s3[v] : 0.f;
+            w4[v] = hz0 ? sc[v] + s4[v] : 0.f;
+            w5[v] = hz1 ? sc[v] + s5[v] : 0.f;
+        }
+    } else {
+        float d0[4], d1[4];
+        ld4(cf.fx, own, true, w0);           // low x face (0 at x = 0)
+        window(cf.fx, d0, w1);               // high x face = the x+1 neighbour's low face
+        if (xw1) w1[3] = 0.f;
+        ld4(cf.fy, own, true, w2);
+        ld4(cf.fy, opp + dy, hy1, w3);
+        ld4(cf.fz, own, true, w4);
+        ld4(cf.fz, opp + dz, hz1, w5);
+        (void)d0;
+        (void)d1;
+    }
+    float bb[4];
+    ld4(b, own, true, bb);
+    const float hh = SFORM ? 2.f * h2 : h2;
+    float out[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        float num = 0.f;
+        if (!FROM_ZERO) {
+            num = w0[v] * xm[v];
+            num += w1[v] * xp[v];
+            num += w2[v] * ym[v];
+            num += w3[v] * yp[v];
+            num += w4[v] * zm[v];
+            num += w5[v] * zp[v];
+        }
+        const float den = ((w0[v] + w1[v]) + (w2[v] + w3[v])) + (w4[v] + w5[v]);
+        out[v] = __fdividef(hh * bb[v] + num, den);
+    }
+    *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
+// The red children of coarse cell (I, J, K) are the red cells at k = I of the 4 fine rows
+// (2J + b, 2K + c); one thread handles coarse cells I0..I0+3 of one coarse row.
+template <bool SFORM>
+__global__ void k_rr_red_vec(Lay L, Lay Lc, float ih2, Coef32 cf, const float *__restrict__ b,
+                             const float *__restrict__ xv, float *bc) {
+    const int hx = L.hx, kv = hx >> 2;
+    const i64 T = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 crows = (i64)Lc.ny * Lc.nz;
+    if (T >= crows * kv) return;
+    const i64 crow = T / kv;
+    const int k0 = (int)(T - crow * kv) << 2;
+    const int J = (int)(crow % Lc.ny), K = (int)(crow / Lc.ny);
+    const i64 dy = hx, dz = (i64)L.ny * hx;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        const int y = 2 * J + (ch & 1), z = 2 * K + (ch >> 1);
+        const int p = (y + z) & 1;  // red cells of this row sit at x = 2k + p
+        const i64 row = (i64)z * L.ny + y;
+        const i64 own = row * hx + k0;               // red half
+        const i64 opp = L.half + row * hx + k0;      // black half
+        const bool hy0 = y > 0, hy1 = y < L.ny - 1, hz0 = z > 0, hz1 = z < L.nz - 1;
+        const bool xw0 = (p == 0 && k0 == 0), xw1 = (p == 1 && k0 + 4 == hx);
+        auto window = [&](const float *O, float (&m)[4], float (&q)[4]) {
+            const float4 c4 = *reinterpret_cast<const float4 *>(O + opp);
+            if (p) {
+                const float e = (k0 + 4 < hx) ? O[opp + 4] : 0.f;
+                m[0] = c4.x; m[1] = c4.y; m[2] = c4.z; m[3] = c4.w;
+                q[0] = c4.y; q[1] = c4.z; q[2] = c4.w; q[3] = e;
+            } else {
+                const float e = (k0 > 0) ? O[opp - 1] : 0.f;
+                m[0] = e; m[1] = c4.x; m[2] = c4.y; m[3] = c4.z;
+                q[0] = c4.x; q[1] = c4.y; q[2] = c4.z; q[3] = c4.w;
+            }
+        };
+        auto ld4 = [&](const float *A, i64 off, bool ok, float (&v)[4]) {
+            if (ok) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(A + off);
+                v[0] = c4.x; v[1] = c4.y; v[2] = c4.z; v[3] = c4.w;
+            } else {
+                v[0] = v[1] = v[2] = v[3] = 0.f;
+            }
+        };
+        float xc[4], xm[4], xp[4], ym[4], yp[4], zm[4], zp[4], bb[4];
+        ld4(xv, own, true, xc);
+        window(xv, xm, xp);
+        ld4(xv, opp - dy, hy0, ym);
+        ld4(xv, opp + dy, hy1, yp);
+        ld4(xv, opp - dz, hz0, zm);
+        ld4(xv, opp + dz, hz1, zp);
+        ld4(b, own, true, bb);
+        float w0[4], w1[4], w2[4], w3[4], w4[4], w5[4];
+        if (SFORM) {
+            float sc[4], sm_[4], sp_[4], s2[4], s3[4], s4[4], s5[4];
+            ld4(cf.s, own, true, sc);
+            window(cf.s, sm_, sp_);
+            ld4(cf.s, opp - dy, hy0, s2);
+            ld4(cf.s, opp + dy, hy1, s3);
+            ld4(cf.s, opp - dz, hz0, s4);
+            ld4(cf.s, opp + dz, hz1, s5);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                w0[v] = (v == 0 && xw0) ? 0.f : 0.5f * (sc[v] + sm_[v]);
+                w1[v] = (v == 3 && xw1) ? 0.f : 0.5f * (sc[v] + sp_[v]);
+                w2[v] = hy0 ? 0.5f * (sc[v] + s2[v]) : 0.f;
+                w3[v] = hy1 ? 0.5f * (sc[v] + s3[v]) : 0.f;
+                w4[v] = hz0 ? 0.5f * (sc[v] + s4[v]) : 0.f;
+                w5[v] = hz1 ? 0.5f * (sc[v] + s5[v]) : 0.f;
+            }
+        } else {
+            float d0[4];
+            ld4(cf.fx, own, true, w0);
+            window(cf.fx, d0, w1);
+            if (xw1) w1[3] = 0.f;
+            ld4(cf.fy, own, true, w2);
+            ld4(cf.fy, opp + dy, hy1, w3);
+            ld4(cf.fz, own, true, w4);
+            ld4(cf.fz, opp + dz, hz1, w5);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float ax = w0[v] * (xc[v] - xm[v]);
+            ax += w1[v] * (xc[v] - xp[v]);
+            ax += w2[v] * (xc[v] - ym[v]);
+            ax += w3[v] * (xc[v] - yp[v]);
+            ax += w4[v] * (xc[v] - zm[v]);
+            ax += w5[v] * (xc[v] - zp[v]);
+            acc[v] += bb[v] - ax * ih2;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) bc[sto(Lc, k0 + v, J, K)] = acc[v] * 0.125f;
+}
+
+// ---- vectorised red-only prolongation + correction (split fine level, hx % 4 == 0) -------
+// one thread adds P ec to 4 consecutive red cells of one fine row
+__global__ void k_prolong_red_vec(Lay L, Lay Lc, const float *__restrict__ ec, float *xv, int kind) {
+    const int hx = L.hx, kv = hx >> 2;
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 rows = (i64)L.ny * L.nz;
+    if (t >= rows * kv) return;
+    const i64 row = t / kv;
+    const int k0 = (int)(t - row * kv) << 2;
+    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    const int p = (y + z) & 1;  // red x = 2k + p, coarse I = k
+    const int J = y >> 1, K = z >> 1;
+    float out[4];
+    float4 x4 = *reinterpret_cast<const float4 *>(xv + row * hx + k0);
+    out[0] = x4.x; out[1] = x4.y; out[2] = x4.z; out[3] = x4.w;
+    if (kind == MG_PROLONG_CONSTANT) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[v] += __ldg(ec + sto(Lc, k0 + v, J, K));
+    } else {
+        int J2 = (y & 1) ? J + 1 : J - 1;
+        int K2 = (z & 1) ? K + 1 : K - 1;
+        if (J2 < 0 || J2 >= Lc.ny) J2 = J;
+        if (K2 < 0 || K2 >= Lc.nz) K2 = K;
+        // coarse values at I = k0 - 1 .. k0 + 4 of the four coarse rows
+        float c[4][6];
+        const int Js[2] = {J, J2}, Ks[2] = {K, K2};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int JJ = Js[r & 1], KK = Ks[r >> 1];
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+                int I = k0 - 1 + u;
+                if (I < 0) I = 0;
+                if (I >= Lc.nx) I = Lc.nx - 1;
+                c[r][u] = __ldg(ec + sto(Lc, I, JJ, KK));
+            }
+        }
+        const float w0 = 0.75f, w1 = 0.25f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int I = k0 + v;
+            int I2 = p ? I + 1 : I - 1;
+            if (I2 < 0 || I2 >= Lc.nx) I2 = I;
+            const int u1 = I + 1 - k0, u2 = I2 + 1 - k0;  // positions in c[][]
+            float a = w0 * w0 * w0 * c[0][u1];
+            a += w1 * w0 * w0 * c[0][u2];
+            a += w0 * w1 * w0 * c[1][u1];
+            a += w1 * w1 * w0 * c[1][u2];
+            a += w0 * w0 * w1 * c[2][u1];
+            a += w1 * w0 * w1 * c[2][u2];
+            a += w0 * w1 * w1 * c[3][u1];
+            a += w1 * w1 * w1 * c[3][u2];
+            out[v] += a;
+        }
+    }
+    *reinterpret_cast<float4 *>(xv + row * hx + k0) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// ---- residual (generic) ------------------------------------------------------------------
+// r(x, y, z) = b - A x   (FP32, any layout)
+__device__ __forceinline__ float resid_any(const Lay &L, float ih2, const Coef32 &cf, const float *__restrict__ b,
+                                           const float *__restrict__ xv, int x, int y, int z) {
+    float num, den;
+    stencil_any(L, cf, xv, x, y, z, num, den);
+    const i64 c = sto(L, x, y, z);
+    const float ax = xv[c] * den - num;
+    return b[c] - (cf.s ? 0.5f : 1.f) * ax * ih2;
+}
+
+__global__ void k_residual_any(Lay L, float ih2, Coef32 cf, const float *__restrict__ b,
+                               const float *__restrict__ xv, float *r, int apply_only) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    const i64 c = sto(L, x, y, z);
+    if (apply_only) {
+        float num, den;
+        stencil_any(L, cf, xv, x, y, z, num, den);
+        r[c] = (cf.s ? 0.5f : 1.f) * (xv[c] * den - num) * ih2;
+    } else {
+        r[c] = resid_any(L, ih2, cf, b, xv, x, y, z);
+    }
+}
+
+// coarse b = mean of the children's residuals; red_only: black children contribute 0
+// (exact after a black half sweep, which solves every black row)
+__global__ void k_resid_restrict_any(Lay L, Lay Lc, float ih2, Coef32 cf, const float *__restrict__ b,
+                                     const float *__restrict__ xv, float *bc, int red_only) {
+    const i64 T = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= Lc.n) return;
+    const int I = (int)(T % Lc.nx);
+    const i64 row = T / Lc.nx;
+    const int J = (int)(row % Lc.ny), K = (int)(row / Lc.ny);
+    float s = 0.f;
+    for (int cc = 0; cc < 2; ++cc)
+        for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa) {
+                const int x = 2 * I + aa, y = 2 * J + bb, z = 2 * K + cc;
+                if (red_only && ((x + y + z) & 1)) continue;
+                s += resid_any(L, ih2, cf, b, xv, x, y, z);
+            }
+    bc[sto(Lc, I, J, K)] = s * 0.125f;
+}
+
+// x += P ec on cells of colour `only_col` (0 red, 1 black) or on all cells (-1)
+__global__ void k_prolong_any(Lay L, Lay Lc, const float *__restrict__ ec, float *xv, int kind, int only_col) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    if (only_col >= 0 && ((x + y + z) & 1) != only_col) return;
+    const int I = x >> 1, J = y >> 1, K = z >> 1;
+    float v;
+    if (kind == MG_PROLONG_CONSTANT) {
+        v = ec[sto(Lc, I, J, K)];
+    } else {
+        int I2 = (x & 1) ? I + 1 : I - 1;
+        int J2 = (y & 1) ? J + 1 : J - 1;
+        int K2 = (z & 1) ? K + 1 : K - 1;
+        if (I2 < 0 || I2 >= Lc.nx) I2 = I;
+        if (J2 < 0 || J2 >= Lc.ny) J2 = J;
+        if (K2 < 0 || K2 >= Lc.nz) K2 = K;
+        const float w0 = 0.75f, w1 = 0.25f;
+        v = w0 * w0 * w0 * ec[sto(Lc, I, J, K)];
+        v += w1 * w0 * w0 * ec[sto(Lc, I2, J, K)];
+        v += w0 * w1 * w0 * ec[sto(Lc, I, J2, K)];
+        v += w1 * w1 * w0 * ec[sto(Lc, I2, J2, K)];
+        v += w0 * w0 * w1 * ec[sto(Lc, I, J, K2)];
+        v += w1 * w0 * w1 * ec[sto(Lc, I2, J, K2)];
+        v += w0 * w1 * w1 * ec[sto(Lc, I, J2, K2)];
+        v += w1 * w1 * w1 * ec[sto(Lc, I2, J2, K2)];
+    }
+    xv[sto(L, x, y, z)] += v;
+}
+
+// e = pinv r on the coarsest level (FP64 accumulation), pinv in natural cell order
+__global__ void k_coarse_matvec_lay(Lay L, const double *__restrict__ pinv, const float *__restrict__ r, float *e) {
+    const int nc = (int)L.n;
+    const int row = (int)(((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nc) return;
+    const double *a = pinv + (i64)row * nc;
+    double s = 0.0;
+    for (int q = lane; q < nc; q += 32) {
+        const int x = q % L.nx, y = (q / L.nx) % L.ny, z = q / (L.nx * L.ny);
+        s += a[q] * (double)r[sto(L, x, y, z)];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const int x = row % L.nx, y = (row / L.nx) % L.ny, z = row / (L.nx * L.ny);
+        e[sto(L, x, y, z)] = (float)s;
+    }
+}
+
+// natural <-> level storage
+__global__ void k_pack(Lay L, const float *__restrict__ nat, float *st) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = nat[t];
+}
+__global__ void k_unpack(Lay L, const float *__restrict__ st, float *nat) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    nat[t] = st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))];
+}
+__global__ void k_pack64(Lay L, const double *__restrict__ nat, float *st) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = (float)nat[t];
+}
+__global__ void k_pack_inv64(Lay L, const double *__restrict__ rho, float *st) {
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n) return;
+    const int x = (int)(t % L.nx);
+    const i64 row = t / L.nx;
+    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = (float)(1.0 / rho[t]);
+}
+
+}  // namespace
+
+Lay make_lay(Dims d) {
+    Lay L;
+    L.nx = d.nx;
+    L.ny = d.ny;
+    L.nz = d.nz;
+    L.n = d.n;
+    L.split = (d.nx % 2 == 0);
+    L.hx = d.nx / 2;
+    L.half = d.n / 2;
+    return L;
+}
+
+void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
+                   const float *fz, const float *b, float *x, int col, bool from_zero) {
+    Coef32 cf{sinv, fx, fy, fz};
+    count_launch();
+    if (L.split && L.hx % 4 == 0) {
+        const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
+        if (sinv) {
+            if (from_zero) k_half_vec<true, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col);
+            else k_half_vec<true, false><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col);
+        } else {
+            if (from_zero) k_half_vec<false, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col);
+            else k_half_vec<false, false><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col);
+        }
+    } else {
+        const i64 work = (i64)L.ny * L.nz * ((L.nx + 1) / 2);
+        k_half_any<<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col, from_zero ? 1 : 0);
+    }
+}
+
+void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
+                       const float *fz, const float *b, const float *x, float *r, bool apply_only) {
+    Coef32 cf{sinv, fx, fy, fz};
+    count_launch();
+    k_residual_any<<<blocks_for(L.n), kThreads, 0, s>>>(L, (float)ih2, cf, b, x, r, apply_only ? 1 : 0);
+}
+
+void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const float *sinv, const float *fx,
+                             const float *fy, const float *fz, const float *b, const float *x, float *bc,
+                             bool red_only) {
+    Coef32 cf{sinv, fx, fy, fz};
+    count_launch();
+    if (red_only && L.split && L.hx % 4 == 0) {
+        const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 4);
+        if (sinv) k_rr_red_vec<true><<<blocks_for(work), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        else k_rr_red_vec<false><<<blocks_for(work), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        return;
+    }
+    k_resid_restrict_any<<<blocks_for(Lc.n), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc, red_only ? 1 : 0);
+}
+
+void launch_prolong32(cudaStream_t s, Lay L, Lay Lc, const float *ec, float *x, int kind, int only_col) {
+    count_launch();
+    if (only_col == 0 && L.split && L.hx % 4 == 0) {
+        const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
+        k_prolong_red_vec<<<blocks_for(work), kThreads, 0, s>>>(L, Lc, ec, x, kind);
+        return;
+    }
+    k_prolong_any<<<blocks_for(L.n), kThreads, 0, s>>>(L, Lc, ec, x, kind, only_col);
+}
+
+void launch_coarse_matvec32(cudaStream_t s, Lay L, const double *pinv, const float *r, float *e) {
+    count_launch();
+    k_coarse_matvec_lay<<<blocks_for(L.n * 32), kThreads, 0, s>>>(L, pinv, r, e);
+}
+
+void launch_pack32(cudaStream_t s, Lay L, const float *nat, float *st) {
+    count_launch();
+    k_pack<<<blocks_for(L.n), kThreads, 0, s>>>(L, nat, st);
+}
+void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat) {
+    count_launch();
+    k_unpack<<<blocks_for(L.n), kThreads, 0, s>>>(L, st, nat);
+}
+void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st) {
+    count_launch();
+    k_pack64<<<blocks_for(L.n), kThreads, 0, s>>>(L, nat, st);
+}
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st) {
+    count_launch();
+    k_pack_inv64<<<blocks_for(L.n), kThreads, 0, s>>>(L, rho, st);
+}
+
+}  // namespace mg

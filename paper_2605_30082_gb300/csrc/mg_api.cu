@@ -25,11 +25,16 @@ namespace {
 
 struct Level {
     Dims d;
+    mg::Lay lay;  // storage of the FP32 arrays of this level
     double h, h2, ih2;
     double *fx64, *fy64, *fz64, *invd64;
-    float *fx32, *fy32, *fz32, *invd32;
-    double *x64, *b64;  // FP64 path, levels >= 1
-    float *x32, *b32;   // MIXED inner cycle, all levels (level 0: e and scaled r)
+    double *d64;            // level 0: sum of the interior face coefficients (FP64 residual)
+    float *fx32, *fy32, *fz32;
+    double *x64, *b64;      // FP64 path: iterate and RHS, levels >= 1
+    float *x32, *b32;       // MIXED inner cycle, all levels (level 0: e and the scaled r)
+    float *s1_32, *s2_32;   // MIXED: scratch of the component entry points, all levels
+    float *s32;             // MIXED, level 0: 1/rho per cell (used when the operator came from rho)
+    // (every FP32 array of a level is stored in that level's layout `lay`)
 };
 
 constexpr int kProfEvents = 8192;
@@ -51,6 +56,7 @@ struct mg_handle {
     void *arena;
     size_t arena_bytes;
     int have_op;
+    int sform0;        // level-0 FP32 kernels use s = 1/rho (operator set from a density)
     cudaEvent_t ev0, ev1;
     // optional per-class timing of level-0 kernels (events recorded around launches)
     int prof_on;
@@ -109,23 +115,6 @@ template <>
 Coef<double> coef<double>(const Level &L) {
     return Coef<double>{L.fx64, L.fy64, L.fz64, L.invd64};
 }
-template <>
-Coef<float> coef<float>(const Level &L) {
-    return Coef<float>{L.fx32, L.fy32, L.fz32, L.invd32};
-}
-template <typename T>
-T *lvl_x(Level &L);
-template <>
-double *lvl_x<double>(Level &L) { return L.x64; }
-template <>
-float *lvl_x<float>(Level &L) { return L.x32; }
-template <typename T>
-T *lvl_b(Level &L);
-template <>
-double *lvl_b<double>(Level &L) { return L.b64; }
-template <>
-float *lvl_b<float>(Level &L) { return L.b32; }
-
 // ---- optional timing of level-0 kernels ------------------------------------------
 void prof_begin(mg_handle *h, int cls) {
     if (!h->prof_on || h->pev_used + 2 > kProfEvents) return;
@@ -151,40 +140,102 @@ void prof_collect(mg_handle *h) {
     h->pev_used = 0;
 }
 
-// ---- the V-cycle --------------------------------------------------------------------
-template <typename T>
-void smooth(mg_handle *h, int l, T *x, const T *b, int sweeps, int order) {
+// ---- FP64 V-cycle: in-place per-colour half sweeps, standalone transfers --------------
+// (FP64 arithmetic, not bytes, bounds these kernels on GB300, so they do no
+// redundant work; see the fused FP32 passes below for the bandwidth-bound cycle)
+void smooth64(mg_handle *h, int l, double *x, const double *b, int sweeps, int order) {
     Level &L = h->lv[l];
-    for (int sw = 0; sw < sweeps; ++sw) {
+    for (int sw = 0; sw < sweeps; ++sw)
         for (int half = 0; half < 2; ++half) {
-            int colour = order ? 1 - half : half;
             if (l == 0) prof_begin(h, MG_PROF_SMOOTH);
-            mg::launch_rbgs_half<T>(h->s, L.d, L.h2, coef<T>(L), b, x, colour);
+            mg::launch_rbgs_half64(h->s, L.d, L.h2, coef<double>(L), b, x, order ? 1 - half : half);
             if (l == 0) prof_end(h);
         }
+}
+
+void presmooth_restrict64(mg_handle *h, int l, const double *b, double *x, double *bc, int sweeps) {
+    Level &L = h->lv[l];
+    smooth64(h, l, x, b, sweeps, 0);
+    if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
+    mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), b, x, bc);
+    if (l == 0) prof_end(h);
+}
+
+void prolong_postsmooth64(mg_handle *h, int l, const double *b, const double *ec, double *x, int sweeps) {
+    if (l == 0) prof_begin(h, MG_PROF_PROLONG);
+    mg::launch_prolong<double>(h->s, h->lv[l + 1].d, ec, x, h->o.prolong);
+    if (l == 0) prof_end(h);
+    smooth64(h, l, x, b, sweeps, 1);
+}
+
+// one V-cycle on level l for A x = b, x in place (x_zero: x starts at zero)
+void vcycle64(mg_handle *h, int l, const double *b, double *x, bool x_zero) {
+    if (l == h->nlev - 1) {
+        if (l == 0) prof_begin(h, MG_PROF_COARSE);
+        mg::launch_coarse_matvec<double>(h->s, h->nc, h->pinv, b, x);
+        if (l == 0) prof_end(h);
+        return;
+    }
+    Level &L = h->lv[l], &C = h->lv[l + 1];
+    if (x_zero) cudaMemsetAsync(x, 0, sizeof(double) * (size_t)L.d.n, h->s);
+    presmooth_restrict64(h, l, b, x, C.b64, h->o.pre);
+    vcycle64(h, l + 1, C.b64, C.x64, true);
+    prolong_postsmooth64(h, l, b, C.x64, x, h->o.post);
+}
+
+// ---- FP32 V-cycle on colour-split levels ------------------------------------------------
+const float *sinv32(mg_handle *h, int l) { return (l == 0 && h->sform0) ? h->lv[0].s32 : nullptr; }
+
+void half32(mg_handle *h, int l, const float *b, float *x, int col, bool from_zero) {
+    Level &L = h->lv[l];
+    if (l == 0) prof_begin(h, MG_PROF_SMOOTH);
+    mg::launch_half32(h->s, L.lay, L.h2, sinv32(h, l), L.fx32, L.fy32, L.fz32, b, x, col, from_zero);
+    if (l == 0) prof_end(h);
+}
+
+// `sweeps` red-black sweeps in place; order 0 red first, 1 black first; from_zero: x = 0 on entry
+void smooth32(mg_handle *h, int l, const float *b, float *x, int sweeps, int order, bool from_zero) {
+    for (int sw = 0; sw < sweeps; ++sw) {
+        half32(h, l, b, x, order ? 1 : 0, from_zero && sw == 0);
+        half32(h, l, b, x, order ? 0 : 1, false);
     }
 }
 
-template <typename T>
-void vcycle(mg_handle *h, int l, const T *b, T *x) {
+// x <- pre-smoothing (from zero if from_zero), bc = R(b - A x)
+void presmooth_restrict32(mg_handle *h, int l, const float *b, float *x, float *bc, int sweeps, bool from_zero) {
+    Level &L = h->lv[l], &C = h->lv[l + 1];
+    if (sweeps == 0 && from_zero) cudaMemsetAsync(x, 0, sizeof(float) * (size_t)L.d.n, h->s);
+    smooth32(h, l, b, x, sweeps, 0, from_zero);
+    if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
+    // after a pre-smoothing sweep (black last) every black residual is zero
+    mg::launch_resid_restrict32(h->s, L.lay, C.lay, L.ih2, sinv32(h, l), L.fx32, L.fy32, L.fz32, b, x, bc,
+                                sweeps > 0);
+    if (l == 0) prof_end(h);
+}
+
+// x <- post-smoothing of x + P ec
+void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, float *x, int sweeps) {
+    Level &L = h->lv[l], &C = h->lv[l + 1];
+    if (l == 0) prof_begin(h, MG_PROF_PROLONG);
+    // the first post sweep (black first) overwrites every black cell: correct the red ones only
+    mg::launch_prolong32(h->s, L.lay, C.lay, ec, x, h->o.prolong, sweeps > 0 ? 0 : -1);
+    if (l == 0) prof_end(h);
+    smooth32(h, l, b, x, sweeps, 1, false);
+}
+
+// one V-cycle on level l for A x = b from x = 0; result in x
+void vcycle32(mg_handle *h, int l, const float *b, float *x) {
     Level &L = h->lv[l];
     if (l == h->nlev - 1) {
         if (l == 0) prof_begin(h, MG_PROF_COARSE);
-        mg::launch_coarse_matvec<T>(h->s, h->nc, h->pinv, b, x);
+        mg::launch_coarse_matvec32(h->s, L.lay, h->pinv, b, x);
         if (l == 0) prof_end(h);
         return;
     }
     Level &C = h->lv[l + 1];
-    smooth<T>(h, l, x, b, h->o.pre, 0);
-    if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
-    mg::launch_resid_restrict<T>(h->s, L.d, L.ih2, coef<T>(L), b, x, lvl_b<T>(C));
-    if (l == 0) prof_end(h);
-    if (l + 1 < h->nlev - 1) cudaMemsetAsync(lvl_x<T>(C), 0, sizeof(T) * (size_t)C.d.n, h->s);
-    vcycle<T>(h, l + 1, lvl_b<T>(C), lvl_x<T>(C));
-    if (l == 0) prof_begin(h, MG_PROF_PROLONG);
-    mg::launch_prolong<T>(h->s, C.d, lvl_x<T>(C), x, h->o.prolong);
-    if (l == 0) prof_end(h);
-    smooth<T>(h, l, x, b, h->o.post, 1);
+    presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, true);
+    vcycle32(h, l + 1, C.b32, C.x32);
+    prolong_postsmooth32(h, l, b, C.x32, x, h->o.post);
 }
 
 // ---- set-up of the operator hierarchy -------------------------------------------------
@@ -197,11 +248,11 @@ int finish_operator(mg_handle *h) {
     bool mixed = h->o.precision == MG_MIXED;
     for (int l = 0; l < h->nlev; ++l) {
         Level &L = h->lv[l];
-        mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, mixed ? L.invd32 : nullptr);
+        mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, l == 0 ? L.d64 : nullptr);
         if (mixed) {
-            mg::launch_to_f32(s, L.d.n, L.fx64, L.fx32);
-            mg::launch_to_f32(s, L.d.n, L.fy64, L.fy32);
-            mg::launch_to_f32(s, L.d.n, L.fz64, L.fz32);
+            mg::launch_pack64to32(s, L.lay, L.fx64, L.fx32);
+            mg::launch_pack64to32(s, L.lay, L.fy64, L.fy32);
+            mg::launch_pack64to32(s, L.lay, L.fz64, L.fz32);
         }
     }
     // dense pseudo-inverse of the coarsest operator
@@ -266,8 +317,8 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         double scale = 1.0 / nb;  // r32 = scale * r (scale = 1 / previous residual norm)
         auto residual = [&](bool write32) -> int {
             prof_begin(h, MG_PROF_FINE_RESIDUAL);
-            mg::launch_fine_residual(s, F.d, F.ih2, F.fx64, F.fy64, F.fz64, h->bt, p,
-                                     write32 ? F.b32 : nullptr, scale, h->partials, h->red + 6);
+            mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, p,
+                                   write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
             prof_end(h);
             MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->red + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
             MG_CUDA(h, cudaStreamSynchronize(s));
@@ -276,7 +327,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         };
         rc = residual(mixed);
         if (rc) return rc;
-        double rn = std::sqrt(h->hred[6]);
+        double rn = std::sqrt(h->hred[6]) * F.ih2;  // the kernel sums (h^2 r)^2
         double mu = h->hred[7] / (double)n;
         rr = rn / nb;
         hist[hist_n++] = rr;
@@ -284,18 +335,17 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         if (rr <= h->o.rtol) status = MG_OK;
         for (int c = 1; c <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++c) {
             if (mixed) {
-                MG_CUDA(h, cudaMemsetAsync(F.x32, 0, sizeof(float) * (size_t)n, s));
-                vcycle<float>(h, 0, F.b32, F.x32);
+                vcycle32(h, 0, F.b32, F.x32);
                 prof_begin(h, MG_PROF_UPDATE);
-                mg::launch_update(s, n, p, F.x32, 1.0 / scale, mu);
+                mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
                 prof_end(h);
                 scale = 1.0 / rn;
             } else {
-                vcycle<double>(h, 0, h->bt, p);
+                vcycle64(h, 0, h->bt, p, false);
             }
             rc = residual(mixed);
             if (rc) return rc;
-            rn = std::sqrt(h->hred[6]);
+            rn = std::sqrt(h->hred[6]) * F.ih2;
             double mu_new = h->hred[7] / (double)n;
             if (!mixed) mg::launch_add_const(s, n, p, -mu_new);  // FP64 path: zero mean each cycle
             mu = mixed ? mu_new : 0.0;
@@ -327,6 +377,14 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         fail(h, status, "not converged: relres %.3e after %d cycles (rtol %.3e)", rr, cycles, h->o.rtol);
     if (status == MG_ERR_DIVERGED) fail(h, status, "diverged: relres %.3e at cycle %d", rr, cycles);
     return status;
+}
+
+// smoothing components need the sweep scratch of the handle's own V-cycle precision
+int check_cycle_dtype(mg_handle *h, int dtype) {
+    if ((dtype == MG_F64) != (h->o.precision == MG_FP64))
+        return fail(h, MG_ERR_ARG, "smoothing components run in the handle's V-cycle precision "
+                                   "(MG_F64 for MG_FP64 handles, MG_F32 for MG_MIXED handles)");
+    return MG_OK;
 }
 
 int check_level(mg_handle *h, int level, int dtype, bool need_coarser) {
@@ -393,6 +451,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
     for (int l = 0; l < nl; ++l) {
         Level &L = h->lv[l];
         L.d = mg::make_dims(o->nx >> l, o->ny >> l, o->nz >> l);
+        L.lay = mg::make_lay(L.d);
         L.h = std::ldexp(o->h, l);
         L.h2 = L.h * L.h;
         L.ih2 = 1.0 / L.h2;
@@ -401,13 +460,16 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         add((void **)&L.fy64, 8 * n);
         add((void **)&L.fz64, 8 * n);
         add((void **)&L.invd64, 8 * n);
+        if (l == 0) add((void **)&L.d64, 8 * n);
         if (mixed) {
             add((void **)&L.fx32, 4 * n);
             add((void **)&L.fy32, 4 * n);
             add((void **)&L.fz32, 4 * n);
-            add((void **)&L.invd32, 4 * n);
             add((void **)&L.x32, 4 * n);
             add((void **)&L.b32, 4 * n);
+            add((void **)&L.s1_32, 4 * n);
+            add((void **)&L.s2_32, 4 * n);
+            if (l == 0) add((void **)&L.s32, 4 * n);
         } else if (l > 0) {
             add((void **)&L.x64, 8 * n);
             add((void **)&L.b64, 8 * n);
@@ -495,6 +557,8 @@ int mg_set_density(mg_handle *h, const double *rho) {
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
     mg::launch_faces_from_rho(h->s, F.d, rho, F.fx64, F.fy64, F.fz64, h->err);
+    h->sform0 = h->o.precision == MG_MIXED;
+    if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, rho, F.s32);
     return finish_operator(h);
 }
 
@@ -505,6 +569,7 @@ int mg_set_face_coeffs(mg_handle *h, const double *bx, const double *by, const d
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
     mg::launch_faces_from_api(h->s, F.d, bx, by, bz, F.fx64, F.fy64, F.fz64, h->err);
+    h->sform0 = 0;
     return finish_operator(h);
 }
 
@@ -579,23 +644,83 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
     return MG_OK;
 }
 
+// FP32 components take natural-layout arrays: they are packed into the level's storage
+// (scratch s1_32, s2_32, x32 of the level), run through the same kernels the V-cycle
+// uses, and unpacked.
 int mg_apply(mg_handle *h, int level, int dtype, const void *x, void *y) {
     int rc = check_level(h, level, dtype, false);
     if (rc) return rc;
     if (!x || !y) return fail(h, MG_ERR_ARG, "mg_apply: null array");
     Level &L = h->lv[level];
-    if (dtype == MG_F64) mg::launch_apply<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)x, (double *)y);
-    else mg::launch_apply<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)x, (float *)y);
+    if (dtype == MG_F64) {
+        mg::launch_apply<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)x, (double *)y);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_residual32(h->s, L.lay, L.ih2, sinv32(h, level), L.fx32, L.fy32, L.fz32, nullptr, L.s1_32,
+                              L.s2_32, true);
+        mg::launch_unpack32(h->s, L.lay, L.s2_32, (float *)y);
+    }
     return check_launch(h, "mg_apply");
 }
 
 int mg_smooth(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps, int order) {
     int rc = check_level(h, level, dtype, false);
     if (rc) return rc;
+    rc = check_cycle_dtype(h, dtype);
+    if (rc) return rc;
     if (!x || !b || sweeps < 0) return fail(h, MG_ERR_ARG, "mg_smooth: bad argument");
-    if (dtype == MG_F64) smooth<double>(h, level, (double *)x, (const double *)b, sweeps, order);
-    else smooth<float>(h, level, (float *)x, (const float *)b, sweeps, order);
+    if (sweeps == 0) return MG_OK;
+    Level &L = h->lv[level];
+    if (dtype == MG_F64) {
+        smooth64(h, level, (double *)x, (const double *)b, sweeps, order ? 1 : 0);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
+        smooth32(h, level, L.s2_32, L.s1_32, sweeps, order ? 1 : 0, false);
+        mg::launch_unpack32(h->s, L.lay, L.s1_32, (float *)x);
+    }
     return check_launch(h, "mg_smooth");
+}
+
+int mg_presmooth_restrict(mg_handle *h, int level, int dtype, void *x, const void *b, int sweeps,
+                          int x_is_zero, void *bc) {
+    int rc = check_level(h, level, dtype, true);
+    if (rc) return rc;
+    rc = check_cycle_dtype(h, dtype);
+    if (rc) return rc;
+    if (!x || !b || !bc || sweeps < 0) return fail(h, MG_ERR_ARG, "mg_presmooth_restrict: bad argument");
+    Level &L = h->lv[level], &C = h->lv[level + 1];
+    if (dtype == MG_F64) {
+        if (x_is_zero) MG_CUDA(h, cudaMemsetAsync(x, 0, 8 * (size_t)L.d.n, h->s));
+        presmooth_restrict64(h, level, (const double *)b, (double *)x, (double *)bc, sweeps);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
+        if (!x_is_zero) mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        presmooth_restrict32(h, level, L.s2_32, L.s1_32, C.s2_32, sweeps, x_is_zero != 0);
+        mg::launch_unpack32(h->s, L.lay, L.s1_32, (float *)x);
+        mg::launch_unpack32(h->s, C.lay, C.s2_32, (float *)bc);
+    }
+    return check_launch(h, "mg_presmooth_restrict");
+}
+
+int mg_prolong_postsmooth(mg_handle *h, int level, int dtype, const void *ec, void *x, const void *b,
+                          int sweeps) {
+    int rc = check_level(h, level, dtype, true);
+    if (rc) return rc;
+    rc = check_cycle_dtype(h, dtype);
+    if (rc) return rc;
+    if (!x || !b || !ec || sweeps < 0) return fail(h, MG_ERR_ARG, "mg_prolong_postsmooth: bad argument");
+    Level &L = h->lv[level], &C = h->lv[level + 1];
+    if (dtype == MG_F64) {
+        prolong_postsmooth64(h, level, (const double *)b, (const double *)ec, (double *)x, sweeps);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
+        mg::launch_pack32(h->s, C.lay, (const float *)ec, C.s1_32);
+        prolong_postsmooth32(h, level, L.s2_32, C.s1_32, L.s1_32, sweeps);
+        mg::launch_unpack32(h->s, L.lay, L.s1_32, (float *)x);
+    }
+    return check_launch(h, "mg_prolong_postsmooth");
 }
 
 int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b, void *r,
@@ -608,7 +733,11 @@ int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b
         mg::launch_residual<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x, (double *)r);
         if (norm2) mg::launch_sum_sumsq<double>(h->s, L.d.n, (const double *)r, h->partials, h->red + 10);
     } else {
-        mg::launch_residual<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)b, (const float *)x, (float *)r);
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
+        mg::launch_residual32(h->s, L.lay, L.ih2, sinv32(h, level), L.fx32, L.fy32, L.fz32, L.s2_32, L.s1_32,
+                              L.x32, false);
+        mg::launch_unpack32(h->s, L.lay, L.x32, (float *)r);
         if (norm2) mg::launch_sum_sumsq<float>(h->s, L.d.n, (const float *)r, h->partials, h->red + 10);
     }
     rc = check_launch(h, "mg_residual");
@@ -625,11 +754,17 @@ int mg_residual_restrict(mg_handle *h, int level, int dtype, const void *x, cons
     int rc = check_level(h, level, dtype, true);
     if (rc) return rc;
     if (!x || !b || !bc) return fail(h, MG_ERR_ARG, "mg_residual_restrict: null array");
-    Level &L = h->lv[level];
-    if (dtype == MG_F64)
-        mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x, (double *)bc);
-    else
-        mg::launch_resid_restrict<float>(h->s, L.d, L.ih2, coef<float>(L), (const float *)b, (const float *)x, (float *)bc);
+    Level &L = h->lv[level], &C = h->lv[level + 1];
+    if (dtype == MG_F64) {
+        mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x,
+                                          (double *)bc);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
+        mg::launch_resid_restrict32(h->s, L.lay, C.lay, L.ih2, sinv32(h, level), L.fx32, L.fy32, L.fz32, L.s2_32,
+                                    L.s1_32, C.s2_32, false);
+        mg::launch_unpack32(h->s, C.lay, C.s2_32, (float *)bc);
+    }
     return check_launch(h, "mg_residual_restrict");
 }
 
@@ -637,9 +772,15 @@ int mg_prolong_correct(mg_handle *h, int level, int dtype, const void *ec, void 
     int rc = check_level(h, level, dtype, true);
     if (rc) return rc;
     if (!ec || !x) return fail(h, MG_ERR_ARG, "mg_prolong_correct: null array");
-    Level &C = h->lv[level + 1];
-    if (dtype == MG_F64) mg::launch_prolong<double>(h->s, C.d, (const double *)ec, (double *)x, h->o.prolong);
-    else mg::launch_prolong<float>(h->s, C.d, (const float *)ec, (float *)x, h->o.prolong);
+    Level &L = h->lv[level], &C = h->lv[level + 1];
+    if (dtype == MG_F64) {
+        mg::launch_prolong<double>(h->s, C.d, (const double *)ec, (double *)x, h->o.prolong);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
+        mg::launch_pack32(h->s, C.lay, (const float *)ec, C.s1_32);
+        mg::launch_prolong32(h->s, L.lay, C.lay, C.s1_32, L.s1_32, h->o.prolong, -1);
+        mg::launch_unpack32(h->s, L.lay, L.s1_32, (float *)x);
+    }
     return check_launch(h, "mg_prolong_correct");
 }
 
@@ -647,8 +788,14 @@ int mg_coarse_solve(mg_handle *h, int dtype, const void *r, void *e) {
     int rc = check_level(h, h ? h->nlev - 1 : 0, dtype, false);
     if (rc) return rc;
     if (!r || !e) return fail(h, MG_ERR_ARG, "mg_coarse_solve: null array");
-    if (dtype == MG_F64) mg::launch_coarse_matvec<double>(h->s, h->nc, h->pinv, (const double *)r, (double *)e);
-    else mg::launch_coarse_matvec<float>(h->s, h->nc, h->pinv, (const float *)r, (float *)e);
+    Level &L = h->lv[h->nlev - 1];
+    if (dtype == MG_F64) {
+        mg::launch_coarse_matvec<double>(h->s, h->nc, h->pinv, (const double *)r, (double *)e);
+    } else {
+        mg::launch_pack32(h->s, L.lay, (const float *)r, L.s1_32);
+        mg::launch_coarse_matvec32(h->s, L.lay, h->pinv, L.s1_32, L.s2_32);
+        mg::launch_unpack32(h->s, L.lay, L.s2_32, (float *)e);
+    }
     return check_launch(h, "mg_coarse_solve");
 }
 

@@ -32,10 +32,21 @@ inline Dims make_dims(int nx, int ny, int nz) {
     return d;
 }
 
+// Storage layout of an FP32 level: colour-split (all red cells, then all black, each
+// colour row by row, cell x of a row at k = x >> 1) when nx is even, else natural.
+struct Lay {
+    int nx, ny, nz;
+    i64 n;
+    bool split;
+    int hx;     // nx / 2
+    i64 half;   // n / 2
+};
+Lay make_lay(Dims d);
+
 template <typename T>
 struct Coef {
     const T *fx, *fy, *fz;  // low-face coefficients
-    const T *invd;          // 1 / sum of the cell's interior face coefficients
+    const T *invd;          // 1 / sum of the cell's interior face coefficients (FP64 only)
 };
 
 // process-wide count of kernel launches (read through mg_kernel_launches)
@@ -54,11 +65,13 @@ void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const doubl
                            const double *bz, double *fx, double *fy, double *fz, unsigned *err);
 void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double *fy,
                          const double *fz, double *bx, double *by, double *bz);
+// 1 / sum of the interior face coefficients of each cell, and (diag non-null) the sum itself
 void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
-                    double *invd64, float *invd32);
+                    double *invd64, double *diag);
 void launch_coarsen(cudaStream_t s, Dims fine, const double *ffx, const double *ffy,
                     const double *ffz, double *cfx, double *cfy, double *cfz);
 void launch_to_f32(cudaStream_t s, i64 n, const double *src, float *dst);
+
 void launch_csf_faces(cudaStream_t s, Dims d, double h, const double *f, const double *kappa,
                       double *cx, double *cy, double *cz);
 void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double *ux, const double *uy,
@@ -72,8 +85,28 @@ void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mo
 void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 
 // ---- V-cycle kernels --------------------------------------------------------------
-template <typename T>
-void launch_rbgs_half(cudaStream_t s, Dims d, double h2, Coef<T> c, const T *b, T *p, int colour);
+// ---- FP32 colour-split level kernels (kernels_split.cu) ----
+// half sweep of colour col in place; sinv = 1/rho per cell (beta = (s_L + s_R)/2) when
+// non-null, else the low-face arrays; from_zero: the other colour is taken as zero
+void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
+                   const float *fz, const float *b, float *x, int col, bool from_zero);
+// r = b - A x (or r = A x when apply_only)
+void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
+                       const float *fz, const float *b, const float *x, float *r, bool apply_only);
+// bc = mean of the 8 children's residuals (red_only: black children count as 0)
+void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const float *sinv, const float *fx,
+                             const float *fy, const float *fz, const float *b, const float *x, float *bc,
+                             bool red_only);
+// x += P ec on the cells of colour only_col (0 red, 1 black) or all cells (-1)
+void launch_prolong32(cudaStream_t s, Lay L, Lay Lc, const float *ec, float *x, int kind, int only_col);
+void launch_coarse_matvec32(cudaStream_t s, Lay L, const double *pinv, const float *r, float *e);
+void launch_pack32(cudaStream_t s, Lay L, const float *nat, float *st);
+void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat);
+void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st);
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st);
+// FP64 red-black half sweep of one colour, in place
+void launch_rbgs_half64(cudaStream_t s, Dims d, double h2, Coef<double> c, const double *b, double *p,
+                        int colour);
 template <typename T>
 void launch_apply(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *x, T *y);
 template <typename T>
@@ -94,11 +127,17 @@ void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, doubl
 void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
                      double *partials, double *out);
 // fine FP64 residual r = b - A p: out[0] = sum r^2, out[1] = sum p; optional r32 = scale * r
-void launch_fine_residual(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
+// stored in the level-0 FP32 layout L
+void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const double *fx, const double *fy,
                           const double *fz, const double *b, const double *p, float *r32,
                           double scale, double *partials, double *out);
-// p = p - shift + alpha * e32   (shift a host scalar)
-void launch_update(cudaStream_t s, i64 n, double *p, const float *e32, double alpha, double shift);
+// fine FP64 residual in diagonal form, h^2 r = h^2 b - (diag p_c - sum_f beta_f p_nb):
+// out[0] = sum (h^2 r)^2, out[1] = sum p; optional r32 = s32 * h^2 r in the level-0 layout L
+void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
+                        const double *fz, const double *diag, const double *b, const double *p, float *r32,
+                        float s32, double *partials, double *out);
+// p = p - shift + alpha * e32 (e32 in the level-0 FP32 layout L; shift a host scalar)
+void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift);
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c);
 void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, const double *p,
                          const double *fx, const double *fy, const double *fz, const double *csfx,

@@ -23,12 +23,20 @@ DIMS = [(72, 40, 24), (40, 24, 56), (32, 32, 32)]
 TOL = {torch.float64: 1e-13, torch.float32: 2e-6}
 
 
-def make(dims, precision, seed=3, prolong="trilinear", coarsest=4):
+def make(dims, precision, seed=3, prolong="trilinear", coarsest=4, coeffs="rho"):
+    """A solver and the oracle hierarchy on the same random density.
+
+    coeffs="rho" loads the operator with mg_set_density (the finest FP32 level then
+    sweeps with s = 1/rho per cell); "faces" loads the same coefficients with
+    mg_set_face_coeffs (the finest FP32 level sweeps with the three face arrays)."""
     nx, ny, nz = dims
     h = 1.0 / 64
     s = Solver(dims, h=h, precision=precision, coarsest=coarsest, prolong=prolong)
     rho = random_rho(dims, seed)
-    s.set_density(dev(rho))
+    if coeffs == "rho":
+        s.set_density(dev(rho))
+    else:
+        s.set_face_coeffs(*(dev(f) for f in O.faces_from_density(rho)))
     M = O.Multigrid(O.faces_from_density(rho), h, coarsest=coarsest,
                     prolong=O.TRILINEAR if prolong == "trilinear" else O.CONSTANT)
     return s, M
@@ -88,9 +96,9 @@ def test_csf_faces_and_rhs_match_oracle():
 
 
 @pytest.mark.parametrize("dims", DIMS)
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_apply_smooth_residual_match_oracle(dims, dtype):
-    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed")
+@pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
+def test_apply_smooth_residual_match_oracle(dims, dtype, coeffs):
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed", coeffs=coeffs)
     tol = TOL[dtype]
     for l in range(M.nlevels):
         nx, ny, nz = M.level_dims(l)
@@ -196,3 +204,63 @@ def test_density_errors_are_reported_not_faulted():
     rho[3, 4, 5] = 2.0
     s.set_density(dev(rho))  # recovers
     s.solve(dev(rnd((n, n, n), 1)))
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
+@pytest.mark.parametrize("sweeps,zero", [(0, False), (1, True), (2, True), (2, False), (3, False)])
+def test_fused_presmooth_restrict_matches_oracle(dims, dtype, coeffs, sweeps, zero):
+    """The V-cycle's downward step as one fused pass chain: sweeps + residual + 8:1 restriction."""
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed", coeffs=coeffs)
+    tol = TOL[dtype]
+    npd = np.float32 if dtype == torch.float32 else np.float64
+    for l in range(M.nlevels - 1):
+        nx, ny, nz = M.level_dims(l)
+        cx, cy, cz = M.level_dims(l + 1)
+        H = s.h * 2**l
+        faces = M.level_faces(l)
+        if dtype == torch.float32:
+            faces = tuple(f.astype(np.float32).astype(np.float64) for f in faces)
+        x = np.zeros((nz, ny, nx), npd) if zero else rnd((nz, ny, nx), 80 + l).astype(npd)
+        b = rnd((nz, ny, nx), 90 + l).astype(npd)
+        xg = dev(x, dtype) if not zero else torch.full((nz, ny, nx), 123.0, dtype=dtype, device="cuda")
+        bc = torch.empty((cz, cy, cx), dtype=dtype, device="cuda")
+        assert L.mg_presmooth_restrict(s._h, l, xg, dev(b, dtype), sweeps, bc, x_is_zero=zero) == 0
+        xs = O.rbgs(faces, b, x, H, sweeps, 0)
+        assert rel(host(xg), xs) < tol if sweeps else np.array_equal(host(xg), x)
+        # restriction of the residual of the returned x
+        bc_from_x = O.restrict(O.residual(faces, b, host(xg), H))
+        assert rel(host(bc), bc_from_x) < (1e-13 if dtype == torch.float64 else 1e-5)
+        assert rel(host(bc), O.restrict(O.residual(faces, b, xs, H))) < (1e-12 if dtype == torch.float64 else 2e-5)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
+@pytest.mark.parametrize("prolong", ["trilinear", "constant"])
+@pytest.mark.parametrize("sweeps", [0, 1, 2, 3])
+def test_fused_prolong_postsmooth_matches_oracle(dims, dtype, coeffs, prolong, sweeps):
+    """The V-cycle's upward step: correction x + P ec then post sweeps (black first), fused."""
+    s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed", prolong=prolong, coeffs=coeffs)
+    tol = TOL[dtype]
+    kind = O.TRILINEAR if prolong == "trilinear" else O.CONSTANT
+    npd = np.float32 if dtype == torch.float32 else np.float64
+    for l in range(M.nlevels - 1):
+        nx, ny, nz = M.level_dims(l)
+        cx, cy, cz = M.level_dims(l + 1)
+        H = s.h * 2**l
+        faces = M.level_faces(l)
+        if dtype == torch.float32:
+            faces = tuple(f.astype(np.float32).astype(np.float64) for f in faces)
+        x = rnd((nz, ny, nx), 100 + l).astype(npd)
+        b = rnd((nz, ny, nx), 110 + l).astype(npd)
+        ec = rnd((cz, cy, cx), 120 + l).astype(npd)
+        xg = dev(x, dtype)
+        assert L.mg_prolong_postsmooth(s._h, l, dev(ec, dtype), xg, dev(b, dtype), sweeps) == 0
+        want = O.rbgs(faces, b, O.prolong_correct(ec, x, kind), H, sweeps, 1)
+        assert rel(host(xg), want) < tol
+
+
+def test_smoothing_components_need_the_cycle_precision():
+    s, _ = make((16, 16, 16), "mixed")
+    x = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda")
+    assert L.mg_smooth(s._h, 0, x, x.clone(), 1) == L.MG_ERR_ARG
