@@ -30,8 +30,17 @@ if ROOT not in sys.path:
 
 METRIC = "time-to-1e-10 residual & fine-grid GLUP/s at 512^3, FP64 vs mixed; HBM GB/s"
 RHO_PHASE = (998.0, 880.0, 1.2)
-# FP32 bytes a fused red-black sweep must move per cell: read x, b, 3 face coefficients, write x
-SWEEP_BYTES_PER_CELL_FP32 = 24
+# Algorithmic bytes per grid cell of the finest-level FP32 half sweep (colour-split storage,
+# coefficients s = 1/rho): read the other colour's x (2), s of both colours (4), this colour's
+# b (2), write this colour's x (2); the first pre-smoothing half sweep starts from x = 0 (8).
+HALF_BYTES, HALF_ZERO_BYTES = 10, 8
+# finest-level half sweeps per V(2,2) timed in the SMOOTH class: 1 from zero + 6 (the 8th is
+# fused with the outer update)
+HALF_PER_CYCLE = 7
+# FP64 outer residual: 7 fused multiply-adds per cell; GB300 nominal FP64 rate (NVIDIA B300
+# specification: 1.25 TFLOP/s; no FP64 figure is in MEASURED_PEAKS.json)
+RESID_FMA_PER_CELL = 7
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -245,17 +254,28 @@ def run_ours(args):
         t_fp64, cyc_fp64 = time_solve(s64)
         s64.close()
 
-    # ---- roofline of the dominant kernel (finest-level FP32 smoother)
+    # ---- rooflines: finest-level FP32 half sweep (HBM) and FP64 outer residual (FP64 ALU)
+    cells = n**3
     n_sm, ms_sm = prof["smooth"]
     avg_sm = ms_sm / max(n_sm, 1)
-    cells = n**3
-    sweeps_per_launch = 0.5  # one colour per launch (half sweep)
-    alg_bytes = 20 * cells  # half sweep: other-colour x, own b and x write, all faces (see design notes)
+    ncyc_sm = n_sm / HALF_PER_CYCLE
+    bytes_sm = ncyc_sm * (HALF_ZERO_BYTES + (HALF_PER_CYCLE - 1) * HALF_BYTES) * cells
     peak = _measured_peak_hbm()
-    achieved = alg_bytes / (avg_sm * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 3), "traffic": _traffic_from_profiles("rbgs_half", cells),
-                "kernel": "k_rbgs_half<float> (finest level)", "launch_ms": round(avg_sm, 4)}
+    gbs_sm = bytes_sm / (ms_sm * 1e-3) / 1e9
+    roof_sm = {"bound": "hbm", "achieved": round(gbs_sm, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(gbs_sm / peak, 3),
+               "traffic": _traffic_from_profiles("k_half_vec", cells),
+               "kernel": "k_half_vec<sform> (finest-level FP32 red-black half sweep)",
+               "launch_ms": round(avg_sm, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    n_fr, ms_fr = prof["fine_residual"]
+    avg_fr = ms_fr / max(n_fr, 1)
+    tf_fr = 2 * RESID_FMA_PER_CELL * cells / (avg_fr * 1e-3) / 1e12
+    roof_fr = {"bound": "alu", "achieved": round(tf_fr, 3), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+               "frac": round(tf_fr / FP64_PEAK_TFLOPS, 3),
+               "traffic": _traffic_from_profiles("k_fine_resid_pair", cells),
+               "kernel": "k_fine_resid_pair (FP64 outer residual)", "launch_ms": round(avg_fr, 4),
+               "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak available)"}
+    roofline = roof_sm if ms_sm >= ms_fr else roof_fr
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -290,7 +310,9 @@ def run_ours(args):
             "speedup_mixed_vs_fp64": None if t_fp64 is None else round(t_fp64 / t_mixed, 3),
             "adjoint_over_forward": round(stats["adj"][2] / stats["fwd"][2], 3),
             "solve_glups_mixed": round(cells * cyc_mixed / (t_mixed * 1e-3) / 1e9, 3),
-            "smoother_glups": round(cells * sweeps_per_launch / (avg_sm * 1e-3) / 1e9, 3),
+            "smoother_glups": round(cells * (n_sm / 2) / (ms_sm * 1e-3) / 1e9, 3),
+            "roofline_smoother": roof_sm,
+            "roofline_fp64_residual": roof_fr,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
             "kernel_launches_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         },

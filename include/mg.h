@@ -40,7 +40,9 @@
  *   - Array arguments are DEVICE pointers (CUDA global memory of the device the
  *     handle was created on), owned by the caller, contiguous, in the layouts
  *     above; the library keeps no reference to them after the call returns.
- *     Unless a parameter says otherwise they are double (FP64).
+ *     Unless a parameter says otherwise they are double (FP64).  The solution
+ *     arrays of mg_solve (p) and mg_adjoint (lam) must be 16-byte aligned (any
+ *     cudaMalloc or torch allocation is); MG_ERR_ARG otherwise.
  *   - Work is queued on the CUDA stream given to mg_create.  Entry points that
  *     need a scalar result on the host (mg_solve, mg_adjoint, the norm outputs)
  *     synchronise that stream; the others return once the work is queued.

@@ -94,10 +94,11 @@ __global__ void k_residual(Dims d, T ih2, Coef<T> cf, const T *__restrict__ b,
     r[c] = b[c] - flux_sum(d, i, j, k, c, cf, x) * ih2;
 }
 
-// one thread per coarse cell: mean of the residuals of its 8 children
+// one thread per coarse cell: mean of the residuals of its 8 children; red_only: the black
+// children count as 0 (exact after a black half sweep, which solves every black row)
 template <typename T>
 __global__ void k_resid_restrict(Dims f, Dims cd, T ih2, Coef<T> cf, const T *__restrict__ b,
-                                 const T *__restrict__ x, T *bc) {
+                                 const T *__restrict__ x, T *bc, int red_only) {
     i64 C = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (C >= cd.n) return;
     int I, J, K;
@@ -107,18 +108,21 @@ __global__ void k_resid_restrict(Dims f, Dims cd, T ih2, Coef<T> cf, const T *__
         for (int bb = 0; bb < 2; ++bb)
             for (int aa = 0; aa < 2; ++aa) {
                 int i = 2 * I + aa, j = 2 * J + bb, k = 2 * K + cc;
+                if (red_only && ((i + j + k) & 1)) continue;
                 i64 c = ((i64)k * f.ny + j) * f.nx + i;
                 s += b[c] - flux_sum(f, i, j, k, c, cf, x) * ih2;
             }
     bc[C] = s / T(8);
 }
 
+// e += P ec on the cells of colour only_col (0 red, 1 black) or on all cells (-1)
 template <typename T>
-__global__ void k_prolong(Dims cd, Dims f, const T *__restrict__ ec, T *e, int kind) {
+__global__ void k_prolong(Dims cd, Dims f, const T *__restrict__ ec, T *e, int kind, int only_col) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= f.n) return;
     int i, j, k;
     cell_ijk(f, c, i, j, k);
+    if (only_col >= 0 && ((i + j + k) & 1) != only_col) return;
     int I = i >> 1, J = j >> 1, K = k >> 1;
     T v;
     if (kind == MG_PROLONG_CONSTANT) {
@@ -182,17 +186,17 @@ void launch_residual(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *b, 
 
 template <typename T>
 void launch_resid_restrict(cudaStream_t s, Dims fine, double ih2, Coef<T> c, const T *b,
-                           const T *x, T *bc) {
+                           const T *x, T *bc, bool red_only) {
     Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
     count_launch();
-    k_resid_restrict<T><<<blocks_for(cd.n), kThreads, 0, s>>>(fine, cd, (T)ih2, c, b, x, bc);
+    k_resid_restrict<T><<<blocks_for(cd.n), kThreads, 0, s>>>(fine, cd, (T)ih2, c, b, x, bc, red_only ? 1 : 0);
 }
 
 template <typename T>
-void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind) {
+void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind, int only_col) {
     Dims f = make_dims(coarse.nx * 2, coarse.ny * 2, coarse.nz * 2);
     count_launch();
-    k_prolong<T><<<blocks_for(f.n), kThreads, 0, s>>>(coarse, f, ec, e, kind);
+    k_prolong<T><<<blocks_for(f.n), kThreads, 0, s>>>(coarse, f, ec, e, kind, only_col);
 }
 
 template <typename T>
@@ -207,8 +211,8 @@ void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r
     template void launch_residual<T>(cudaStream_t, Dims, double, Coef<T>, const T *, const T *,  \
                                      T *);                                                       \
     template void launch_resid_restrict<T>(cudaStream_t, Dims, double, Coef<T>, const T *,       \
-                                           const T *, T *);                                      \
-    template void launch_prolong<T>(cudaStream_t, Dims, const T *, T *, int);                    \
+                                           const T *, T *, bool);                                \
+    template void launch_prolong<T>(cudaStream_t, Dims, const T *, T *, int, int);               \
     template void launch_coarse_matvec<T>(cudaStream_t, int, const double *, const T *, T *);
 
 MG_INSTANTIATE(double)

@@ -78,12 +78,13 @@ __global__ void k_sum_sumsq(i64 n, const T *__restrict__ x, double *partials) {
     block_sum2(a, b, partials + 2 * blockIdx.x);
 }
 
+// b64 = (b - mean(b)) * scale; partials: sum of b64^2
 __global__ void k_sub_mean(i64 n, const double *__restrict__ b, const double *__restrict__ sum,
-                           double *b64, double *partials) {
+                           double scale, double *b64, double *partials) {
     double mean = sum[0] / (double)n;
     double q = 0.0;
     for (i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (i64)gridDim.x * blockDim.x) {
-        double v = b[m] - mean;
+        double v = (b[m] - mean) * scale;
         b64[m] = v;
         q += v * v;
     }
@@ -125,14 +126,83 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
 }
 
-// h^2 r = h^2 b - (d p_c - sum_f beta_f p_nb), d = sum_f beta_f (8 FP64 operations per cell);
-// partials: (sum (h^2 r)^2 accumulated in FP32 per thread, sum p in FP64); r32 = s32 * h^2 r
-__global__ void k_fine_resid2(Dims d, Lay L, double h2, const double *__restrict__ fx,
-                              const double *__restrict__ fy, const double *__restrict__ fz,
-                              const double *__restrict__ dg, const double *__restrict__ b,
-                              const double *__restrict__ p, float *r32, float s32, double *partials) {
-    float q = 0.f;
-    double sp = 0.0;
+// h^2 r = h^2 b - (d p_c - sum_f beta_f p_nb), d = sum_f beta_f: 7 FP64 fused multiply-adds
+// per cell when b arrives already scaled by h^2 (SCALED), one more multiply otherwise.
+// partials: (sum (h^2 r)^2 and sum p, each accumulated in FP32 per thread); r32 = s32 * h^2 r.
+// The FP32 sum of p only steers the per-iteration gauge shift; the exit gauge is exact.
+// One thread handles the cell pair x = 2k, 2k+1 of a row (even nx): aligned double2 loads,
+// and the pair's red and black r32 values land at index k of the two colour halves.
+template <bool SCALED>
+__global__ void k_fine_resid_pair(Dims d, Lay L, double h2, const double *__restrict__ fx,
+                                  const double *__restrict__ fy, const double *__restrict__ fz,
+                                  const double *__restrict__ dg, const double *__restrict__ b,
+                                  const double *__restrict__ p, float *r32, float s32, double *partials) {
+    float q = 0.f, sp = 0.f;
+    const int nx = d.nx, ny = d.ny, nz = d.nz, hx = nx >> 1;
+    const int nxy = nx * ny;
+    const int npairs = (int)(d.n >> 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npairs; t += gridDim.x * blockDim.x) {
+        const int row = t / hx, k = t - row * hx;
+        const int j = row % ny, z = row / ny;
+        const int c = row * nx + 2 * k;  // cells c (x = 2k) and c + 1
+        const double2 pc = *reinterpret_cast<const double2 *>(p + c);
+        const double2 bb = *reinterpret_cast<const double2 *>(b + c);
+        const double2 fxa = *reinterpret_cast<const double2 *>(fx + c);   // low x faces of both cells
+        const double2 fya = *reinterpret_cast<const double2 *>(fy + c);
+        const double2 fza = *reinterpret_cast<const double2 *>(fz + c);
+        const double2 dd = *reinterpret_cast<const double2 *>(dg + c);
+        double a0 = SCALED ? bb.x : h2 * bb.x;
+        double a1 = SCALED ? bb.y : h2 * bb.y;
+        // x faces: cell 0 low (x-1), shared face (between the pair), cell 1 high (x+2)
+        if (k > 0) a0 = fma(fxa.x, p[c - 1], a0);
+        a0 = fma(fxa.y, pc.y, a0);
+        a1 = fma(fxa.y, pc.x, a1);
+        if (k < hx - 1) a1 = fma(fx[c + 2], p[c + 2], a1);
+        if (j > 0) {
+            const double2 pm = *reinterpret_cast<const double2 *>(p + c - nx);
+            a0 = fma(fya.x, pm.x, a0);
+            a1 = fma(fya.y, pm.y, a1);
+        }
+        if (j < ny - 1) {
+            const double2 f = *reinterpret_cast<const double2 *>(fy + c + nx);
+            const double2 pp = *reinterpret_cast<const double2 *>(p + c + nx);
+            a0 = fma(f.x, pp.x, a0);
+            a1 = fma(f.y, pp.y, a1);
+        }
+        if (z > 0) {
+            const double2 pm = *reinterpret_cast<const double2 *>(p + c - nxy);
+            a0 = fma(fza.x, pm.x, a0);
+            a1 = fma(fza.y, pm.y, a1);
+        }
+        if (z < nz - 1) {
+            const double2 f = *reinterpret_cast<const double2 *>(fz + c + nxy);
+            const double2 pp = *reinterpret_cast<const double2 *>(p + c + nxy);
+            a0 = fma(f.x, pp.x, a0);
+            a1 = fma(f.y, pp.y, a1);
+        }
+        a0 = fma(-dd.x, pc.x, a0);
+        a1 = fma(-dd.y, pc.y, a1);
+        const float r0 = d2f_trunc(a0), r1 = d2f_trunc(a1);
+        if (r32) {
+            const int par = (j + z) & 1;  // colour of cell x = 2k
+            const i64 base = (i64)row * hx + k;
+            r32[par * L.half + base] = r0 * s32;
+            r32[(1 - par) * L.half + base] = r1 * s32;
+        }
+        q = fmaf(r0, r0, q);
+        q = fmaf(r1, r1, q);
+        sp += d2f_trunc(pc.x) + d2f_trunc(pc.y);
+    }
+    block_sum2((double)q, (double)sp, partials + 2 * blockIdx.x);
+}
+
+// the same residual, one thread per cell (any nx; used when nx is odd)
+template <bool SCALED>
+__global__ void k_fine_resid_cell(Dims d, Lay L, double h2, const double *__restrict__ fx,
+                                  const double *__restrict__ fy, const double *__restrict__ fz,
+                                  const double *__restrict__ dg, const double *__restrict__ b,
+                                  const double *__restrict__ p, float *r32, float s32, double *partials) {
+    float q = 0.f, sp = 0.f;
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const i64 nxy = d.nxy;
     for (i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x; c < d.n; c += (i64)gridDim.x * blockDim.x) {
@@ -140,7 +210,7 @@ __global__ void k_fine_resid2(Dims d, Lay L, double h2, const double *__restrict
         const i64 row = c / nx;
         const int j = (int)(row % ny), k = (int)(row / ny);
         const double pc = p[c];
-        double acc = h2 * b[c];
+        double acc = SCALED ? b[c] : h2 * b[c];
         if (i > 0) acc = fma(fx[c], p[c - 1], acc);
         if (i < nx - 1) acc = fma(fx[c + 1], p[c + 1], acc);
         if (j > 0) acc = fma(fy[c], p[c - nx], acc);
@@ -151,9 +221,9 @@ __global__ void k_fine_resid2(Dims d, Lay L, double h2, const double *__restrict
         const float rf = d2f_trunc(acc);
         if (r32) r32[sto(L, i, j, k)] = rf * s32;
         q = fmaf(rf, rf, q);
-        sp += pc;
+        sp += d2f_trunc(pc);
     }
-    block_sum2((double)q, sp, partials + 2 * blockIdx.x);
+    block_sum2((double)q, (double)sp, partials + 2 * blockIdx.x);
 }
 
 // r = b - ih2 * sum_f beta_f (p_c - p_nb); partials: (sum r^2, sum p)
@@ -262,11 +332,11 @@ void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, doubl
 template void launch_sum_sumsq<double>(cudaStream_t, i64, const double *, double *, double *);
 template void launch_sum_sumsq<float>(cudaStream_t, i64, const float *, double *, double *);
 
-void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
+void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double scale, double *b64,
                      double *partials, double *out) {
     int nb = reduce_blocks(n);
     count_launch();
-    k_sub_mean<<<nb, kReduceThreads, 0, s>>>(n, b, sum, b64, partials);
+    k_sub_mean<<<nb, kReduceThreads, 0, s>>>(n, b, sum, scale, b64, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
@@ -282,11 +352,21 @@ void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const doubl
 }
 
 void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
-                        const double *fz, const double *diag, const double *b, const double *p, float *r32,
-                        float s32, double *partials, double *out) {
-    int nb = reduce_blocks(d.n);
+                        const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
+                        float *r32, float s32, double *partials, double *out) {
+    if (d.nx & 1) {
+        int nb = reduce_blocks(d.n);
+        count_launch();
+        if (b_scaled) k_fine_resid_cell<true><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+        else k_fine_resid_cell<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+        count_launch();
+        k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+        return;
+    }
+    int nb = reduce_blocks(d.n / 2);
     count_launch();
-    k_fine_resid2<<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    if (b_scaled) k_fine_resid_pair<true><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    else k_fine_resid_pair<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }

@@ -99,10 +99,33 @@ __global__ void k_half_any(Lay L, float h2, Coef32 cf, const float *__restrict__
     xv[sto(L, x, y, z)] = __fdividef(hh * b[sto(L, x, y, z)] + num, den);
 }
 
+// FP32 -> FP64 exactly with integer operations (FP32 subnormals become zero); keeps the
+// widening off GB300's low-rate FP64 pipe (binary32: 1 sign, 8 exponent (bias 127), 23
+// fraction bits; binary64: 1, 11 (bias 1023), 52)
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned ed = (e == 0xffu) ? 0x7ffu : (e - 127u + 1023u);
+    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+struct Upd {
+    double *p;      // natural FP64 solution of the finest level
+    double alpha;   // scale of the correction
+    double shift;   // gauge shift
+};
+
 // ---- vectorised half sweep on split levels (hx % 4 == 0) ---------------------------------
-// one thread updates 4 consecutive cells (k0..k0+3) of colour col in one row
-template <bool SFORM, bool FROM_ZERO>
-__global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col) {
+// one thread updates 4 consecutive cells (k0..k0+3) of colour col in one row.
+// UPDATE (last red half sweep of the finest level): instead of storing the 4 new red values,
+// add alpha * x - shift for them and for the 4 black values of the same row positions --
+// together the 8 consecutive cells x = 2 k0 .. 2 k0 + 7 -- to the FP64 solution.
+template <bool SFORM, bool FROM_ZERO, bool UPDATE = false>
+__global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col,
+                           Upd up = Upd{}) {
     const int hx = L.hx, kv = hx >> 2;
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 rows = (i64)L.ny * L.nz;
@@ -194,7 +217,22 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
         const float den = ((w0[v] + w1[v]) + (w2[v] + w3[v])) + (w4[v] + w5[v]);
         out[v] = __fdividef(hh * bb[v] + num, den);
     }
-    *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+    if (!UPDATE) {
+        *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+        // red at x = 2k + p, black at x = 2k + 1 - p; same-row black values O[k0..k0+3]
+        const float4 blk = *reinterpret_cast<const float4 *>(xv + opp);
+        const float bk[4] = {blk.x, blk.y, blk.z, blk.w};
+        double *pr = up.p + row * L.nx + 2 * k0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const double2 pv = *reinterpret_cast<const double2 *>(pr + 2 * v);
+            const double er = widen(out[v]), eb = widen(bk[v]);
+            const double e0 = p ? eb : er, e1 = p ? er : eb;  // cells 2(k0+v) and 2(k0+v)+1
+            *reinterpret_cast<double2 *>(pr + 2 * v) =
+                make_double2(fma(up.alpha, e0, pv.x - up.shift), fma(up.alpha, e1, pv.y - up.shift));
+        }
+    }
 }
 
 // ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
@@ -511,6 +549,20 @@ void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const fl
         const i64 work = (i64)L.ny * L.nz * ((L.nx + 1) / 2);
         k_half_any<<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col, from_zero ? 1 : 0);
     }
+}
+
+bool half32_update_ok(Lay L) { return L.split && L.hx % 4 == 0; }
+
+void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
+                          const float *fz, const float *b, const float *x, double *p, double alpha,
+                          double shift) {
+    Coef32 cf{sinv, fx, fy, fz};
+    Upd up{p, alpha, shift};
+    count_launch();
+    const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
+    float *xv = const_cast<float *>(x);  // read only in the UPDATE variant
+    if (sinv) k_half_vec<true, false, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+    else k_half_vec<false, false, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
 }
 
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -157,13 +158,15 @@ void presmooth_restrict64(mg_handle *h, int l, const double *b, double *x, doubl
     Level &L = h->lv[l];
     smooth64(h, l, x, b, sweeps, 0);
     if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
-    mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), b, x, bc);
+    // after a pre-smoothing sweep (black last) every black residual is zero
+    mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), b, x, bc, sweeps > 0);
     if (l == 0) prof_end(h);
 }
 
 void prolong_postsmooth64(mg_handle *h, int l, const double *b, const double *ec, double *x, int sweeps) {
     if (l == 0) prof_begin(h, MG_PROF_PROLONG);
-    mg::launch_prolong<double>(h->s, h->lv[l + 1].d, ec, x, h->o.prolong);
+    // the first post sweep (black first) overwrites every black cell: correct the red ones only
+    mg::launch_prolong<double>(h->s, h->lv[l + 1].d, ec, x, h->o.prolong, sweeps > 0 ? 0 : -1);
     if (l == 0) prof_end(h);
     smooth64(h, l, x, b, sweeps, 1);
 }
@@ -213,18 +216,36 @@ void presmooth_restrict32(mg_handle *h, int l, const float *b, float *x, float *
     if (l == 0) prof_end(h);
 }
 
-// x <- post-smoothing of x + P ec
-void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, float *x, int sweeps) {
+// The outer update fused into the last half sweep of the finest level (MIXED)
+struct OuterUpdate {
+    double *p;
+    double alpha, shift;
+};
+
+// x <- post-smoothing of x + P ec.  With `up` (finest level, sweeps >= 1), the last (red)
+// half sweep adds alpha * x - shift to the FP64 solution instead of storing x.
+void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, float *x, int sweeps,
+                          const OuterUpdate *up = nullptr) {
     Level &L = h->lv[l], &C = h->lv[l + 1];
     if (l == 0) prof_begin(h, MG_PROF_PROLONG);
     // the first post sweep (black first) overwrites every black cell: correct the red ones only
     mg::launch_prolong32(h->s, L.lay, C.lay, ec, x, h->o.prolong, sweeps > 0 ? 0 : -1);
     if (l == 0) prof_end(h);
-    smooth32(h, l, b, x, sweeps, 1, false);
+    if (!up) {
+        smooth32(h, l, b, x, sweeps, 1, false);
+        return;
+    }
+    smooth32(h, l, b, x, sweeps - 1, 1, false);
+    half32(h, l, b, x, 1, false);
+    prof_begin(h, MG_PROF_UPDATE);
+    mg::launch_half32_update(h->s, L.lay, L.h2, sinv32(h, l), L.fx32, L.fy32, L.fz32, b, x, up->p, up->alpha,
+                             up->shift);
+    prof_end(h);
 }
 
-// one V-cycle on level l for A x = b from x = 0; result in x
-void vcycle32(mg_handle *h, int l, const float *b, float *x) {
+// one V-cycle on level l for A x = b from x = 0; result in x (or, with `up` on level 0,
+// added to the FP64 solution by the last half sweep)
+void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *up = nullptr) {
     Level &L = h->lv[l];
     if (l == h->nlev - 1) {
         if (l == 0) prof_begin(h, MG_PROF_COARSE);
@@ -235,7 +256,7 @@ void vcycle32(mg_handle *h, int l, const float *b, float *x) {
     Level &C = h->lv[l + 1];
     presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, true);
     vcycle32(h, l + 1, C.b32, C.x32);
-    prolong_postsmooth32(h, l, b, C.x32, x, h->o.post);
+    prolong_postsmooth32(h, l, b, C.x32, x, h->o.post, up);
 }
 
 // ---- set-up of the operator hierarchy -------------------------------------------------
@@ -290,13 +311,16 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     double hist[MG_HIST_LEN];
     MG_CUDA(h, cudaEventRecord(h->ev0, s));
     // b~ = b - mean(b), |b~|
+    // MIXED keeps b~ scaled by h^2 (what its FP64 residual kernel consumes)
+    const bool mixed = h->o.precision == MG_MIXED;
+    const double bscale = mixed ? F.h2 : 1.0;
     mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red);
-    mg::launch_sub_mean(s, n, b, h->red, h->bt, h->partials, h->red + 2);
+    mg::launch_sub_mean(s, n, b, h->red, bscale, h->bt, h->partials, h->red + 2);
     MG_CUDA(h, cudaMemcpyAsync(h->hred, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     MG_CUDA(h, cudaStreamSynchronize(s));
     int rc = check_launch(h, "rhs preparation");
     if (rc) return rc;
-    const double nb = std::sqrt(h->hred[2]);
+    const double nb = std::sqrt(h->hred[2]) / bscale;
     if (!std::isfinite(nb)) return fail(h, MG_ERR_ARG, "right-hand side is not finite");
     int status = MG_OK;
     int cycles = 0;
@@ -313,11 +337,11 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         } else {
             MG_CUDA(h, cudaMemsetAsync(p, 0, sizeof(double) * (size_t)n, s));
         }
-        const bool mixed = h->o.precision == MG_MIXED;
         double scale = 1.0 / nb;  // r32 = scale * r (scale = 1 / previous residual norm)
+        const bool fuse = mixed && h->nlev > 1 && h->o.post >= 1 && mg::half32_update_ok(F.lay);
         auto residual = [&](bool write32) -> int {
             prof_begin(h, MG_PROF_FINE_RESIDUAL);
-            mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, p,
+            mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, mixed, p,
                                    write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
             prof_end(h);
             MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->red + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -335,10 +359,15 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         if (rr <= h->o.rtol) status = MG_OK;
         for (int c = 1; c <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++c) {
             if (mixed) {
-                vcycle32(h, 0, F.b32, F.x32);
-                prof_begin(h, MG_PROF_UPDATE);
-                mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
-                prof_end(h);
+                if (fuse) {
+                    OuterUpdate up{p, 1.0 / scale, mu};
+                    vcycle32(h, 0, F.b32, F.x32, &up);
+                } else {
+                    vcycle32(h, 0, F.b32, F.x32);
+                    prof_begin(h, MG_PROF_UPDATE);
+                    mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
+                    prof_end(h);
+                }
                 scale = 1.0 / rn;
             } else {
                 vcycle64(h, 0, h->bt, p, false);
@@ -358,7 +387,12 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             }
             if (rr <= h->o.rtol) status = MG_OK;
         }
-        if (mu != 0.0) mg::launch_add_const(s, n, p, -mu);  // final zero-mean gauge
+        // exact zero-mean gauge at exit (the per-iteration shifts use an FP32 sum)
+        mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 12);
+        MG_CUDA(h, cudaMemcpyAsync(h->hred + 12, h->red + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MG_CUDA(h, cudaStreamSynchronize(s));
+        mg::launch_add_const(s, n, p, -h->hred[12] / (double)n);
+        (void)mu;
     }
     MG_CUDA(h, cudaEventRecord(h->ev1, s));
     MG_CUDA(h, cudaEventSynchronize(h->ev1));
@@ -606,9 +640,12 @@ int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, c
     return check_launch(h, "mg_rhs");
 }
 
+static bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
+
 int mg_solve(mg_handle *h, const double *b, double *p, mg_stats *st) {
     if (!h) return MG_ERR_ARG;
     if (!b || !p) return fail(h, MG_ERR_ARG, "mg_solve: null array");
+    if (!aligned16(p)) return fail(h, MG_ERR_ARG, "mg_solve: p must be 16-byte aligned");
     if (!h->have_op) return fail(h, MG_ERR_STATE, "mg_solve: coefficients not set");
     h->msg[0] = 0;
     return solve_impl(h, b, p, h->o.warm_start, st);
@@ -619,6 +656,7 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
                double *dLdsigma, mg_stats *st) {
     if (!h) return MG_ERR_ARG;
     if (!w || !p || !lam) return fail(h, MG_ERR_ARG, "mg_adjoint: w, p, lam must be non-null");
+    if (!aligned16(lam)) return fail(h, MG_ERR_ARG, "mg_adjoint: lam must be 16-byte aligned");
     bool g = gbx || gby || gbz;
     if (g && !(gbx && gby && gbz)) return fail(h, MG_ERR_ARG, "mg_adjoint: give all three gradients or none");
     bool csf = csfx || csfy || csfz;
@@ -757,7 +795,7 @@ int mg_residual_restrict(mg_handle *h, int level, int dtype, const void *x, cons
     Level &L = h->lv[level], &C = h->lv[level + 1];
     if (dtype == MG_F64) {
         mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x,
-                                          (double *)bc);
+                                          (double *)bc, false);
     } else {
         mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
         mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
@@ -774,7 +812,7 @@ int mg_prolong_correct(mg_handle *h, int level, int dtype, const void *ec, void 
     if (!ec || !x) return fail(h, MG_ERR_ARG, "mg_prolong_correct: null array");
     Level &L = h->lv[level], &C = h->lv[level + 1];
     if (dtype == MG_F64) {
-        mg::launch_prolong<double>(h->s, C.d, (const double *)ec, (double *)x, h->o.prolong);
+        mg::launch_prolong<double>(h->s, C.d, (const double *)ec, (double *)x, h->o.prolong, -1);
     } else {
         mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
         mg::launch_pack32(h->s, C.lay, (const float *)ec, C.s1_32);

@@ -90,6 +90,14 @@ void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 // non-null, else the low-face arrays; from_zero: the other colour is taken as zero
 void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
                    const float *fz, const float *b, float *x, int col, bool from_zero);
+// the last red half sweep of the finest level with the outer update fused in: the new red
+// values and the black values of the same row positions (x, split, level 0) go straight
+// into p = (p - shift) + alpha * x (p natural FP64); x itself is not written.
+// Needs a split layout with hx % 4 == 0 (half32_update_ok).
+bool half32_update_ok(Lay L);
+void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
+                          const float *fz, const float *b, const float *x, double *p, double alpha,
+                          double shift);
 // r = b - A x (or r = A x when apply_only)
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
                        const float *fz, const float *b, const float *x, float *r, bool apply_only);
@@ -111,11 +119,13 @@ template <typename T>
 void launch_apply(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *x, T *y);
 template <typename T>
 void launch_residual(cudaStream_t s, Dims d, double ih2, Coef<T> c, const T *b, const T *x, T *r);
+// bc = mean of the 8 children's residuals (red_only: black children count as 0)
 template <typename T>
 void launch_resid_restrict(cudaStream_t s, Dims fine, double ih2, Coef<T> c, const T *b,
-                           const T *x, T *bc);
+                           const T *x, T *bc, bool red_only);
+// e += P ec on the cells of colour only_col (0 red, 1 black) or all cells (-1)
 template <typename T>
-void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind);
+void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind, int only_col);
 template <typename T>
 void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r, T *e);
 
@@ -123,8 +133,8 @@ void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r
 // partials: reduce_blocks(n) x 2 doubles; out: 2 doubles (deterministic order)
 template <typename T>
 void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out);
-// b64 = b - out_mean[0]/n, with sum of squares of b64 into out[0]
-void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double *b64,
+// b64 = (b - sum[0]/n) * scale, with the sum of squares of b64 into out[0]
+void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double scale, double *b64,
                      double *partials, double *out);
 // fine FP64 residual r = b - A p: out[0] = sum r^2, out[1] = sum p; optional r32 = scale * r
 // stored in the level-0 FP32 layout L
@@ -134,8 +144,8 @@ void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const doubl
 // fine FP64 residual in diagonal form, h^2 r = h^2 b - (diag p_c - sum_f beta_f p_nb):
 // out[0] = sum (h^2 r)^2, out[1] = sum p; optional r32 = s32 * h^2 r in the level-0 layout L
 void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
-                        const double *fz, const double *diag, const double *b, const double *p, float *r32,
-                        float s32, double *partials, double *out);
+                        const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
+                        float *r32, float s32, double *partials, double *out);
 // p = p - shift + alpha * e32 (e32 in the level-0 FP32 layout L; shift a host scalar)
 void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift);
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c);
