@@ -35,6 +35,11 @@
  *   FP64     plain FP64 V-cycles on p until |b~ - A p| / |b~| <= rtol.
  *   MIXED    FP64 defect correction: r = b~ - A p in FP64, one FP32 V-cycle
  *            on r, p += correction in FP64, zero mean; same stopping rule.
+ *   MIXED_DF as MIXED, but the outer residual and update carry p, b~ and the
+ *            finest-level coefficients as pairs of FP32 numbers (hi + lo, about
+ *            48 significant bits) and use FP32 arithmetic with error-free
+ *            transformations; FP64 is used only to enter and leave the loop.
+ *            Needs an even nx and |b~| < 1e30.
  *
  * Conventions for every entry point:
  *   - Array arguments are DEVICE pointers (CUDA global memory of the device the
@@ -71,7 +76,7 @@ enum {
     MG_ERR_STATE = -7          /* call order: e.g. solve before coefficients were set */
 };
 
-enum { MG_FP64 = 0, MG_MIXED = 1 };
+enum { MG_FP64 = 0, MG_MIXED = 1, MG_MIXED_DF = 2 };
 enum { MG_PROLONG_TRILINEAR = 0, MG_PROLONG_CONSTANT = 1 };
 enum { MG_F64 = 0, MG_F32 = 1 }; /* element type of component-level arrays */
 
@@ -84,7 +89,7 @@ typedef struct mg_handle mg_handle;
 typedef struct {
     int nx, ny, nz;   /* cells per dimension, each >= 1, nx*ny*nz >= 2 */
     double h;         /* grid spacing, > 0 */
-    int precision;    /* MG_FP64 or MG_MIXED */
+    int precision;    /* MG_FP64, MG_MIXED or MG_MIXED_DF */
     int pre, post;    /* RBGS sweeps before / after the coarse correction (>= 0) */
     int coarsest;     /* stop coarsening once the largest dimension is <= this (>= 2) */
     int prolong;      /* MG_PROLONG_TRILINEAR or MG_PROLONG_CONSTANT */
@@ -177,8 +182,8 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
 
 /* ---- component steps of the V-cycle on level `level` --------------------------
  * For callers that assemble their own cycles, and for step-by-step checking.
- * dtype MG_F64 uses the FP64 coefficients, MG_F32 the FP32 copies (MIXED
- * handles only); arrays are then double or float cell arrays of that level.
+ * dtype MG_F64 uses the FP64 coefficients, MG_F32 the FP32 copies (MIXED and
+ * MIXED_DF handles); arrays are then double or float cell arrays of that level.
  * Physical scaling: level l has spacing h * 2^l. */
 
 /* y = A_l x */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmgpoisson.so")
 
 MG_OK, MG_ERR_ARG, MG_ERR_DENSITY, MG_ERR_NOT_CONVERGED = 0, -1, -2, -3
 MG_ERR_DIVERGED, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_STATE = -4, -5, -6, -7
-MG_FP64, MG_MIXED = 0, 1
+MG_FP64, MG_MIXED, MG_MIXED_DF = 0, 1, 2
 MG_PROLONG_TRILINEAR, MG_PROLONG_CONSTANT = 0, 1
 MG_F64, MG_F32 = 0, 1
 MG_MAX_LEVELS, MG_MAX_COARSE, MG_HIST_LEN = 24, 1024, 256

@@ -113,17 +113,33 @@ __device__ __forceinline__ double widen(float f) {
 }
 
 struct Upd {
-    double *p;      // natural FP64 solution of the finest level
+    double *p;      // natural FP64 solution of the finest level (UPDATE 1)
+    float2 *p2;     // natural double-float solution of the finest level (UPDATE 2)
     double alpha;   // scale of the correction
     double shift;   // gauge shift
 };
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// double-float (h, l) + t, renormalised (Knuth's TwoSum on the high parts)
+__device__ __forceinline__ void df_add(float &h, float &l, float t) {
+    float s, e;
+    two_sum_f(h, t, s, e);
+    e += l;
+    h = s + e;
+    l = e - (h - s);
+}
 
 // ---- vectorised half sweep on split levels (hx % 4 == 0) ---------------------------------
 // one thread updates 4 consecutive cells (k0..k0+3) of colour col in one row.
 // UPDATE (last red half sweep of the finest level): instead of storing the 4 new red values,
 // add alpha * x - shift for them and for the 4 black values of the same row positions --
-// together the 8 consecutive cells x = 2 k0 .. 2 k0 + 7 -- to the FP64 solution.
-template <bool SFORM, bool FROM_ZERO, bool UPDATE = false>
+// together the 8 consecutive cells x = 2 k0 .. 2 k0 + 7 -- to the solution: the FP64 one
+// (UPDATE 1) or the double-float one (UPDATE 2).
+template <bool SFORM, bool FROM_ZERO, int UPDATE = 0>
 __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col,
                            Upd up = Upd{}) {
     const int hx = L.hx, kv = hx >> 2;
@@ -217,8 +233,21 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
         const float den = ((w0[v] + w1[v]) + (w2[v] + w3[v])) + (w4[v] + w5[v]);
         out[v] = __fdividef(hh * bb[v] + num, den);
     }
-    if (!UPDATE) {
+    if (UPDATE == 0) {
         *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+    } else if (UPDATE == 2) {
+        const float4 blk = *reinterpret_cast<const float4 *>(xv + opp);
+        const float bk[4] = {blk.x, blk.y, blk.z, blk.w};
+        const float al = (float)up.alpha, sh = (float)up.shift;
+        float2 *pr = up.p2 + row * L.nx + 2 * k0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float4 pv = *reinterpret_cast<const float4 *>(pr + 2 * v);  // (h0, l0, h1, l1)
+            const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
+            df_add(pv.x, pv.y, fmaf(al, e0, -sh));
+            df_add(pv.z, pv.w, fmaf(al, e1, -sh));
+            *reinterpret_cast<float4 *>(pr + 2 * v) = pv;
+        }
     } else {
         // red at x = 2k + p, black at x = 2k + 1 - p; same-row black values O[k0..k0+3]
         const float4 blk = *reinterpret_cast<const float4 *>(xv + opp);
@@ -554,15 +583,20 @@ void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const fl
 bool half32_update_ok(Lay L) { return L.split && L.hx % 4 == 0; }
 
 void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
-                          const float *fz, const float *b, const float *x, double *p, double alpha,
+                          const float *fz, const float *b, const float *x, double *p, float2 *p2, double alpha,
                           double shift) {
     Coef32 cf{sinv, fx, fy, fz};
-    Upd up{p, alpha, shift};
+    Upd up{p, p2, alpha, shift};
     count_launch();
     const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
-    float *xv = const_cast<float *>(x);  // read only in the UPDATE variant
-    if (sinv) k_half_vec<true, false, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
-    else k_half_vec<false, false, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+    float *xv = const_cast<float *>(x);  // read only in the UPDATE variants
+    if (p2) {
+        if (sinv) k_half_vec<true, false, 2><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+        else k_half_vec<false, false, 2><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+    } else {
+        if (sinv) k_half_vec<true, false, 1><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+        else k_half_vec<false, false, 1><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+    }
 }
 
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,

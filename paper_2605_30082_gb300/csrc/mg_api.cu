@@ -30,6 +30,7 @@ struct Level {
     double h, h2, ih2;
     double *fx64, *fy64, *fz64, *invd64;
     double *d64;            // level 0: sum of the interior face coefficients (FP64 residual)
+    float2 *fx2, *fy2, *fz2, *d2;  // MIXED_DF, level 0: coefficients and diagonal as FP32 pairs
     float *fx32, *fy32, *fz32;
     double *x64, *b64;      // FP64 path: iterate and RHS, levels >= 1
     float *x32, *b32;       // MIXED inner cycle, all levels (level 0: e and the scaled r)
@@ -49,7 +50,8 @@ struct mg_handle {
     Level lv[MG_MAX_LEVELS];
     int nc;
     double *pinv, *gj_tmp, *scal;
-    double *bt;        // zero-mean fine RHS
+    double *bt;        // zero-mean fine RHS (scaled by h^2 in the mixed modes)
+    float2 *bt2, *p2;  // MIXED_DF: the RHS and the solution as FP32 pairs
     double *partials;  // reduction partials
     double *red;       // device reduction results (16 doubles)
     double *hred;      // pinned host copy of red
@@ -218,7 +220,8 @@ void presmooth_restrict32(mg_handle *h, int l, const float *b, float *x, float *
 
 // The outer update fused into the last half sweep of the finest level (MIXED)
 struct OuterUpdate {
-    double *p;
+    double *p;     // FP64 solution (MIXED)
+    float2 *p2;    // double-float solution (MIXED_DF)
     double alpha, shift;
 };
 
@@ -238,8 +241,8 @@ void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, 
     smooth32(h, l, b, x, sweeps - 1, 1, false);
     half32(h, l, b, x, 1, false);
     prof_begin(h, MG_PROF_UPDATE);
-    mg::launch_half32_update(h->s, L.lay, L.h2, sinv32(h, l), L.fx32, L.fy32, L.fz32, b, x, up->p, up->alpha,
-                             up->shift);
+    mg::launch_half32_update(h->s, L.lay, L.h2, sinv32(h, l), L.fx32, L.fy32, L.fz32, b, x, up->p, up->p2,
+                             up->alpha, up->shift);
     prof_end(h);
 }
 
@@ -266,7 +269,7 @@ int finish_operator(mg_handle *h) {
         Level &F = h->lv[l], &C = h->lv[l + 1];
         mg::launch_coarsen(s, F.d, F.fx64, F.fy64, F.fz64, C.fx64, C.fy64, C.fz64);
     }
-    bool mixed = h->o.precision == MG_MIXED;
+    bool mixed = h->o.precision != MG_FP64;
     for (int l = 0; l < h->nlev; ++l) {
         Level &L = h->lv[l];
         mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, l == 0 ? L.d64 : nullptr);
@@ -275,6 +278,13 @@ int finish_operator(mg_handle *h) {
             mg::launch_pack64to32(s, L.lay, L.fy64, L.fy32);
             mg::launch_pack64to32(s, L.lay, L.fz64, L.fz32);
         }
+    }
+    if (h->o.precision == MG_MIXED_DF) {
+        Level &F = h->lv[0];
+        mg::launch_split(s, F.d.n, F.fx64, F.fx2);
+        mg::launch_split(s, F.d.n, F.fy64, F.fy2);
+        mg::launch_split(s, F.d.n, F.fz64, F.fz2);
+        mg::launch_split(s, F.d.n, F.d64, F.d2);
     }
     // dense pseudo-inverse of the coarsest operator
     Level &C = h->lv[h->nlev - 1];
@@ -311,8 +321,9 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     double hist[MG_HIST_LEN];
     MG_CUDA(h, cudaEventRecord(h->ev0, s));
     // b~ = b - mean(b), |b~|
-    // MIXED keeps b~ scaled by h^2 (what its FP64 residual kernel consumes)
-    const bool mixed = h->o.precision == MG_MIXED;
+    // the mixed modes keep b~ scaled by h^2 (what their outer residual kernels consume)
+    const bool mixed = h->o.precision != MG_FP64;
+    const bool df = h->o.precision == MG_MIXED_DF;
     const double bscale = mixed ? F.h2 : 1.0;
     mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red);
     mg::launch_sub_mean(s, n, b, h->red, bscale, h->bt, h->partials, h->red + 2);
@@ -322,6 +333,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     if (rc) return rc;
     const double nb = std::sqrt(h->hred[2]) / bscale;
     if (!std::isfinite(nb)) return fail(h, MG_ERR_ARG, "right-hand side is not finite");
+    if (df && !(nb < 1e30)) return fail(h, MG_ERR_ARG, "MG_MIXED_DF needs |b - mean b| < 1e30");
     int status = MG_OK;
     int cycles = 0;
     double rr = 0.0;
@@ -339,10 +351,18 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         }
         double scale = 1.0 / nb;  // r32 = scale * r (scale = 1 / previous residual norm)
         const bool fuse = mixed && h->nlev > 1 && h->o.post >= 1 && mg::half32_update_ok(F.lay);
+        if (df) {
+            mg::launch_split(s, n, h->bt, h->bt2);
+            mg::launch_split(s, n, p, h->p2);
+        }
         auto residual = [&](bool write32) -> int {
             prof_begin(h, MG_PROF_FINE_RESIDUAL);
-            mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, mixed, p,
-                                   write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
+            if (df)
+                mg::launch_resid_df(s, F.d, F.lay, F.fx2, F.fy2, F.fz2, F.d2, h->bt2, h->p2,
+                                    write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
+            else
+                mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, mixed, p,
+                                       write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
             prof_end(h);
             MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->red + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
             MG_CUDA(h, cudaStreamSynchronize(s));
@@ -360,12 +380,13 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         for (int c = 1; c <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++c) {
             if (mixed) {
                 if (fuse) {
-                    OuterUpdate up{p, 1.0 / scale, mu};
+                    OuterUpdate up{df ? nullptr : p, df ? h->p2 : nullptr, 1.0 / scale, mu};
                     vcycle32(h, 0, F.b32, F.x32, &up);
                 } else {
                     vcycle32(h, 0, F.b32, F.x32);
                     prof_begin(h, MG_PROF_UPDATE);
-                    mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
+                    if (df) mg::launch_update_df(s, F.d, F.lay, h->p2, F.x32, 1.0 / scale, mu);
+                    else mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
                     prof_end(h);
                 }
                 scale = 1.0 / rn;
@@ -387,6 +408,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             }
             if (rr <= h->o.rtol) status = MG_OK;
         }
+        if (df) mg::launch_join(s, n, h->p2, p);
         // exact zero-mean gauge at exit (the per-iteration shifts use an FP32 sum)
         mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 12);
         MG_CUDA(h, cudaMemcpyAsync(h->hred + 12, h->red + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -417,7 +439,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
 int check_cycle_dtype(mg_handle *h, int dtype) {
     if ((dtype == MG_F64) != (h->o.precision == MG_FP64))
         return fail(h, MG_ERR_ARG, "smoothing components run in the handle's V-cycle precision "
-                                   "(MG_F64 for MG_FP64 handles, MG_F32 for MG_MIXED handles)");
+                                   "(MG_F64 for MG_FP64 handles, MG_F32 for the mixed modes)");
     return MG_OK;
 }
 
@@ -426,8 +448,8 @@ int check_level(mg_handle *h, int level, int dtype, bool need_coarser) {
     if (level < 0 || level >= h->nlev || (need_coarser && level >= h->nlev - 1))
         return fail(h, MG_ERR_ARG, "level %d out of range (levels: %d)", level, h->nlev);
     if (dtype != MG_F64 && dtype != MG_F32) return fail(h, MG_ERR_ARG, "dtype must be MG_F64 or MG_F32");
-    if (dtype == MG_F32 && h->o.precision != MG_MIXED)
-        return fail(h, MG_ERR_ARG, "MG_F32 components need a MG_MIXED handle");
+    if (dtype == MG_F32 && h->o.precision == MG_FP64)
+        return fail(h, MG_ERR_ARG, "MG_F32 components need a mixed-precision handle");
     if (!h->have_op) return fail(h, MG_ERR_STATE, "coefficients not set");
     return MG_OK;
 }
@@ -456,7 +478,8 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
     if (!o) return MG_ERR_ARG;
     if (o->nx < 1 || o->ny < 1 || o->nz < 1 || (i64)o->nx * o->ny * o->nz < 2 ||
         (i64)o->nx * o->ny * o->nz > (i64)2000000000 || !(o->h > 0.0) || !std::isfinite(o->h) ||
-        (o->precision != MG_FP64 && o->precision != MG_MIXED) || o->pre < 0 || o->post < 0 ||
+        (o->precision != MG_FP64 && o->precision != MG_MIXED && o->precision != MG_MIXED_DF) ||
+        (o->precision == MG_MIXED_DF && o->nx % 2 != 0) || o->pre < 0 || o->post < 0 ||
         o->pre > 64 || o->post > 64 || o->coarsest < 2 ||
         (o->prolong != MG_PROLONG_TRILINEAR && o->prolong != MG_PROLONG_CONSTANT) || !(o->rtol >= 0.0) ||
         o->max_cycles < 0)
@@ -472,7 +495,8 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
     h->s = (cudaStream_t)stream;
     h->nlev = nl;
     h->nc = (int)nc;
-    const bool mixed = o->precision == MG_MIXED;
+    const bool mixed = o->precision != MG_FP64;
+    const bool dfm = o->precision == MG_MIXED_DF;
 
     // plan the arena: (pointer slot, bytes) pairs, each rounded up to 256 B
     struct Slot {
@@ -504,6 +528,12 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
             add((void **)&L.s1_32, 4 * n);
             add((void **)&L.s2_32, 4 * n);
             if (l == 0) add((void **)&L.s32, 4 * n);
+            if (l == 0 && dfm) {
+                add((void **)&L.fx2, 8 * n);
+                add((void **)&L.fy2, 8 * n);
+                add((void **)&L.fz2, 8 * n);
+                add((void **)&L.d2, 8 * n);
+            }
         } else if (l > 0) {
             add((void **)&L.x64, 8 * n);
             add((void **)&L.b64, 8 * n);
@@ -513,6 +543,10 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
     add((void **)&h->gj_tmp, 8 * (size_t)nc * nc);
     add((void **)&h->scal, 8 * 4);
     add((void **)&h->bt, 8 * (size_t)h->lv[0].d.n);
+    if (dfm) {
+        add((void **)&h->bt2, 8 * (size_t)h->lv[0].d.n);
+        add((void **)&h->p2, 8 * (size_t)h->lv[0].d.n);
+    }
     add((void **)&h->partials, 16 * (size_t)mg::reduce_blocks(h->lv[0].d.n));
     add((void **)&h->red, 8 * 16);
     add((void **)&h->err, 256);
@@ -591,7 +625,7 @@ int mg_set_density(mg_handle *h, const double *rho) {
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
     mg::launch_faces_from_rho(h->s, F.d, rho, F.fx64, F.fy64, F.fz64, h->err);
-    h->sform0 = h->o.precision == MG_MIXED;
+    h->sform0 = h->o.precision != MG_FP64;
     if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, rho, F.s32);
     return finish_operator(h);
 }

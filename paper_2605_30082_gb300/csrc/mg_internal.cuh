@@ -95,9 +95,20 @@ void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const fl
 // into p = (p - shift) + alpha * x (p natural FP64); x itself is not written.
 // Needs a split layout with hx % 4 == 0 (half32_update_ok).
 bool half32_update_ok(Lay L);
+// p2 non-null: the double-float solution is updated instead of p
 void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
-                          const float *fz, const float *b, const float *x, double *p, double alpha,
+                          const float *fz, const float *b, const float *x, double *p, float2 *p2, double alpha,
                           double shift);
+
+// ---- MG_MIXED_DF outer loop (kernels_df.cu): double-float (hi, lo) FP32 pairs ----
+void launch_split(cudaStream_t s, i64 n, const double *src, float2 *dst);   // hi = fl32(v), lo = fl32(v - hi)
+void launch_join(cudaStream_t s, i64 n, const float2 *src, double *dst);    // v = hi + lo in FP64
+// h^2 r = b + sum_f beta_f p_nb - d p_c (b scaled by h^2); out[0] = sum (h^2 r)^2, out[1] = sum p;
+// optional r32 = s32 * h^2 r in the split level-0 layout.  Needs even nx.
+void launch_resid_df(cudaStream_t s, Dims d, Lay L, const float2 *fx, const float2 *fy, const float2 *fz,
+                     const float2 *diag, const float2 *b, const float2 *p, float *r32, float s32,
+                     double *partials, double *out);
+void launch_update_df(cudaStream_t s, Dims d, Lay L, float2 *p, const float *e32, double alpha, double shift);
 // r = b - A x (or r = A x when apply_only)
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
                        const float *fz, const float *b, const float *x, float *r, bool apply_only);

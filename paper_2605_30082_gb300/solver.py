@@ -23,9 +23,9 @@ class MgError(RuntimeError):
 class Solver:
     """Multigrid pressure Poisson solver for one grid on the current CUDA device.
 
-    Parameters mirror ``mg_opts``: dims = (nx, ny, nz), h, precision ('fp64' or
-    'mixed'), pre/post sweeps, coarsest, prolong ('trilinear' or 'constant'),
-    rtol, max_cycles, warm_start.
+    Parameters mirror ``mg_opts``: dims = (nx, ny, nz), h, precision ('fp64',
+    'mixed' or 'mixed_df'), pre/post sweeps, coarsest, prolong ('trilinear' or
+    'constant'), rtol, max_cycles, warm_start.
     """
 
     def __init__(self, dims, h=None, precision="mixed", pre=2, post=2, coarsest=None,
@@ -34,9 +34,9 @@ class Solver:
         o = L.mg_default_opts()
         o.nx, o.ny, o.nz = nx, ny, nz
         o.h = float(h if h is not None else 1.0 / max(nx, ny, nz))
-        o.precision = {"fp64": L.MG_FP64, "mixed": L.MG_MIXED}[precision]
+        o.precision = {"fp64": L.MG_FP64, "mixed": L.MG_MIXED, "mixed_df": L.MG_MIXED_DF}[precision]
         o.pre, o.post = int(pre), int(post)
-        o.coarsest = int(coarsest if coarsest is not None else (8 if precision == "mixed" else 4))
+        o.coarsest = int(coarsest if coarsest is not None else (4 if precision == "fp64" else 8))
         o.prolong = {"trilinear": L.MG_PROLONG_TRILINEAR, "constant": L.MG_PROLONG_CONSTANT}[prolong]
         o.rtol = float(rtol)
         o.max_cycles = int(max_cycles)

@@ -27,7 +27,7 @@ def csf_case(n):
     return c
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 def test_adjoint_matches_oracle_32cubed(prec):
     c = csf_case(32)
     h, sigma = c["h"], 0.03

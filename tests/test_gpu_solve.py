@@ -44,7 +44,7 @@ def test_fp64_reproduces_oracle_iteration_32cubed(c32):
     assert abs(host(p).mean()) < 1e-14 * np.abs(host(p)).max()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 def test_solution_matches_exact_32cubed(c32, prec):
     s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8)
     s.set_density(dev(c32["rho"]))
@@ -56,7 +56,7 @@ def test_solution_matches_exact_32cubed(c32, prec):
 
 
 @pytest.mark.parametrize("dims", [(64, 64, 64), (64, 48, 32), (96, 40, 24)])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 def test_ragged_grids_match_exact(dims, prec):
     nx, ny, nz = dims
     h = 1.0 / 64
@@ -115,6 +115,22 @@ def test_edge_cases():
     with pytest.raises(MgError) as ei:
         s.solve(dev(bad))
     assert ei.value.code == MG_ERR_ARG
+
+
+def test_mixed_df_matches_mixed_and_needs_even_nx():
+    """The double-float outer loop reaches the same discrete solution as the FP64 one."""
+    dims = (48, 32, 40)
+    rho = random_rho(dims, 12)
+    b = np.random.default_rng(8).standard_normal((40, 32, 48))
+    ps = {}
+    for prec in ("mixed", "mixed_df"):
+        s = Solver(dims, h=1 / 48, precision=prec, coarsest=8, rtol=1e-12, max_cycles=400)
+        s.set_density(dev(rho))
+        ps[prec] = host(s.solve(dev(b)))
+        assert s.last_stats.relres <= 1e-12
+    assert rel(ps["mixed_df"], ps["mixed"]) < 1e-10
+    with pytest.raises(MgError):
+        Solver((47, 32, 40), precision="mixed_df")
 
 
 def test_wrong_shapes_and_devices_are_rejected():
