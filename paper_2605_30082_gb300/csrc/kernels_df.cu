@@ -174,6 +174,180 @@ __global__ void k_final_df(const double *__restrict__ partials, int nb, double *
     }
 }
 
+// ---- s-form double-float residual (operator set from a density) ------------------------
+// With s = 1/rho per cell and beta_f = (s_c + s_nb) / 2,
+//   2 h^2 r_c = 2 h^2 b_c + sum_f (s_c + s_nb) (p_nb - p_c),
+// which reads 24 B per cell (p, h^2 b, s as double-float pairs) instead of the face form's 48.
+// Intermediate pairs stay unnormalised: the high parts of every sum are exact (TwoSum) and
+// the low parts collect the errors in FP32, dropping terms of relative size 2^-48.
+__device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, float &dh, float &dl) {
+    float e;
+    two_sum(ah, -bh, dh, e);
+    dl = e + (al - bl);
+}
+__device__ __forceinline__ void df_sum(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    float e;
+    two_sum(ah, bh, sh, e);
+    sl = e + (al + bl);
+}
+// (sa + sb) * (pa - pb) for double-float sa, sb, pa, pb; unnormalised product
+__device__ __forceinline__ void df_face(float sah, float sal, float sbh, float sbl, float pah, float pal,
+                                        float pbh, float pbl, float &fh, float &fl) {
+    float bh, bl, dh, dl;
+    df_sum(sah, sal, sbh, sbl, bh, bl);
+    df_diff(pah, pal, pbh, pbl, dh, dl);
+    fh = bh * dh;
+    fl = fmaf(bh, dh, -fh);
+    fl = fmaf(bh, dl, fmaf(bl, dh, fl));
+}
+__device__ __forceinline__ void df_acc(float &ah, float &al, float fh, float fl) {
+    float s, t;
+    two_sum(ah, fh, s, t);
+    ah = s;
+    al += t + fl;
+}
+
+constexpr int kDfsZ = 16;        // planes per tile
+constexpr int kDfsThreads = 128;
+
+// One thread per cell pair x = 2k, 2k+1 of a row (even nx); a warp covers 32 pairs of one row
+// and each thread marches kDfsZ planes in z, carrying the (z-1, z) face product from the
+// previous plane.  Persistent blocks take tiles (row chunk, row, z-chunk) in a fixed order so
+// the partial sums do not depend on scheduling.  Outputs as k_resid_df.
+__global__ void __launch_bounds__(kDfsThreads, 6)
+    k_resid_dfs(Dims d, Lay L, const float2 *__restrict__ s2, const float2 *__restrict__ b, const float2 *__restrict__ p,
+                float *r32, float s32, double *partials, int tiles_x, int tiles_y, i64 ntiles) {
+    const int nx = d.nx, ny = d.ny, nz = d.nz, hx = nx >> 1;
+    const i64 nxy = d.nxy;
+    const int vb = blockDim.x, lane = threadIdx.x & 31;
+    const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [](const float2 *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
+    double qd = 0.0, spd = 0.0;
+    for (i64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tx = (int)(t % tiles_x);
+        const i64 rest = t / tiles_x;
+        const int yb = (int)(rest % tiles_y), zc = (int)(rest / tiles_y);
+        const int kvi = tx * vb + threadIdx.x, yi = yb * blockDim.y + threadIdx.y;
+        const bool active = kvi < hx && yi < ny;
+        const int k = min(kvi, hx - 1), y = min(yi, ny - 1);
+        const bool kl = k > 0, kr = k < hx - 1, hy0 = y > 0, hy1 = y < ny - 1;
+        const int z0 = zc * kDfsZ, z1 = min(z0 + kDfsZ, nz);
+        i64 c = ((i64)z0 * ny + y) * nx + 2 * k;
+        float4 pc = ld(p, c), sc = ld(s2, c);
+        // carried (z-1, z) face products of the two cells
+        float4 cz = f0;
+        if (z0 > 0) {
+            const float4 pm = ld(p, c - nxy), sm = ld(s2, c - nxy);
+            df_face(sm.x, sm.y, sc.x, sc.y, pc.x, pc.y, pm.x, pm.y, cz.x, cz.y);
+            df_face(sm.z, sm.w, sc.z, sc.w, pc.z, pc.w, pm.z, pm.w, cz.z, cz.w);
+        }
+        float q = 0.f, sp = 0.f;
+        for (int z = z0; z < z1; ++z) {
+            const bool hz0 = z > 0, hz1 = z < nz - 1;
+            float4 pp = f0, sq = f0;
+            if (hz1) {
+                pp = ld(p, c + nxy);
+                sq = ld(s2, c + nxy);
+            }
+            const float4 bb = ld(b, c);
+            float a0h = 2.f * bb.x, a0l = 2.f * bb.y, a1h = 2.f * bb.z, a1l = 2.f * bb.w;
+            float fh, fl;
+            // faces to z-1: minus the carried products
+            if (hz0) {
+                df_acc(a0h, a0l, -cz.x, -cz.y);
+                df_acc(a1h, a1l, -cz.z, -cz.w);
+            }
+            // faces to z+1, carried to the next plane
+            if (hz1) {
+                df_face(sc.x, sc.y, sq.x, sq.y, pp.x, pp.y, pc.x, pc.y, cz.x, cz.y);
+                df_face(sc.z, sc.w, sq.z, sq.w, pp.z, pp.w, pc.z, pc.w, cz.z, cz.w);
+                df_acc(a0h, a0l, cz.x, cz.y);
+                df_acc(a1h, a1l, cz.z, cz.w);
+            }
+            if (hy0) {
+                const float4 pn = ld(p, c - nx), sn = ld(s2, c - nx);
+                df_face(sc.x, sc.y, sn.x, sn.y, pn.x, pn.y, pc.x, pc.y, fh, fl);
+                df_acc(a0h, a0l, fh, fl);
+                df_face(sc.z, sc.w, sn.z, sn.w, pn.z, pn.w, pc.z, pc.w, fh, fl);
+                df_acc(a1h, a1l, fh, fl);
+            }
+            if (hy1) {
+                const float4 pn = ld(p, c + nx), sn = ld(s2, c + nx);
+                df_face(sc.x, sc.y, sn.x, sn.y, pn.x, pn.y, pc.x, pc.y, fh, fl);
+                df_acc(a0h, a0l, fh, fl);
+                df_face(sc.z, sc.w, sn.z, sn.w, pn.z, pn.w, pc.z, pc.w, fh, fl);
+                df_acc(a1h, a1l, fh, fl);
+            }
+            // x faces: inside the pair, then x-1 of cell 0 and x+1 of cell 1 (neighbour lanes)
+            df_face(sc.x, sc.y, sc.z, sc.w, pc.z, pc.w, pc.x, pc.y, fh, fl);
+            df_acc(a0h, a0l, fh, fl);
+            df_acc(a1h, a1l, -fh, -fl);
+            float plh = __shfl_up_sync(0xffffffffu, pc.z, 1), pll = __shfl_up_sync(0xffffffffu, pc.w, 1);
+            float slh = __shfl_up_sync(0xffffffffu, sc.z, 1), sll = __shfl_up_sync(0xffffffffu, sc.w, 1);
+            float prh = __shfl_down_sync(0xffffffffu, pc.x, 1), prl = __shfl_down_sync(0xffffffffu, pc.y, 1);
+            float srh = __shfl_down_sync(0xffffffffu, sc.x, 1), srl = __shfl_down_sync(0xffffffffu, sc.y, 1);
+            if (lane == 0) {
+                const float2 pv = kl ? p[c - 1] : make_float2(0.f, 0.f), sv = kl ? s2[c - 1] : make_float2(0.f, 0.f);
+                plh = pv.x; pll = pv.y; slh = sv.x; sll = sv.y;
+            }
+            if (lane == 31) {
+                const float2 pv = kr ? p[c + 2] : make_float2(0.f, 0.f), sv = kr ? s2[c + 2] : make_float2(0.f, 0.f);
+                prh = pv.x; prl = pv.y; srh = sv.x; srl = sv.y;
+            }
+            df_face(sc.x, sc.y, slh, sll, plh, pll, pc.x, pc.y, fh, fl);
+            if (kl) df_acc(a0h, a0l, fh, fl);
+            df_face(sc.z, sc.w, srh, srl, prh, prl, pc.z, pc.w, fh, fl);
+            if (kr) df_acc(a1h, a1l, fh, fl);
+            const float r0 = 0.5f * (a0h + a0l), r1 = 0.5f * (a1h + a1l);
+            if (active) {
+                if (r32) {
+                    const int par = (y + z) & 1;
+                    const i64 base = ((i64)z * ny + y) * hx + k;
+                    r32[par * L.half + base] = r0 * s32;
+                    r32[(1 - par) * L.half + base] = r1 * s32;
+                }
+                q = fmaf(r0, r0, q);
+                q = fmaf(r1, r1, q);
+                sp += pc.x + pc.z;
+            }
+            pc = pp;
+            sc = sq;
+            c += nxy;
+        }
+        qd += (double)q;
+        spd += (double)sp;
+    }
+    // block sum -> partials[2 * blockIdx.x], fixed order
+    __shared__ double sa[32], sb[32];
+    double a = qd, bsum = spd;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int warp = tid >> 5;
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = bsum;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x * blockDim.y) >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        bsum = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+        }
+        if (lane == 0) {
+            partials[2 * blockIdx.x] = a;
+            partials[2 * blockIdx.x + 1] = bsum;
+        }
+    }
+}
+
 __device__ __forceinline__ i64 sto(const Lay &L, int x, int y, int z) {
     const i64 row = (i64)z * L.ny + y;
     if (!L.split) return row * L.nx + x;
@@ -215,6 +389,22 @@ void launch_resid_df(cudaStream_t s, Dims d, Lay L, const float2 *fx, const floa
     k_resid_df<<<nb, kReduceThreads, 0, s>>>(d, L, fx, fy, fz, diag, b, p, r32, s32, partials);
     count_launch();
     k_final_df<<<1, 256, 0, s>>>(partials, nb, out);
+}
+
+void launch_resid_dfs(cudaStream_t s, Dims d, Lay L, const float2 *s2, const float2 *b, const float2 *p,
+                      float *r32, float s32, double *partials, double *out) {
+    const int hx = d.nx / 2;
+    const int vb = (hx % 64 == 0) ? 64 : 32;
+    const dim3 blk(vb, kDfsThreads / vb);
+    const int tiles_x = (hx + vb - 1) / vb, tiles_y = (d.ny + (int)blk.y - 1) / (int)blk.y;
+    const i64 ntiles = (i64)tiles_x * tiles_y * ((d.nz + kDfsZ - 1) / kDfsZ);
+    i64 nb = 152 * 6;
+    if (nb > ntiles) nb = ntiles;
+    if (nb > reduce_blocks(d.n)) nb = reduce_blocks(d.n);  // the partials buffer holds reduce_blocks(n) pairs
+    count_launch();
+    k_resid_dfs<<<(unsigned)nb, blk, 0, s>>>(d, L, s2, b, p, r32, s32, partials, tiles_x, tiles_y, ntiles);
+    count_launch();
+    k_final_df<<<1, 256, 0, s>>>(partials, (int)nb, out);
 }
 
 void launch_update_df(cudaStream_t s, Dims d, Lay L, float2 *p, const float *e32, double alpha, double shift) {

@@ -264,6 +264,182 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
     }
 }
 
+// ---- z-marching vectorised half sweep (split levels, hx % 4 == 0, hx / 4 >= 32) -----------
+// A warp covers 32 consecutive 4-cell vectors of one row.  Each thread walks ZC planes in z
+// and keeps the other colour's x (and s) of planes z-1, z and z+1 in registers, so each plane
+// of the other colour comes from memory once per sweep instead of three times (z-1, z, z+1).
+// The same-row window scalars (x at k0-1 and k0+4) come from the neighbouring lanes; the
+// lanes at a warp's edge load them.  Lanes past the end of a row, or rows past ny, compute on
+// clamped (in-bounds) indices and store nothing; all lanes of a warp share one row and one
+// z-range, so the shuffles are always converged.  Arithmetic per cell is that of k_half_vec.
+template <bool SFORM, bool FROM_ZERO, int UPDATE, int ZC>
+__global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, const float *__restrict__ b,
+                                                    float *xv, int col, Upd up) {
+    const int hx = L.hx, kv = hx >> 2;
+    const int kvi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int yi = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = kvi < kv && yi < L.ny;
+    const int k0 = min(kvi, kv - 1) << 2;
+    const int y = min(yi, L.ny - 1);
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, L.nz);
+    const int lane = threadIdx.x & 31;
+    const i64 dy = hx, dz = (i64)L.ny * hx;
+    const bool hy0 = y > 0, hy1 = y < L.ny - 1;
+    const bool kl = k0 > 0, kr = k0 + 4 < hx;
+    i64 opp = (i64)(1 - col) * L.half + ((i64)z0 * L.ny + y) * hx + k0;
+    i64 own = (i64)col * L.half + ((i64)z0 * L.ny + y) * hx + k0;
+    const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
+    // planes z-1 and z of the other colour (x, and s in SFORM)
+    float4 xzm = f0, xzc = f0, szm = f0, szc = f0;
+    if (!FROM_ZERO) {
+        if (z0 > 0) xzm = ld(xv, opp - dz);
+        xzc = ld(xv, opp);
+    }
+    if (SFORM) {
+        if (z0 > 0) szm = ld(cf.s, opp - dz);
+        szc = ld(cf.s, opp);
+    }
+    const float hh = SFORM ? 2.f * h2 : h2;
+    for (int z = z0; z < z1; ++z) {
+        const bool hz0 = z > 0, hz1 = z < L.nz - 1;
+        const int p = (col + y + z) & 1;  // x = 2k + p
+        const bool xw0 = (p == 0 && !kl), xw1 = (p == 1 && !kr);
+        float4 xzp = f0, ym = f0, yp = f0;
+        if (!FROM_ZERO) {
+            if (hz1) xzp = ld(xv, opp + dz);
+            if (hy0) ym = ld(xv, opp - dy);
+            if (hy1) yp = ld(xv, opp + dy);
+        }
+        float w0[4], w1[4], w2[4], w3[4], w4[4], w5[4];
+        float4 szp = f0;
+        if (SFORM) {
+            float4 s2 = f0, s3 = f0;
+            if (hz1) szp = ld(cf.s, opp + dz);
+            if (hy0) s2 = ld(cf.s, opp - dy);
+            if (hy1) s3 = ld(cf.s, opp + dy);
+            const float4 sc4 = ld(cf.s, own);
+            float sl = __shfl_up_sync(0xffffffffu, szc.w, 1), sr = __shfl_down_sync(0xffffffffu, szc.x, 1);
+            if (lane == 0) sl = kl ? cf.s[opp - 1] : 0.f;
+            if (lane == 31) sr = kr ? cf.s[opp + 4] : 0.f;
+            const float so[4] = {szc.x, szc.y, szc.z, szc.w}, sc[4] = {sc4.x, sc4.y, sc4.z, sc4.w};
+            const float s2v[4] = {s2.x, s2.y, s2.z, s2.w}, s3v[4] = {s3.x, s3.y, s3.z, s3.w};
+            const float s4v[4] = {szm.x, szm.y, szm.z, szm.w}, s5v[4] = {szp.x, szp.y, szp.z, szp.w};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float sm = p ? so[v] : (v ? so[v - 1] : sl);
+                const float sp = p ? (v < 3 ? so[v + 1] : sr) : so[v];
+                w0[v] = (v == 0 && xw0) ? 0.f : sc[v] + sm;
+                w1[v] = (v == 3 && xw1) ? 0.f : sc[v] + sp;
+                w2[v] = hy0 ? sc[v] + s2v[v] : 0.f;
+                w3[v] = hy1 ? sc[v] + s3v[v] : 0.f;
+                w4[v] = hz0 ? sc[v] + s4v[v] : 0.f;
+                w5[v] = hz1 ? sc[v] + s5v[v] : 0.f;
+            }
+        } else {
+            const float4 fo = ld(cf.fx, opp);  // low x faces of the other colour = high faces of own
+            float fr = __shfl_down_sync(0xffffffffu, fo.x, 1);
+            if (lane == 31) fr = kr ? cf.fx[opp + 4] : 0.f;
+            const float fov[4] = {fo.x, fo.y, fo.z, fo.w};
+            const float4 a0 = ld(cf.fx, own), a2 = ld(cf.fy, own), a4 = ld(cf.fz, own);
+            const float4 a3 = hy1 ? ld(cf.fy, opp + dy) : f0, a5 = hz1 ? ld(cf.fz, opp + dz) : f0;
+            const float a0v[4] = {a0.x, a0.y, a0.z, a0.w}, a2v[4] = {a2.x, a2.y, a2.z, a2.w};
+            const float a3v[4] = {a3.x, a3.y, a3.z, a3.w}, a4v[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float a5v[4] = {a5.x, a5.y, a5.z, a5.w};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                w0[v] = a0v[v];
+                w1[v] = (v == 3 && xw1) ? 0.f : (p ? (v < 3 ? fov[v + 1] : fr) : fov[v]);
+                w2[v] = a2v[v];
+                w3[v] = a3v[v];
+                w4[v] = a4v[v];
+                w5[v] = a5v[v];
+            }
+        }
+        const float4 b4 = ld(b, own);
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+        float out[4];
+        if (FROM_ZERO) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float den = ((w0[v] + w1[v]) + (w2[v] + w3[v])) + (w4[v] + w5[v]);
+                out[v] = __fdividef(hh * bv[v], den);
+            }
+        } else {
+            float xl = __shfl_up_sync(0xffffffffu, xzc.w, 1), xr = __shfl_down_sync(0xffffffffu, xzc.x, 1);
+            if (lane == 0) xl = kl ? xv[opp - 1] : 0.f;
+            if (lane == 31) xr = kr ? xv[opp + 4] : 0.f;
+            const float xo[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
+            const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+            const float zmv[4] = {xzm.x, xzm.y, xzm.z, xzm.w}, zpv[4] = {xzp.x, xzp.y, xzp.z, xzp.w};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float xm = p ? xo[v] : (v ? xo[v - 1] : xl);
+                const float xp = (v == 3 && xw1) ? 0.f : (p ? (v < 3 ? xo[v + 1] : xr) : xo[v]);
+                float num = w0[v] * xm;
+                num += w1[v] * xp;
+                num += w2[v] * ymv[v];
+                num += w3[v] * ypv[v];
+                num += w4[v] * zmv[v];
+                num += w5[v] * zpv[v];
+                const float den = ((w0[v] + w1[v]) + (w2[v] + w3[v])) + (w4[v] + w5[v]);
+                out[v] = __fdividef(hh * bv[v] + num, den);
+            }
+        }
+        if (active) {
+            if (UPDATE == 0) {
+                *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+            } else {
+                // red at x = 2k + p, black at x = 2k + 1 - p; the black values are xzc
+                const float bk[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
+                const i64 nat = ((i64)z * L.ny + y) * L.nx + 2 * k0;
+                if (UPDATE == 2) {
+                    const float al = (float)up.alpha, sh = (float)up.shift;
+                    float2 *pr = up.p2 + nat;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float4 pv = *reinterpret_cast<const float4 *>(pr + 2 * v);  // (h0, l0, h1, l1)
+                        const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
+                        df_add(pv.x, pv.y, fmaf(al, e0, -sh));
+                        df_add(pv.z, pv.w, fmaf(al, e1, -sh));
+                        *reinterpret_cast<float4 *>(pr + 2 * v) = pv;
+                    }
+                } else {
+                    double *pr = up.p + nat;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const double2 pv = *reinterpret_cast<const double2 *>(pr + 2 * v);
+                        const double er = widen(out[v]), eb = widen(bk[v]);
+                        const double e0 = p ? eb : er, e1 = p ? er : eb;
+                        *reinterpret_cast<double2 *>(pr + 2 * v) = make_double2(
+                            fma(up.alpha, e0, pv.x - up.shift), fma(up.alpha, e1, pv.y - up.shift));
+                    }
+                }
+            }
+        }
+        xzm = xzc;
+        xzc = xzp;
+        szm = szc;
+        szc = szp;
+        own += dz;
+        opp += dz;
+    }
+}
+
+constexpr int kZChunk = 16;
+
+bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
+
+template <bool SFORM, bool FROM_ZERO, int UPDATE>
+void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
+                const Upd &up) {
+    const int kv = L.hx / 4;
+    const int vb = (kv % 64 == 0) ? 64 : 32;  // lanes per row
+    const int ry = 64 / vb;                    // rows per block
+    const dim3 blk(vb, ry), grd((kv + vb - 1) / vb, (L.ny + ry - 1) / ry, (L.nz + kZChunk - 1) / kZChunk);
+    k_half_z<SFORM, FROM_ZERO, UPDATE, kZChunk><<<grd, blk, 0, s>>>(L, h2, cf, b, x, col, up);
+}
+
 // ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
 // The red children of coarse cell (I, J, K) are the red cells at k = I of the 4 fine rows
 // (2J + b, 2K + c); one thread handles coarse cells I0..I0+3 of one coarse row.
@@ -539,12 +715,17 @@ __global__ void k_pack64(Lay L, const double *__restrict__ nat, float *st) {
     const i64 row = t / L.nx;
     st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = (float)nat[t];
 }
-__global__ void k_pack_inv64(Lay L, const double *__restrict__ rho, float *st) {
+// s = 1/rho: FP32 in the level's layout, and optionally as a double-float pair (hi, lo) in the
+// natural layout for the double-float outer residual
+__global__ void k_pack_inv64(Lay L, const double *__restrict__ rho, float *st, float2 *s2) {
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.n) return;
     const int x = (int)(t % L.nx);
     const i64 row = t / L.nx;
-    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = (float)(1.0 / rho[t]);
+    const double v = 1.0 / rho[t];
+    const float hi = (float)v;
+    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = hi;
+    if (s2) s2[t] = make_float2(hi, (float)(v - (double)hi));
 }
 
 }  // namespace
@@ -565,7 +746,15 @@ void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const fl
                    const float *fz, const float *b, float *x, int col, bool from_zero) {
     Coef32 cf{sinv, fx, fy, fz};
     count_launch();
-    if (L.split && L.hx % 4 == 0) {
+    if (half_z_ok(L)) {
+        if (sinv) {
+            if (from_zero) run_half_z<true, true, 0>(s, L, (float)h2, cf, b, x, col, Upd{});
+            else run_half_z<true, false, 0>(s, L, (float)h2, cf, b, x, col, Upd{});
+        } else {
+            if (from_zero) run_half_z<false, true, 0>(s, L, (float)h2, cf, b, x, col, Upd{});
+            else run_half_z<false, false, 0>(s, L, (float)h2, cf, b, x, col, Upd{});
+        }
+    } else if (L.split && L.hx % 4 == 0) {
         const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
         if (sinv) {
             if (from_zero) k_half_vec<true, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, x, col);
@@ -590,6 +779,16 @@ void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, c
     count_launch();
     const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
     float *xv = const_cast<float *>(x);  // read only in the UPDATE variants
+    if (half_z_ok(L)) {
+        if (p2) {
+            if (sinv) run_half_z<true, false, 2>(s, L, (float)h2, cf, b, xv, 0, up);
+            else run_half_z<false, false, 2>(s, L, (float)h2, cf, b, xv, 0, up);
+        } else {
+            if (sinv) run_half_z<true, false, 1>(s, L, (float)h2, cf, b, xv, 0, up);
+            else run_half_z<false, false, 1>(s, L, (float)h2, cf, b, xv, 0, up);
+        }
+        return;
+    }
     if (p2) {
         if (sinv) k_half_vec<true, false, 2><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
         else k_half_vec<false, false, 2><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
@@ -647,9 +846,9 @@ void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st) {
     count_launch();
     k_pack64<<<blocks_for(L.n), kThreads, 0, s>>>(L, nat, st);
 }
-void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st) {
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st, float2 *s2) {
     count_launch();
-    k_pack_inv64<<<blocks_for(L.n), kThreads, 0, s>>>(L, rho, st);
+    k_pack_inv64<<<blocks_for(L.n), kThreads, 0, s>>>(L, rho, st, s2);
 }
 
 }  // namespace mg

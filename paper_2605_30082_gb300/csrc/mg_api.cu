@@ -31,6 +31,7 @@ struct Level {
     double *fx64, *fy64, *fz64, *invd64;
     double *d64;            // level 0: sum of the interior face coefficients (FP64 residual)
     float2 *fx2, *fy2, *fz2, *d2;  // MIXED_DF, level 0: coefficients and diagonal as FP32 pairs
+    float2 *s2;                    // MIXED_DF, level 0: 1/rho as FP32 pairs (operator from a density)
     float *fx32, *fy32, *fz32;
     double *x64, *b64;      // FP64 path: iterate and RHS, levels >= 1
     float *x32, *b32;       // MIXED inner cycle, all levels (level 0: e and the scaled r)
@@ -357,7 +358,10 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         }
         auto residual = [&](bool write32) -> int {
             prof_begin(h, MG_PROF_FINE_RESIDUAL);
-            if (df)
+            if (df && h->sform0)
+                mg::launch_resid_dfs(s, F.d, F.lay, F.s2, h->bt2, h->p2, write32 ? F.b32 : nullptr,
+                                     (float)(F.ih2 * scale), h->partials, h->red + 6);
+            else if (df)
                 mg::launch_resid_df(s, F.d, F.lay, F.fx2, F.fy2, F.fz2, F.d2, h->bt2, h->p2,
                                     write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
             else
@@ -533,6 +537,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
                 add((void **)&L.fy2, 8 * n);
                 add((void **)&L.fz2, 8 * n);
                 add((void **)&L.d2, 8 * n);
+                add((void **)&L.s2, 8 * n);
             }
         } else if (l > 0) {
             add((void **)&L.x64, 8 * n);
@@ -626,7 +631,7 @@ int mg_set_density(mg_handle *h, const double *rho) {
     Level &F = h->lv[0];
     mg::launch_faces_from_rho(h->s, F.d, rho, F.fx64, F.fy64, F.fz64, h->err);
     h->sform0 = h->o.precision != MG_FP64;
-    if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, rho, F.s32);
+    if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, rho, F.s32, h->o.precision == MG_MIXED_DF ? F.s2 : nullptr);
     return finish_operator(h);
 }
 

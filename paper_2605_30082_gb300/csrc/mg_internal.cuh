@@ -108,6 +108,9 @@ void launch_join(cudaStream_t s, i64 n, const float2 *src, double *dst);    // v
 void launch_resid_df(cudaStream_t s, Dims d, Lay L, const float2 *fx, const float2 *fy, const float2 *fz,
                      const float2 *diag, const float2 *b, const float2 *p, float *r32, float s32,
                      double *partials, double *out);
+// s-form double-float residual: s2 = 1/rho as FP32 pairs (natural layout), otherwise as launch_resid_df
+void launch_resid_dfs(cudaStream_t s, Dims d, Lay L, const float2 *s2, const float2 *b, const float2 *p,
+                      float *r32, float s32, double *partials, double *out);
 void launch_update_df(cudaStream_t s, Dims d, Lay L, float2 *p, const float *e32, double alpha, double shift);
 // r = b - A x (or r = A x when apply_only)
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
@@ -122,7 +125,7 @@ void launch_coarse_matvec32(cudaStream_t s, Lay L, const double *pinv, const flo
 void launch_pack32(cudaStream_t s, Lay L, const float *nat, float *st);
 void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat);
 void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st);
-void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st);
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st, float2 *s2);
 // FP64 red-black half sweep of one colour, in place
 void launch_rbgs_half64(cudaStream_t s, Dims d, double h2, Coef<double> c, const double *b, double *p,
                         int colour);

@@ -20,6 +20,9 @@ from _helpers import RHO_PHASE, dev, dropfilm_case, host, random_rho, rel
 pytestmark = pytest.mark.gpu
 
 DIMS = [(72, 40, 24), (40, 24, 56), (32, 32, 32)]
+# rows of >= 128 four-cell vectors per colour take the z-marching half sweep: 64 and 48 vectors
+# per row (a half-idle second block), z-chunks of 16 with a ragged last chunk, odd coarse dims
+WIDE = [(256, 12, 20), (384, 4, 36)]
 TOL = {torch.float64: 1e-13, torch.float32: 2e-6}
 
 
@@ -95,7 +98,7 @@ def test_csf_faces_and_rhs_match_oracle():
     assert rel(host(b2), want) < 1e-14
 
 
-@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dims", DIMS + WIDE)
 @pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
 def test_apply_smooth_residual_match_oracle(dims, dtype, coeffs):
     s, M = make(dims, "fp64" if dtype == torch.float64 else "mixed", coeffs=coeffs)
@@ -206,7 +209,7 @@ def test_density_errors_are_reported_not_faulted():
     s.solve(dev(rnd((n, n, n), 1)))
 
 
-@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dims", DIMS + WIDE)
 @pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
 @pytest.mark.parametrize("sweeps,zero", [(0, False), (1, True), (2, True), (2, False), (3, False)])
 def test_fused_presmooth_restrict_matches_oracle(dims, dtype, coeffs, sweeps, zero):
@@ -234,7 +237,7 @@ def test_fused_presmooth_restrict_matches_oracle(dims, dtype, coeffs, sweeps, ze
         assert rel(host(bc), O.restrict(O.residual(faces, b, xs, H))) < (1e-12 if dtype == torch.float64 else 2e-5)
 
 
-@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dims", DIMS + WIDE)
 @pytest.mark.parametrize("dtype,coeffs", [(torch.float64, "rho"), (torch.float32, "rho"), (torch.float32, "faces")])
 @pytest.mark.parametrize("prolong", ["trilinear", "constant"])
 @pytest.mark.parametrize("sweeps", [0, 1, 2, 3])

@@ -55,7 +55,7 @@ def test_solution_matches_exact_32cubed(c32, prec):
     assert abs(s.last_stats.cycles - nc_o) <= 2
 
 
-@pytest.mark.parametrize("dims", [(64, 64, 64), (64, 48, 32), (96, 40, 24)])
+@pytest.mark.parametrize("dims", [(64, 64, 64), (64, 48, 32), (96, 40, 24), (256, 16, 24), (384, 4, 36)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 def test_ragged_grids_match_exact(dims, prec):
     nx, ny, nz = dims
@@ -117,15 +117,22 @@ def test_edge_cases():
     assert ei.value.code == MG_ERR_ARG
 
 
-def test_mixed_df_matches_mixed_and_needs_even_nx():
-    """The double-float outer loop reaches the same discrete solution as the FP64 one."""
+@pytest.mark.parametrize("coeffs", ["rho", "faces"])
+def test_mixed_df_matches_mixed_and_needs_even_nx(coeffs):
+    """The double-float outer loop reaches the same discrete solution as the FP64 one.
+
+    coeffs="rho": the residual forms beta = (s_c + s_nb) / 2 from s = 1/rho in double-float;
+    "faces": it reads the face coefficients and the diagonal as double-float pairs."""
     dims = (48, 32, 40)
     rho = random_rho(dims, 12)
     b = np.random.default_rng(8).standard_normal((40, 32, 48))
     ps = {}
     for prec in ("mixed", "mixed_df"):
         s = Solver(dims, h=1 / 48, precision=prec, coarsest=8, rtol=1e-12, max_cycles=400)
-        s.set_density(dev(rho))
+        if coeffs == "rho":
+            s.set_density(dev(rho))
+        else:
+            s.set_face_coeffs(*(dev(f) for f in O.faces_from_density(rho)))
         ps[prec] = host(s.solve(dev(b)))
         assert s.last_stats.relres <= 1e-12
     assert rel(ps["mixed_df"], ps["mixed"]) < 1e-10
