@@ -126,6 +126,26 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// FP64 -> FP32 rounded to nearest, ties to even, with integer operations on the IEEE-754
+// fields: the 29 dropped fraction bits decide the rounding; a carry out of the fraction
+// increments the exponent (up to infinity).  Results below the FP32 normal range become
+// (signed) zero; NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((u << 12) != 0ull) ? 0x400000u : 0u));
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) return __uint_as_float(sign);
+    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const unsigned rest = (unsigned)(u & 0x1fffffffull);  // the 29 dropped bits
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
+    const unsigned mag = ((unsigned)e32 << 23) + frac + up;  // a carry moves into the exponent
+    return __uint_as_float(sign | (mag >= 0x7f800000u ? 0x7f800000u : mag));
+}
+
 // h^2 r = h^2 b - (d p_c - sum_f beta_f p_nb), d = sum_f beta_f: 7 FP64 fused multiply-adds
 // per cell when b arrives already scaled by h^2 (SCALED), one more multiply otherwise.
 // partials: (sum (h^2 r)^2 and sum p, each accumulated in FP32 per thread); r32 = s32 * h^2 r.
@@ -253,12 +273,15 @@ __global__ void k_fine_residual(Dims d, Lay L, double ih2, const double *__restr
 }
 
 // p = (p - shift) + alpha e: 2 FP64 operations, the FP32 value widened exactly with integer operations
-__global__ void k_update(Dims d, Lay L, double *p, const float *__restrict__ e, double alpha, double shift) {
+__global__ void k_update(Dims d, Lay L, double *p, const float *__restrict__ e, float alpha, float shift) {
     const i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= d.n) return;
     const int i = (int)(m % d.nx);
     const i64 row = m / d.nx;
-    p[m] = fma(alpha, f2d_exact(e[sto(L, i, (int)(row % d.ny), (int)(row / d.ny))]), p[m] - shift);
+    // the correction alpha e - shift is formed in FP32 (e is an FP32 V-cycle result; the outer
+    // loop corrects its rounding), the update itself is one FP64 addition
+    const float c = fmaf(alpha, e[sto(L, i, (int)(row % d.ny), (int)(row / d.ny))], -shift);
+    p[m] += f2d_exact(c);
 }
 
 __global__ void k_add_const(i64 n, double *p, double c) {
@@ -267,53 +290,63 @@ __global__ void k_add_const(i64 n, double *p, double c) {
 }
 
 // dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R) ih2 + sigma csf_f (lam_L - lam_R) ih on the low
-// faces of each cell (walls 0); partial sums of beta_f csf_f (lam_L - lam_R) ih (= dL/dsigma)
-__global__ void k_adjoint_grad(Dims d, double ih, double ih2, const double *__restrict__ lam,
+// faces of each cell (walls 0); partial sums of beta_f csf_f (lam_L - lam_R) ih (= dL/dsigma).
+// Blocks take whole rows (no 64-bit division per cell).  The differences of lambda and p are
+// formed in FP64 (they cancel); their product, an FP32 output, is formed in FP32 from the
+// differences rounded to nearest.  dL/dsigma is summed in FP64.
+__global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const double *__restrict__ lam,
                                const double *__restrict__ p, const double *__restrict__ fx,
                                const double *__restrict__ fy, const double *__restrict__ fz,
                                const double *__restrict__ csx, const double *__restrict__ csy,
-                               const double *__restrict__ csz, double sigma, float *gx, float *gy,
+                               const double *__restrict__ csz, float sigma, float *gx, float *gy,
                                float *gz, double *partials) {
     double ds = 0.0;
-    for (i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x; c < d.n; c += (i64)gridDim.x * blockDim.x) {
-        int i = (int)(c % d.nx);
-        i64 row = c / d.nx;
-        int j = (int)(row % d.ny), k = (int)(row / d.ny);
-        i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
-        i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
-        double lc = lam[c], pc = p[c];
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-        if (i > 0) {
-            double dl = lam[c - 1] - lc;
-            g0 = -dl * (p[c - 1] - pc) * ih2;
-            if (csx) {
-                g0 += sigma * csx[ax] * dl * ih;
-                ds += fx[c] * csx[ax] * dl * ih;
+    const int nx = d.nx, ny = d.ny;
+    const i64 nxy = d.nxy, rows = (i64)ny * d.nz;
+    for (i64 row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const i64 c0 = row * nx;
+        const i64 ax0 = row * (nx + 1);                        // x faces: (nz, ny, nx + 1)
+        const i64 ay0 = ((i64)k * (ny + 1) + j) * nx;          // y faces: (nz, ny + 1, nx)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const i64 c = c0 + i;
+            const double lc = lam[c], pc = p[c];
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            if (i > 0) {
+                const double dl = lam[c - 1] - lc;
+                const float dlf = d2f_rn(dl);
+                g0 = -dlf * d2f_rn(p[c - 1] - pc) * ih2;
+                if (csx) {
+                    g0 = fmaf(sigma * d2f_rn(csx[ax0 + i]) * ih, dlf, g0);
+                    ds += fx[c] * csx[ax0 + i] * dl * ihd;
+                }
             }
-        }
-        if (j > 0) {
-            double dl = lam[c - d.nx] - lc;
-            g1 = -dl * (p[c - d.nx] - pc) * ih2;
-            if (csy) {
-                g1 += sigma * csy[ay] * dl * ih;
-                ds += fy[c] * csy[ay] * dl * ih;
+            if (j > 0) {
+                const double dl = lam[c - nx] - lc;
+                const float dlf = d2f_rn(dl);
+                g1 = -dlf * d2f_rn(p[c - nx] - pc) * ih2;
+                if (csy) {
+                    g1 = fmaf(sigma * d2f_rn(csy[ay0 + i]) * ih, dlf, g1);
+                    ds += fy[c] * csy[ay0 + i] * dl * ihd;
+                }
             }
-        }
-        if (k > 0) {
-            double dl = lam[c - d.nxy] - lc;
-            g2 = -dl * (p[c - d.nxy] - pc) * ih2;
-            if (csz) {
-                g2 += sigma * csz[c] * dl * ih;
-                ds += fz[c] * csz[c] * dl * ih;
+            if (k > 0) {
+                const double dl = lam[c - nxy] - lc;
+                const float dlf = d2f_rn(dl);
+                g2 = -dlf * d2f_rn(p[c - nxy] - pc) * ih2;
+                if (csz) {
+                    g2 = fmaf(sigma * d2f_rn(csz[c]) * ih, dlf, g2);
+                    ds += fz[c] * csz[c] * dl * ihd;
+                }
             }
-        }
-        if (gx) {
-            gx[ax] = (float)g0;
-            gy[ay] = (float)g1;
-            gz[c] = (float)g2;
-            if (i == d.nx - 1) gx[ax + 1] = 0.f;
-            if (j == d.ny - 1) gy[ay + d.nx] = 0.f;
-            if (k == d.nz - 1) gz[c + d.nxy] = 0.f;
+            if (gx) {
+                gx[ax0 + i] = g0;
+                gy[ay0 + i] = g1;
+                gz[c] = g2;
+                if (i == nx - 1) gx[ax0 + nx] = 0.f;
+                if (j == ny - 1) gy[ay0 + i + nx] = 0.f;
+                if (k == d.nz - 1) gz[c + nxy] = 0.f;
+            }
         }
     }
     block_sum2(ds, 0.0, partials + 2 * blockIdx.x);
@@ -373,7 +406,7 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
 
 void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift) {
     count_launch();
-    k_update<<<blocks_for(d.n), kThreads, 0, s>>>(d, L, p, e32, alpha, shift);
+    k_update<<<blocks_for(d.n), kThreads, 0, s>>>(d, L, p, e32, (float)alpha, (float)shift);
 }
 
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {
@@ -387,8 +420,11 @@ void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, co
                          float *gy, float *gz, double *partials, double *out) {
     int nb = reduce_blocks(d.n);
     count_launch();
-    k_adjoint_grad<<<nb, kReduceThreads, 0, s>>>(d, 1.0 / h, 1.0 / (h * h), lam, p, fx, fy, fz,
-                                                 csfx, csfy, csfz, sigma, gx, gy, gz, partials);
+    const i64 rows = (i64)d.ny * d.nz;
+    if (nb > rows) nb = (int)rows;
+    k_adjoint_grad<<<nb, kReduceThreads, 0, s>>>(d, (float)(1.0 / h), (float)(1.0 / (h * h)), 1.0 / h, lam, p,
+                                                 fx, fy, fz, csfx, csfy, csfz, (float)sigma, gx, gy, gz,
+                                                 partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }

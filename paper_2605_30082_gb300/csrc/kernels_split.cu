@@ -115,8 +115,8 @@ __device__ __forceinline__ double widen(float f) {
 struct Upd {
     double *p;      // natural FP64 solution of the finest level (UPDATE 1)
     float2 *p2;     // natural double-float solution of the finest level (UPDATE 2)
-    double alpha;   // scale of the correction
-    double shift;   // gauge shift
+    float alpha;    // scale of the correction, rounded to FP32 on the host
+    float shift;    // gauge shift, rounded to FP32 on the host (no FP64 conversion on the device)
 };
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
@@ -238,11 +238,14 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
     } else if (UPDATE == 2) {
         const float4 blk = *reinterpret_cast<const float4 *>(xv + opp);
         const float bk[4] = {blk.x, blk.y, blk.z, blk.w};
-        const float al = (float)up.alpha, sh = (float)up.shift;
+        const float al = up.alpha, sh = up.shift;
         float2 *pr = up.p2 + row * L.nx + 2 * k0;
+        float4 pvs[4];  // all loads before the first store
+#pragma unroll
+        for (int v = 0; v < 4; ++v) pvs[v] = *reinterpret_cast<const float4 *>(pr + 2 * v);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            float4 pv = *reinterpret_cast<const float4 *>(pr + 2 * v);  // (h0, l0, h1, l1)
+            float4 pv = pvs[v];  // (h0, l0, h1, l1)
             const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
             df_add(pv.x, pv.y, fmaf(al, e0, -sh));
             df_add(pv.z, pv.w, fmaf(al, e1, -sh));
@@ -252,14 +255,17 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
         // red at x = 2k + p, black at x = 2k + 1 - p; same-row black values O[k0..k0+3]
         const float4 blk = *reinterpret_cast<const float4 *>(xv + opp);
         const float bk[4] = {blk.x, blk.y, blk.z, blk.w};
+        const float al = up.alpha, sh = up.shift;
         double *pr = up.p + row * L.nx + 2 * k0;
+        double2 pvs[4];  // all loads before the first store
+#pragma unroll
+        for (int v = 0; v < 4; ++v) pvs[v] = *reinterpret_cast<const double2 *>(pr + 2 * v);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const double2 pv = *reinterpret_cast<const double2 *>(pr + 2 * v);
-            const double er = widen(out[v]), eb = widen(bk[v]);
-            const double e0 = p ? eb : er, e1 = p ? er : eb;  // cells 2(k0+v) and 2(k0+v)+1
+            const double2 pv = pvs[v];
+            const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];  // cells 2(k0+v) and 2(k0+v)+1
             *reinterpret_cast<double2 *>(pr + 2 * v) =
-                make_double2(fma(up.alpha, e0, pv.x - up.shift), fma(up.alpha, e1, pv.y - up.shift));
+                make_double2(pv.x + widen(fmaf(al, e0, -sh)), pv.y + widen(fmaf(al, e1, -sh)));
         }
     }
 }
@@ -394,25 +400,34 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
                 const float bk[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
                 const i64 nat = ((i64)z * L.ny + y) * L.nx + 2 * k0;
                 if (UPDATE == 2) {
-                    const float al = (float)up.alpha, sh = (float)up.shift;
+                    const float al = up.alpha, sh = up.shift;
                     float2 *pr = up.p2 + nat;
+                    // all loads before the first store: otherwise the four read-modify-writes
+                    // of the same row run one HBM round trip after another
+                    float4 pvs[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) pvs[v] = *reinterpret_cast<const float4 *>(pr + 2 * v);  // (h0, l0, h1, l1)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        float4 pv = *reinterpret_cast<const float4 *>(pr + 2 * v);  // (h0, l0, h1, l1)
+                        float4 pv = pvs[v];
                         const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
                         df_add(pv.x, pv.y, fmaf(al, e0, -sh));
                         df_add(pv.z, pv.w, fmaf(al, e1, -sh));
                         *reinterpret_cast<float4 *>(pr + 2 * v) = pv;
                     }
                 } else {
+                    // FP32 correction alpha e - shift, one FP64 addition per cell
+                    const float al = up.alpha, sh = up.shift;
                     double *pr = up.p + nat;
+                    double2 pvs[4];  // all loads before the first store (see above)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) pvs[v] = *reinterpret_cast<const double2 *>(pr + 2 * v);
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const double2 pv = *reinterpret_cast<const double2 *>(pr + 2 * v);
-                        const double er = widen(out[v]), eb = widen(bk[v]);
-                        const double e0 = p ? eb : er, e1 = p ? er : eb;
-                        *reinterpret_cast<double2 *>(pr + 2 * v) = make_double2(
-                            fma(up.alpha, e0, pv.x - up.shift), fma(up.alpha, e1, pv.y - up.shift));
+                        const double2 pv = pvs[v];
+                        const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
+                        *reinterpret_cast<double2 *>(pr + 2 * v) =
+                            make_double2(pv.x + widen(fmaf(al, e0, -sh)), pv.y + widen(fmaf(al, e1, -sh)));
                     }
                 }
             }
@@ -426,18 +441,22 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
     }
 }
 
-constexpr int kZChunk = 16;
-
 bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
 
+// 16 planes per thread where that still gives about 4 waves of 64-thread blocks (12 resident
+// per SM on 152 SMs), else 4
 template <bool SFORM, bool FROM_ZERO, int UPDATE>
 void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
                 const Upd &up) {
     const int kv = L.hx / 4;
     const int vb = (kv % 64 == 0) ? 64 : 32;  // lanes per row
     const int ry = 64 / vb;                    // rows per block
-    const dim3 blk(vb, ry), grd((kv + vb - 1) / vb, (L.ny + ry - 1) / ry, (L.nz + kZChunk - 1) / kZChunk);
-    k_half_z<SFORM, FROM_ZERO, UPDATE, kZChunk><<<grd, blk, 0, s>>>(L, h2, cf, b, x, col, up);
+    const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
+    const dim3 blk(vb, ry);
+    if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 12)
+        k_half_z<SFORM, FROM_ZERO, UPDATE, 16><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf, b, x, col, up);
+    else
+        k_half_z<SFORM, FROM_ZERO, UPDATE, 4><<<dim3(gx, gy, (L.nz + 3) / 4), blk, 0, s>>>(L, h2, cf, b, x, col, up);
 }
 
 // ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
@@ -591,6 +610,85 @@ __global__ void k_prolong_red_vec(Lay L, Lay Lc, const float *__restrict__ ec, f
         }
     }
     *reinterpret_cast<float4 *>(xv + row * hx + k0) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// ---- separable red-only trilinear prolongation (split fine level, coarse nx % 8 == 0) -----
+// One thread takes coarse row (J, K) and I0 = k0 .. k0+7: the 8 red cells k0 .. k0+7 of each of
+// the 4 fine rows y = 2J + d, z = 2K + e.  Fine row (d, e) interpolates in y and z first,
+//   R_de(I) = 9/16 c(J, K) + 3/16 c(J_d, K) + 3/16 c(J, K_e) + 1/16 c(J_d, K_e)
+// with J_d = J - 1 + 2d and K_e = K - 1 + 2e clamped into the grid (the wall mirror), then in x:
+// the red cell at k (x = 2k + p, coarse I = k) gains 3/4 R(I) + 1/4 R(I + 2p - 1), clamped.
+// Each coarse row supplies I = k0 - 1 .. k0 + 8: two float4 (even and odd I, one per colour
+// half) and two scalars.
+__global__ void k_prolong_red8(Lay L, Lay Lc, const float *__restrict__ ec, float *xv) {
+    const int hx = L.hx, kv = hx >> 3;  // 8-cell groups per fine row
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 crows = (i64)Lc.ny * Lc.nz;
+    if (t >= crows * kv) return;
+    const i64 crow = t / kv;
+    const int k0 = (int)(t - crow * kv) << 3;
+    const int J = (int)(crow % Lc.ny), K = (int)(crow / Lc.ny);
+    const int hxc = Lc.hx, ncx = Lc.nx;
+    const int Js[3] = {max(J - 1, 0), J, min(J + 1, Lc.ny - 1)};
+    const int Ks[3] = {max(K - 1, 0), K, min(K + 1, Lc.nz - 1)};
+    float R[4][10];  // [2e + d][I - k0 + 1]
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int u = 0; u < 10; ++u) R[r][u] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {      // coarse row J - 1 + a
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {  // coarse row K - 1 + c
+            const int JJ = Js[a], KK = Ks[c];
+            const int q = (JJ + KK) & 1;  // colour of coarse I even
+            const i64 rowc = (i64)KK * Lc.ny + JJ;
+            const float *ev = ec + (i64)q * Lc.half + rowc * hxc;        // even I, position I / 2
+            const float *od = ec + (i64)(1 - q) * Lc.half + rowc * hxc;  // odd I
+            const float4 e4 = *reinterpret_cast<const float4 *>(ev + (k0 >> 1));
+            const float4 o4 = *reinterpret_cast<const float4 *>(od + (k0 >> 1));
+            float v[10];
+            v[1] = e4.x; v[2] = o4.x; v[3] = e4.y; v[4] = o4.y;
+            v[5] = e4.z; v[6] = o4.z; v[7] = e4.w; v[8] = o4.w;
+            v[0] = k0 > 0 ? od[(k0 >> 1) - 1] : v[1];          // I = k0 - 1, mirrored at the wall
+            v[9] = k0 + 8 < ncx ? ev[(k0 >> 1) + 4] : v[8];    // I = k0 + 8
+            // weight of this coarse row in fine row (d, e): y factor (3/4 own, 1/4 neighbour)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    // fine row (d, e) uses coarse rows J and J_d = J - 1 + 2d, K and K_e = K - 1 + 2e
+                    const bool ya = (a == 1) || (a == 2 * d);
+                    const bool za = (c == 1) || (c == 2 * e);
+                    if (!ya || !za) continue;
+                    // when J_d was clamped onto J the two y weights land on the same row
+                    float wy = (a == 1) ? 0.75f : 0.25f;
+                    float wz = (c == 1) ? 0.75f : 0.25f;
+                    const float w = wy * wz;
+#pragma unroll
+                    for (int u = 0; u < 10; ++u) R[2 * e + d][u] = fmaf(w, v[u], R[2 * e + d][u]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const int y = 2 * J + d, z = 2 * K + e;
+            if (y >= L.ny || z >= L.nz) continue;
+            const int p = (d + e) & 1;  // red x = 2k + p
+            float *xr = xv + ((i64)z * L.ny + y) * hx + k0;
+            float4 a4 = *reinterpret_cast<const float4 *>(xr);
+            float4 b4 = *reinterpret_cast<const float4 *>(xr + 4);
+            float o[8] = {a4.x, a4.y, a4.z, a4.w, b4.x, b4.y, b4.z, b4.w};
+            const float *Rr = R[2 * e + d];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) o[v] += 0.75f * Rr[v + 1] + 0.25f * (p ? Rr[v + 2] : Rr[v]);
+            *reinterpret_cast<float4 *>(xr) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4 *>(xr + 4) = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
 }
 
 // ---- residual (generic) ------------------------------------------------------------------
@@ -775,7 +873,7 @@ void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, c
                           const float *fz, const float *b, const float *x, double *p, float2 *p2, double alpha,
                           double shift) {
     Coef32 cf{sinv, fx, fy, fz};
-    Upd up{p, p2, alpha, shift};
+    Upd up{p, p2, (float)alpha, (float)shift};
     count_launch();
     const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
     float *xv = const_cast<float *>(x);  // read only in the UPDATE variants
@@ -821,6 +919,12 @@ void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const fl
 
 void launch_prolong32(cudaStream_t s, Lay L, Lay Lc, const float *ec, float *x, int kind, int only_col) {
     count_launch();
+    if (only_col == 0 && kind == MG_PROLONG_TRILINEAR && L.split && Lc.split && Lc.nx % 8 == 0 &&
+        2 * Lc.nx == L.nx && 2 * Lc.ny == L.ny && 2 * Lc.nz == L.nz) {
+        const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 8);
+        k_prolong_red8<<<blocks_for(work), kThreads, 0, s>>>(L, Lc, ec, x);
+        return;
+    }
     if (only_col == 0 && L.split && L.hx % 4 == 0) {
         const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
         k_prolong_red_vec<<<blocks_for(work), kThreads, 0, s>>>(L, Lc, ec, x, kind);
