@@ -94,19 +94,27 @@ typedef struct {
     int coarsest;     /* stop coarsening once the largest dimension is <= this (>= 2) */
     int prolong;      /* MG_PROLONG_TRILINEAR or MG_PROLONG_CONSTANT */
     double rtol;      /* relative residual tolerance, |b~ - A p|_2 / |b~|_2 */
-    int max_cycles;   /* V-cycles (FP64) or outer iterations (MIXED), >= 0 */
+    int max_cycles;   /* V-cycles, >= 0 (the mixed modes stop before an outer iteration
+                         that would exceed it) */
     int warm_start;   /* 1: mg_solve starts from the p passed in; 0: from p = 0 */
+    int inner_cycles; /* mixed modes: FP32 V-cycles per outer iteration (1..8), the first from
+                         zero, the next ones continuing from the previous correction; the
+                         FP64 (or double-float) residual and update run once per outer
+                         iteration.  Must be 1 for MG_FP64. */
 } mg_opts;
 
 typedef struct {
     int status;                     /* same as the return value */
-    int cycles;                     /* V-cycles run (one per outer iteration in MIXED) */
+    int cycles;                     /* V-cycles run */
+    int outer;                      /* outer iterations (= cycles for MG_FP64 and for
+                                       inner_cycles 1) */
     double relres;                  /* final relative residual */
-    double relres_hist[MG_HIST_LEN];/* relres after c cycles, c = 0..min(cycles, HIST-1) */
+    double relres_hist[MG_HIST_LEN];/* relres after k outer iterations, k = 0..min(outer, HIST-1) */
     double ms;                      /* device time of the call (CUDA events) */
 } mg_stats;
 
-/* Defaults: 2/2 sweeps, coarsest 4, trilinear, rtol 1e-10, 200 cycles, FP64, cold start. */
+/* Defaults: 2/2 sweeps, coarsest 4, trilinear, rtol 1e-10, 200 cycles, FP64, cold start,
+   one V-cycle per outer iteration. */
 void mg_default_opts(mg_opts *opts);
 
 /* Create a solver for one grid.  `stream` is a cudaStream_t (NULL = legacy

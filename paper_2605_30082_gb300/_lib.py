@@ -37,15 +37,16 @@ class mg_opts(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
                 ("precision", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarsest", C.c_int), ("prolong", C.c_int), ("rtol", C.c_double),
-                ("max_cycles", C.c_int), ("warm_start", C.c_int)]
+                ("max_cycles", C.c_int), ("warm_start", C.c_int), ("inner_cycles", C.c_int)]
 
 
 class mg_stats(C.Structure):
-    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
+    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("outer", C.c_int), ("relres", C.c_double),
                 ("relres_hist", C.c_double * MG_HIST_LEN), ("ms", C.c_double)]
 
     def history(self):
-        return list(self.relres_hist[: min(self.cycles + 1, MG_HIST_LEN)])
+        """relres after each outer iteration (one per V-cycle unless inner_cycles > 1)."""
+        return list(self.relres_hist[: min(self.outer + 1, MG_HIST_LEN)])
 
 
 _lib = None

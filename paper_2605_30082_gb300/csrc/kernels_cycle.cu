@@ -1,8 +1,7 @@
-// Unfused V-cycle kernels on one level: the FP64 red-black half sweep,
-// operator application, residual, residual + 8:1 restriction, prolongation +
-// correction, and the dense coarse solve.  (The FP32 sweeps, with restriction
-// or prolongation fused in, are the z-marching passes of kernels_pass.cu.)  Templated on the level's element
-// type (double for the FP64 path, float for the inner cycle of MIXED).
+// V-cycle kernels of the FP64 path on one level (natural layout): the red-black half sweep,
+// operator application, residual, residual + 8:1 restriction, prolongation + correction,
+// and the dense coarse solve.  Templated on the element type; the FP32 inner cycle of the
+// mixed modes uses the colour-split kernels of kernels_split.cu instead.
 //
 // Operator (cell-centred, homogeneous Neumann walls):
 //   (A x)_c = ih2 * sum_{interior faces f of c} beta_f (x_c - x_nb(f))
@@ -149,6 +148,73 @@ __global__ void k_prolong(Dims cd, Dims f, const T *__restrict__ ec, T *e, int k
 }
 
 // e = pinv r, one warp per row, FP64 accumulation
+// Red-only residual + restriction in diagonal form on a level with the diagonal d = sum beta:
+//   h^2 r_c = h^2 b_c + sum_f beta_f x_nb - d_c x_c   (7 FMA and one multiply per red child),
+// coarse b = ih2/8 * (sum over the 4 red children).  Blocks take coarse rows (grid y, strided),
+// threads coarse I: no 64-bit division per cell.
+__global__ void k_rr_red_diag64(Dims f, Dims cd, double h2, double ih2_8, Coef<double> cf,
+                                const double *__restrict__ dg, const double *__restrict__ b,
+                                const double *__restrict__ x, double *bc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= cd.nx) return;
+    const i64 crows = (i64)cd.ny * cd.nz;
+    for (i64 cr = blockIdx.y; cr < crows; cr += gridDim.y) {
+        const int J = (int)(cr % cd.ny), K = (int)(cr / cd.ny);
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 2 * J + (q & 1), k = 2 * K + (q >> 1);
+            const int i = 2 * I + ((j + k) & 1);  // the red child in this fine row
+            const i64 c = ((i64)k * f.ny + j) * f.nx + i;
+            double a = h2 * b[c];
+            if (i > 0) a = fma(cf.fx[c], x[c - 1], a);
+            if (i < f.nx - 1) a = fma(cf.fx[c + 1], x[c + 1], a);
+            if (j > 0) a = fma(cf.fy[c], x[c - f.nx], a);
+            if (j < f.ny - 1) a = fma(cf.fy[c + f.nx], x[c + f.nx], a);
+            if (k > 0) a = fma(cf.fz[c], x[c - f.nxy], a);
+            if (k < f.nz - 1) a = fma(cf.fz[c + f.nxy], x[c + f.nxy], a);
+            s += fma(-dg[c], x[c], a);
+        }
+        bc[(i64)cr * cd.nx + I] = s * ih2_8;
+    }
+}
+
+// x += P ec on the cells of one colour only; threads take the cells of that colour in a row
+// (grid x), blocks strided rows (grid y)
+template <typename T>
+__global__ void k_prolong_col(Dims cd, Dims f, const T *__restrict__ ec, T *e, int kind, int col) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 rows = (i64)f.ny * f.nz;
+    for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = (int)(row % f.ny), k = (int)(row / f.ny);
+        const int i = 2 * m + ((col + j + k) & 1);
+        if (i >= f.nx) continue;
+        const int I = i >> 1, J = j >> 1, K = k >> 1;
+        T v;
+        if (kind == MG_PROLONG_CONSTANT) {
+            v = ec[((i64)K * cd.ny + J) * cd.nx + I];
+        } else {
+            int I2 = (i & 1) ? I + 1 : I - 1;
+            int J2 = (j & 1) ? J + 1 : J - 1;
+            int K2 = (k & 1) ? K + 1 : K - 1;
+            if (I2 < 0 || I2 >= cd.nx) I2 = I;
+            if (J2 < 0 || J2 >= cd.ny) J2 = J;
+            if (K2 < 0 || K2 >= cd.nz) K2 = K;
+            const T w[2] = {T(0.75), T(0.25)};
+            const int Ii[2] = {I, I2}, Jj[2] = {J, J2}, Kk[2] = {K, K2};
+            v = T(0);
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                    for (int aa = 0; aa < 2; ++aa)
+                        v += w[aa] * w[bb] * w[cc] * ec[((i64)Kk[cc] * cd.ny + Jj[bb]) * cd.nx + Ii[aa]];
+        }
+        e[row * f.nx + i] += v;
+    }
+}
+
 template <typename T>
 __global__ void k_coarse_matvec(int nc, const double *__restrict__ pinv, const T *__restrict__ r,
                                 T *e) {
@@ -196,7 +262,24 @@ template <typename T>
 void launch_prolong(cudaStream_t s, Dims coarse, const T *ec, T *e, int kind, int only_col) {
     Dims f = make_dims(coarse.nx * 2, coarse.ny * 2, coarse.nz * 2);
     count_launch();
+    if (only_col >= 0) {
+        const unsigned gx = (unsigned)(((f.nx + 1) / 2 + 127) / 128);
+        const i64 rows = (i64)f.ny * f.nz;
+        const unsigned gy = (unsigned)(rows < 65535 ? rows : 65535);
+        k_prolong_col<T><<<dim3(gx, gy), 128, 0, s>>>(coarse, f, ec, e, kind, only_col);
+        return;
+    }
     k_prolong<T><<<blocks_for(f.n), kThreads, 0, s>>>(coarse, f, ec, e, kind, only_col);
+}
+
+void launch_rr_red_diag64(cudaStream_t s, Dims fine, double h2, Coef<double> c, const double *dg,
+                          const double *b, const double *x, double *bc) {
+    Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
+    count_launch();
+    const unsigned gx = (unsigned)((cd.nx + 127) / 128);
+    const i64 crows = (i64)cd.ny * cd.nz;
+    const unsigned gy = (unsigned)(crows < 65535 ? crows : 65535);
+    k_rr_red_diag64<<<dim3(gx, gy), 128, 0, s>>>(fine, cd, h2, 1.0 / (8.0 * h2), c, dg, b, x, bc);
 }
 
 template <typename T>

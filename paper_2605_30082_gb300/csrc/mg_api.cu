@@ -162,7 +162,10 @@ void presmooth_restrict64(mg_handle *h, int l, const double *b, double *x, doubl
     smooth64(h, l, x, b, sweeps, 0);
     if (l == 0) prof_begin(h, MG_PROF_RESID_RESTRICT);
     // after a pre-smoothing sweep (black last) every black residual is zero
-    mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), b, x, bc, sweeps > 0);
+    if (sweeps > 0 && L.d64)
+        mg::launch_rr_red_diag64(h->s, L.d, L.h2, coef<double>(L), L.d64, b, x, bc);
+    else
+        mg::launch_resid_restrict<double>(h->s, L.d, L.ih2, coef<double>(L), b, x, bc, sweeps > 0);
     if (l == 0) prof_end(h);
 }
 
@@ -247,9 +250,10 @@ void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, 
     prof_end(h);
 }
 
-// one V-cycle on level l for A x = b from x = 0; result in x (or, with `up` on level 0,
-// added to the FP64 solution by the last half sweep)
-void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *up = nullptr) {
+// one V-cycle on level l for A x = b from x = 0 (or, with from_zero false, from the x passed
+// in); result in x (or, with `up` on level 0, added to the FP64 solution by the last half sweep)
+void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *up = nullptr,
+              bool from_zero = true) {
     Level &L = h->lv[l];
     if (l == h->nlev - 1) {
         if (l == 0) prof_begin(h, MG_PROF_COARSE);
@@ -258,7 +262,7 @@ void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *
         return;
     }
     Level &C = h->lv[l + 1];
-    presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, true);
+    presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, from_zero);
     vcycle32(h, l + 1, C.b32, C.x32);
     prolong_postsmooth32(h, l, b, C.x32, x, h->o.post, up);
 }
@@ -273,7 +277,7 @@ int finish_operator(mg_handle *h) {
     bool mixed = h->o.precision != MG_FP64;
     for (int l = 0; l < h->nlev; ++l) {
         Level &L = h->lv[l];
-        mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, l == 0 ? L.d64 : nullptr);
+        mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, L.d64);
         if (mixed) {
             mg::launch_pack64to32(s, L.lay, L.fx64, L.fx32);
             mg::launch_pack64to32(s, L.lay, L.fy64, L.fy32);
@@ -336,7 +340,8 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     if (!std::isfinite(nb)) return fail(h, MG_ERR_ARG, "right-hand side is not finite");
     if (df && !(nb < 1e30)) return fail(h, MG_ERR_ARG, "MG_MIXED_DF needs |b - mean b| < 1e30");
     int status = MG_OK;
-    int cycles = 0;
+    int cycles = 0, outer = 0;
+    const int inner = mixed ? h->o.inner_cycles : 1;
     double rr = 0.0;
     if (nb == 0.0) {
         MG_CUDA(h, cudaMemsetAsync(p, 0, sizeof(double) * (size_t)n, s));
@@ -381,13 +386,16 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         hist[hist_n++] = rr;
         status = MG_ERR_NOT_CONVERGED;
         if (rr <= h->o.rtol) status = MG_OK;
-        for (int c = 1; c <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++c) {
+        for (int it = 1; cycles + inner <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++it) {
             if (mixed) {
+                // inner_cycles FP32 V-cycles on the scaled residual: the first from zero, the
+                // next ones continuing from the previous correction
+                for (int q = 0; q + 1 < inner; ++q) vcycle32(h, 0, F.b32, F.x32, nullptr, q == 0);
                 if (fuse) {
                     OuterUpdate up{df ? nullptr : p, df ? h->p2 : nullptr, 1.0 / scale, mu};
-                    vcycle32(h, 0, F.b32, F.x32, &up);
+                    vcycle32(h, 0, F.b32, F.x32, &up, inner == 1);
                 } else {
-                    vcycle32(h, 0, F.b32, F.x32);
+                    vcycle32(h, 0, F.b32, F.x32, nullptr, inner == 1);
                     prof_begin(h, MG_PROF_UPDATE);
                     if (df) mg::launch_update_df(s, F.d, F.lay, h->p2, F.x32, 1.0 / scale, mu);
                     else mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
@@ -404,7 +412,8 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             if (!mixed) mg::launch_add_const(s, n, p, -mu_new);  // FP64 path: zero mean each cycle
             mu = mixed ? mu_new : 0.0;
             rr = rn / nb;
-            cycles = c;
+            cycles += inner;
+            outer = it;
             if (hist_n < MG_HIST_LEN) hist[hist_n++] = rr;
             if (!std::isfinite(rr) || rr > 1e12) {
                 status = MG_ERR_DIVERGED;
@@ -427,6 +436,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     if (st) {
         st->status = status;
         st->cycles = cycles;
+        st->outer = outer;
         st->relres = rr;
         for (int q = 0; q < MG_HIST_LEN; ++q) st->relres_hist[q] = q < hist_n ? hist[q] : 0.0;
         float ms = 0.f;
@@ -474,6 +484,7 @@ void mg_default_opts(mg_opts *o) {
     o->rtol = 1e-10;
     o->max_cycles = 200;
     o->warm_start = 0;
+    o->inner_cycles = 1;
 }
 
 int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
@@ -486,7 +497,8 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         (o->precision == MG_MIXED_DF && o->nx % 2 != 0) || o->pre < 0 || o->post < 0 ||
         o->pre > 64 || o->post > 64 || o->coarsest < 2 ||
         (o->prolong != MG_PROLONG_TRILINEAR && o->prolong != MG_PROLONG_CONSTANT) || !(o->rtol >= 0.0) ||
-        o->max_cycles < 0)
+        o->max_cycles < 0 || o->inner_cycles < 1 || o->inner_cycles > 8 ||
+        (o->precision == MG_FP64 && o->inner_cycles != 1))
         return MG_ERR_ARG;
     int nl = num_levels(o->nx, o->ny, o->nz, o->coarsest);
     if (nl > MG_MAX_LEVELS) return MG_ERR_ARG;
@@ -522,7 +534,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         add((void **)&L.fy64, 8 * n);
         add((void **)&L.fz64, 8 * n);
         add((void **)&L.invd64, 8 * n);
-        if (l == 0) add((void **)&L.d64, 8 * n);
+        if (l == 0 || !mixed) add((void **)&L.d64, 8 * n);  // FP64 cycle: diagonal-form restriction
         if (mixed) {
             add((void **)&L.fx32, 4 * n);
             add((void **)&L.fy32, 4 * n);

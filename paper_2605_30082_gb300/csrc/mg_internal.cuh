@@ -127,6 +127,9 @@ void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat);
 void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st);
 void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st, float2 *s2);
 // FP64 red-black half sweep of one colour, in place
+// FP64 red-only residual + restriction in diagonal form (dg = sum of the cell's face betas)
+void launch_rr_red_diag64(cudaStream_t s, Dims fine, double h2, Coef<double> c, const double *dg,
+                          const double *b, const double *x, double *bc);
 void launch_rbgs_half64(cudaStream_t s, Dims d, double h2, Coef<double> c, const double *b, double *p,
                         int colour);
 template <typename T>

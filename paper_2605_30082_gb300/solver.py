@@ -25,11 +25,13 @@ class Solver:
 
     Parameters mirror ``mg_opts``: dims = (nx, ny, nz), h, precision ('fp64',
     'mixed' or 'mixed_df'), pre/post sweeps, coarsest, prolong ('trilinear' or
-    'constant'), rtol, max_cycles, warm_start.
+    'constant'), rtol, max_cycles, warm_start, inner_cycles (mixed modes: FP32 V-cycles per
+    outer FP64 residual).
     """
 
     def __init__(self, dims, h=None, precision="mixed", pre=2, post=2, coarsest=None,
-                 prolong="trilinear", rtol=1e-10, max_cycles=200, warm_start=False, stream=None):
+                 prolong="trilinear", rtol=1e-10, max_cycles=200, warm_start=False, stream=None,
+                 inner_cycles=1):
         nx, ny, nz = (int(v) for v in dims)
         o = L.mg_default_opts()
         o.nx, o.ny, o.nz = nx, ny, nz
@@ -41,6 +43,7 @@ class Solver:
         o.rtol = float(rtol)
         o.max_cycles = int(max_cycles)
         o.warm_start = int(bool(warm_start))
+        o.inner_cycles = int(inner_cycles)
         self.opts = o
         self.dims = (nx, ny, nz)
         self.h = o.h

@@ -75,3 +75,27 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "mg_oracle" not in txt and "liboracle" not in txt, f
+
+
+def _header_struct_fields(text, name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", text)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^\]]*\]", "", decl)  # array extents
+        parts = decl.split(None, 1)[1]          # drop the type
+        names += [p.strip().lstrip("*") for p in parts.split(",")]
+    return names
+
+
+@pytest.mark.parametrize("name", ["mg_opts", "mg_stats"])
+def test_ctypes_structs_mirror_the_header(name):
+    from paper_2605_30082_gb300 import _lib
+
+    text = open(os.path.join(ROOT, "include", "mg.h")).read()
+    assert _header_struct_fields(text, name) == [f[0] for f in getattr(_lib, name)._fields_]

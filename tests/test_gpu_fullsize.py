@@ -43,8 +43,9 @@ def fields(n):
                 b=O.divergence([host(a) for a in u], 1.0 / n))
 
 
-def gpu_solver(c, precision, rtol):
-    s = Solver((c["n"],) * 3, h=c["h"], precision=precision, coarsest=8, rtol=rtol, max_cycles=200)
+def gpu_solver(c, precision, rtol, inner=1):
+    s = Solver((c["n"],) * 3, h=c["h"], precision=precision, coarsest=8, rtol=rtol, max_cycles=200,
+               inner_cycles=inner)
     rho = s.density_from_fractions([c["fd"], c["ff"]], list(RHO_PHASE))
     s.set_density(rho)
     return s, rho
@@ -70,19 +71,19 @@ def test_256_fp64_reproduces_oracle_iteration(c256):
     assert rel(host(p), p_o) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
-def test_256_mixed_reaches_exact_solution(c256, prec):
-    s, _ = gpu_solver(c256, prec, 1e-11)
+@pytest.mark.parametrize("prec,inner", [("mixed", 1), ("mixed_df", 1), ("mixed", 2), ("mixed_df", 2)])
+def test_256_mixed_reaches_exact_solution(c256, prec, inner):
+    s, _ = gpu_solver(c256, prec, 1e-11, inner)
     p = s.solve(s.rhs(u=c256["u"]))
     assert s.last_stats.relres <= 1e-11
     assert rel(host(p), c256["exact"]) <= 1e-9
     # at rtol 1e-10 the iteration error of V(2,2) itself dominates: compare with the oracle's
     # own iteration stopped at the same tolerance (both sit ~1.6e-9 from the exact solution)
     s.close()
-    s, _ = gpu_solver(c256, prec, 1e-10)
+    s, _ = gpu_solver(c256, prec, 1e-10, inner)
     p = host(s.solve(s.rhs(u=c256["u"])))
     p_o, _, nc_o, _, _ = c256["iter"]
-    assert abs(s.last_stats.cycles - nc_o) <= 1
+    assert nc_o - 1 <= s.last_stats.cycles <= nc_o + inner
     assert rel(p, p_o) <= 1e-9
     assert rel(p, c256["exact"]) <= 3e-9
 
@@ -134,11 +135,11 @@ def test_512_level0_sweep_on_subboxes(prec, dtype):
         assert rel(got[m], want[m]) < tol, o
 
 
-@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
-def test_512_benchmark_solve_and_adjoint(prec):
+@pytest.mark.parametrize("prec,inner", [("mixed", 1), ("mixed_df", 1), ("mixed", 2), ("mixed_df", 2)])
+def test_512_benchmark_solve_and_adjoint(prec, inner):
     c = fields(512)
     h = c["h"]
-    s, _ = gpu_solver(c, prec, 1e-10)
+    s, _ = gpu_solver(c, prec, 1e-10, inner)
     b = s.rhs(u=c["u"])
     assert rel(host(b), c["b"]) < 1e-13
     p = s.solve(b)

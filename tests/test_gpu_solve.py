@@ -75,6 +75,36 @@ def test_ragged_grids_match_exact(dims, prec):
         assert s.last_stats.cycles == nc_o and rel(host(p), p_o) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
+@pytest.mark.parametrize("inner", [2, 3])
+def test_inner_cycles_reach_exact_32cubed(c32, prec, inner):
+    """Several FP32 V-cycles per outer FP64 residual: same discrete solution, the V-cycle
+    count within one outer iteration of the one-cycle count."""
+    s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8, inner_cycles=inner)
+    s.set_density(dev(c32["rho"]))
+    p = s.solve(dev(c32["b"]))
+    st = s.last_stats
+    assert st.relres <= 1e-10
+    assert rel(host(p), c32["exact8"]) < 1e-9
+    assert st.cycles == inner * st.outer and len(st.history()) == st.outer + 1
+    nc_o = c32["iter8"][2]
+    assert nc_o - 2 <= st.cycles <= nc_o + inner + 1
+    assert all(b < a for a, b in zip(st.history(), st.history()[1:]))
+
+
+def test_inner_cycles_limits():
+    with pytest.raises(MgError):
+        Solver((16, 16, 16), precision="fp64", inner_cycles=2)
+    for bad in (0, 9):
+        with pytest.raises(MgError):
+            Solver((16, 16, 16), precision="mixed", inner_cycles=bad)
+    # max_cycles bounds the V-cycles: 5 allows two outer iterations of 2
+    s = Solver((16, 16, 16), precision="mixed", coarsest=8, rtol=1e-30, max_cycles=5, inner_cycles=2)
+    s.set_density(dev(random_rho((16, 16, 16), 9)))
+    s.solve(dev(np.random.default_rng(3).standard_normal((16, 16, 16))), raise_on_nonconvergence=False)
+    assert s.last_stats.cycles == 4 and s.last_stats.outer == 2
+
+
 def test_solve_is_deterministic(c32):
     s = Solver((32, 32, 32), h=c32["h"], precision="mixed", coarsest=8)
     s.set_density(dev(c32["rho"]))
