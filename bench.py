@@ -30,17 +30,24 @@ if ROOT not in sys.path:
 
 METRIC = "time-to-1e-10 residual & fine-grid GLUP/s at 512^3, FP64 vs mixed; HBM GB/s"
 RHO_PHASE = (998.0, 880.0, 1.2)
+# FP32 V-cycles per outer FP64 residual and update in the timed configuration
+INNER = 2
 # Algorithmic bytes per grid cell of the finest-level FP32 half sweep (colour-split storage,
 # coefficients s = 1/rho): read the other colour's x (2), s of both colours (4), this colour's
 # b (2), write this colour's x (2); the first pre-smoothing half sweep starts from x = 0 (8).
 HALF_BYTES, HALF_ZERO_BYTES = 10, 8
-# finest-level half sweeps per V(2,2) timed in the SMOOTH class: 1 from zero + 6 (the 8th is
-# fused with the outer update)
-HALF_PER_CYCLE = 7
+# finest-level half sweeps per outer iteration timed in the SMOOTH class: 8 per V(2,2) cycle,
+# less the last one, which is fused with the outer update; one of them starts from zero
+HALF_PER_OUTER = 8 * INNER - 1
 # FP64 outer residual: 7 fused multiply-adds per cell; GB300 nominal FP64 rate (NVIDIA B300
 # specification: 1.25 TFLOP/s; no FP64 figure is in MEASURED_PEAKS.json)
 RESID_FMA_PER_CELL = 7
 FP64_PEAK_TFLOPS = 1.25
+# FP64 flops per grid cell of the plain FP64 V-cycle's finest-level kernels (a fused multiply-
+# add counts 2): half sweep 7 FMA + 1 multiply per updated cell (half the cells); red residual +
+# restriction 7 FMA + 1 multiply + 1 add per red child; red prolongation 8 FMA per red cell;
+# outer residual 7 FMA per cell
+FP64_FLOPS_PER_CELL = {"smooth": 7.5, "resid_restrict": 8.0, "prolong": 8.0, "fine_residual": 14.0}
 
 
 def parse():
@@ -52,7 +59,7 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="cells per dimension (default 512)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves (FP64, other modes)")
     return ap.parse_args()
 
 
@@ -181,7 +188,7 @@ def run_ours(args):
     w = D.normal_weights((n, n, n), seed=1, device=dev)
     torch.cuda.synchronize()
 
-    s = Solver((n, n, n), precision="mixed", coarsest=8, rtol=1e-10, max_cycles=200)
+    s = Solver((n, n, n), precision="mixed", coarsest=8, rtol=1e-10, max_cycles=200, inner_cycles=INNER)
     rho = torch.empty((n, n, n), dtype=torch.float64, device=dev)
     b = torch.empty_like(rho)
     p = torch.zeros_like(rho)
@@ -247,25 +254,46 @@ def run_ours(args):
         return statistics.median(times), cyc
 
     t_mixed, cyc_mixed = time_solve(s)
+    variants = {}
+    for name, prec, inner in (("mixed_inner1", "mixed", 1), ("mixed_df", "mixed_df", INNER)):
+        if args.no_fp64:
+            break
+        sv = Solver((n, n, n), precision=prec, coarsest=8, rtol=1e-10, max_cycles=200, inner_cycles=inner)
+        sv.set_density(rho)
+        variants[name] = time_solve(sv)
+        sv.close()
     t_fp64 = cyc_fp64 = None
+    fp64_prof = None
     if not args.no_fp64:
         s64 = Solver((n, n, n), precision="fp64", coarsest=8, rtol=1e-10, max_cycles=200)
         s64.set_density(rho)
         t_fp64, cyc_fp64 = time_solve(s64)
+        s64.profile(True)
+        s64.solve(b, p)
+        fp64_prof = {}
+        for name, cls in [("smooth", L.MG_PROF_SMOOTH), ("resid_restrict", L.MG_PROF_RESID_RESTRICT),
+                          ("prolong", L.MG_PROF_PROLONG), ("fine_residual", L.MG_PROF_FINE_RESIDUAL)]:
+            k, ms_k = s64.profile_read(cls)
+            tf = FP64_FLOPS_PER_CELL[name] * n**3 * k / (ms_k * 1e-3) / 1e12 if ms_k > 0 else None
+            fp64_prof[name] = {"launches": k, "ms": round(ms_k, 3),
+                               "fp64_tflops": None if tf is None else round(tf, 3),
+                               "frac_of_nominal": None if tf is None else round(tf / FP64_PEAK_TFLOPS, 3)}
+        s64.profile(False)
         s64.close()
+        s.solve(b, p)  # restore p for the gradient pass below
 
     # ---- rooflines: finest-level FP32 half sweep (HBM) and FP64 outer residual (FP64 ALU)
     cells = n**3
     n_sm, ms_sm = prof["smooth"]
     avg_sm = ms_sm / max(n_sm, 1)
-    ncyc_sm = n_sm / HALF_PER_CYCLE
-    bytes_sm = ncyc_sm * (HALF_ZERO_BYTES + (HALF_PER_CYCLE - 1) * HALF_BYTES) * cells
+    nouter_sm = n_sm / HALF_PER_OUTER
+    bytes_sm = nouter_sm * (HALF_ZERO_BYTES + (HALF_PER_OUTER - 1) * HALF_BYTES) * cells
     peak = _measured_peak_hbm()
     gbs_sm = bytes_sm / (ms_sm * 1e-3) / 1e9
     roof_sm = {"bound": "hbm", "achieved": round(gbs_sm, 1), "peak": peak, "unit": "GB/s",
                "frac": round(gbs_sm / peak, 3),
-               "traffic": _traffic_from_profiles("k_half_vec", cells),
-               "kernel": "k_half_vec<sform> (finest-level FP32 red-black half sweep)",
+               "traffic": _traffic_from_profiles("k_half_z", cells),
+               "kernel": "k_half_z<sform> (finest-level FP32 red-black half sweep, z-marching)",
                "launch_ms": round(avg_sm, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     n_fr, ms_fr = prof["fine_residual"]
     avg_fr = ms_fr / max(n_fr, 1)
@@ -284,7 +312,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(fd, ff, u, w, n, (cyc_fp64 or cyc_mixed) * 2)
+        cpu = oracle_sample(fd, ff, u, w, n, (cyc_fp64 or cyc_mixed) + stats["adj"][0])
 
     value = world * cells / (ms_step * 1e-3) / 1e9
     out = {
@@ -300,14 +328,20 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32 inner V-cycle / f64 outer residual, update, coarse solve",
         "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
-        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, mixed V(2,2), coarsest 8^3, "
-                               f"rtol 1e-10, forward + adjoint",
+        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, mixed V(2,2) with {INNER} "
+                               f"FP32 V-cycles per FP64 outer residual, coarsest 8^3, rtol 1e-10, forward + adjoint",
                    "cells": cells, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
         "breakdown": {
-            "time_to_tol_ms": {"mixed": round(t_mixed, 3), "fp64": None if t_fp64 is None else round(t_fp64, 3)},
-            "cycles": {"mixed": cyc_mixed, "fp64": cyc_fp64, "adjoint": stats["adj"][0]},
-            "speedup_mixed_vs_fp64": None if t_fp64 is None else round(t_fp64 / t_mixed, 3),
+            "time_to_tol_ms": {"mixed": round(t_mixed, 3),
+                               **{k: round(v[0], 3) for k, v in variants.items()},
+                               "fp64": None if t_fp64 is None else round(t_fp64, 3)},
+            "cycles": {"mixed": cyc_mixed, **{k: v[1] for k, v in variants.items()}, "fp64": cyc_fp64,
+                       "adjoint": stats["adj"][0]},
+            "speedup_vs_fp64": None if t_fp64 is None else {
+                "mixed": round(t_fp64 / t_mixed, 3),
+                **{k: round(t_fp64 / v[0], 3) for k, v in variants.items()}},
+            "fp64_solver_kernels": fp64_prof,
             "adjoint_over_forward": round(stats["adj"][2] / stats["fwd"][2], 3),
             "solve_glups_mixed": round(cells * cyc_mixed / (t_mixed * 1e-3) / 1e9, 3),
             "smoother_glups": round(cells * (n_sm / 2) / (ms_sm * 1e-3) / 1e9, 3),
@@ -402,9 +436,9 @@ def run_reference(args):
     fd, ff = D.fractions_ramp(geom)
     u = D.face_velocities(n, seed=0)
     w = D.normal_weights((n, n, n), seed=1)
-    # forward + adjoint V-cycles at this size, taken from the FP64 path's measured count (equal to
-    # the oracle's: same algorithm); 512^3 drop/film needs 24 + 24
-    cycles_total = 48 if n == 512 else 2 * 20
+    # forward + adjoint V-cycles at this size, taken from the FP64 path's measured counts (equal
+    # to the oracle's: same algorithm); 512^3 drop/film needs 24 (forward) + 29 (adjoint)
+    cycles_total = 53 if n == 512 else 2 * 20
     for _ in range(max(args.warmup, 0)):
         pass  # the oracle has no warm-up state; each step is independent
     samples = [oracle_sample(fd, ff, u, w, n, cycles_total) for _ in range(max(args.steps, 1))]

@@ -1,0 +1,40 @@
+"""A small solve for kernel profiling: python -m paper_2605_30082_gb300.profile_case NX NY NZ [PRECISION [INNER [CYCLES]]]
+
+Random density in [1.2, 998] and random right-hand side (torch generators, seeds 3 and 4),
+`CYCLES` V-cycles (default 2) of the given precision ('fp64', 'mixed', 'mixed_df'), followed by
+one adjoint solve of as many cycles.  Sized by the caller so that every array is larger than L2
+while the whole case holds a few GB: e.g. 512 512 256 keeps the 512-cell rows (and so the launch
+configuration) of the 512^3 workload at half its cells.
+"""
+import sys
+
+import torch
+
+from . import _lib as L
+from .solver import MgError, Solver
+
+
+def main(argv):
+    nx, ny, nz = (int(a) for a in argv[:3])
+    prec = argv[3] if len(argv) > 3 else "mixed"
+    inner = int(argv[4]) if len(argv) > 4 else 1
+    cycles = int(argv[5]) if len(argv) > 5 else 2
+    dev = torch.device("cuda")
+    g = torch.Generator(device="cuda")
+    rho = 1.2 + 996.8 * torch.rand((nz, ny, nx), generator=g.manual_seed(3), device=dev, dtype=torch.float64)
+    b = torch.randn((nz, ny, nx), generator=g.manual_seed(4), device=dev, dtype=torch.float64)
+    s = Solver((nx, ny, nz), h=1.0 / max(nx, ny, nz), precision=prec, coarsest=8, rtol=1e-30,
+               max_cycles=cycles, inner_cycles=inner if prec != "fp64" else 1)
+    s.set_density(rho)
+    p = s.solve(b, raise_on_nonconvergence=False)
+    try:
+        s.adjoint(b, p)  # stops at the cycle limit, by design
+    except MgError as e:
+        if e.code != L.MG_ERR_NOT_CONVERGED:
+            raise
+    torch.cuda.synchronize()
+    print("ok", s.last_stats.cycles, s.last_stats.relres)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
