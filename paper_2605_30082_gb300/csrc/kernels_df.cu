@@ -43,15 +43,15 @@ __global__ void k_split(i64 n, const double *__restrict__ src, float2 *dst) {
     const i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     const double v = src[m];
-    const float hi = (float)v;
-    dst[m] = make_float2(hi, (float)(v - (double)hi));
+    const float hi = d2f_rn(v);
+    dst[m] = make_float2(hi, d2f_rn(v - f2d_exact(hi)));
 }
 
 __global__ void k_join(i64 n, const float2 *__restrict__ src, double *dst) {
     const i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     const float2 v = src[m];
-    dst[m] = (double)v.x + (double)v.y;
+    dst[m] = f2d_exact(v.x) + f2d_exact(v.y);
 }
 
 // h^2 r = h^2 b + sum_f beta_f p_nb - d p_c in double-float (b already scaled by h^2);

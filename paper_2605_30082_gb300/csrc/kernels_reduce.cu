@@ -97,55 +97,6 @@ __device__ __forceinline__ i64 sto(const Lay &L, int x, int y, int z) {
     return ((x + y + z) & 1) * L.half + row * L.hx + (x >> 1);
 }
 
-// FP64 -> FP32 by truncating the IEEE-754 fields with integer operations (the
-// binary64 layout: 1 sign, 11 exponent (bias 1023), 52 fraction bits; binary32:
-// 1, 8 (bias 127), 23).  Rounds toward zero; results below the FP32 normal range
-// become zero, above it infinity; NaN stays NaN.  Keeps the conversion off the
-// FP64 pipe, which GB300 runs at a small fraction of the FP32 rate.
-__device__ __forceinline__ float d2f_trunc(double v) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(u >> 32);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
-    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
-    const int e32 = e - 1023 + 127;
-    if (e32 <= 0) return __uint_as_float(sign);
-    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
-    return __uint_as_float(sign | ((unsigned)e32 << 23) | frac);
-}
-
-// FP32 -> FP64 exactly with integer operations (FP32 subnormals become zero)
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u;
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned m = u & 0x7fffffu;
-    if (e == 0) return __hiloint2double((int)sign, 0);
-    const unsigned ed = (e == 0xffu) ? 0x7ffu : (e - 127u + 1023u);
-    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
-}
-
-// FP64 -> FP32 rounded to nearest, ties to even, with integer operations on the IEEE-754
-// fields: the 29 dropped fraction bits decide the rounding; a carry out of the fraction
-// increments the exponent (up to infinity).  Results below the FP32 normal range become
-// (signed) zero; NaN stays NaN.
-__device__ __forceinline__ float d2f_rn(double v) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(u >> 32);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
-    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((u << 12) != 0ull) ? 0x400000u : 0u));
-    const int e32 = e - 1023 + 127;
-    if (e32 <= 0) return __uint_as_float(sign);
-    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
-    const unsigned rest = (unsigned)(u & 0x1fffffffull);  // the 29 dropped bits
-    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
-    const unsigned mag = ((unsigned)e32 << 23) + frac + up;  // a carry moves into the exponent
-    return __uint_as_float(sign | (mag >= 0x7f800000u ? 0x7f800000u : mag));
-}
-
 // h^2 r = h^2 b - (d p_c - sum_f beta_f p_nb), d = sum_f beta_f: 7 FP64 fused multiply-adds
 // per cell when b arrives already scaled by h^2 (SCALED), one more multiply otherwise.
 // partials: (sum (h^2 r)^2 and sum p, each accumulated in FP32 per thread); r32 = s32 * h^2 r.

@@ -32,25 +32,33 @@ __global__ void k_density(i64 n, FracArgs a, double *rho) {
 
 __device__ __forceinline__ bool good_positive(double v) { return v > 0.0 && v <= 1.79e308; }
 
-// beta between densities a and b: 1 / harmonic mean = (a + b) / (2 a b)
-__device__ __forceinline__ double inv_harmonic(double a, double b) { return (a + b) / (2.0 * a * b); }
+// s = 1/rho per cell, validating rho (finite and > 0)
+__global__ void k_inv_rho(i64 n, const double *__restrict__ rho, double *sinv, unsigned *err) {
+    const i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double r = rho[m];
+    if (!good_positive(r)) {
+        atomicOr(err, 1u);
+        sinv[m] = 1.0;
+        return;
+    }
+    sinv[m] = recip64(r);
+}
 
-__global__ void k_faces_from_rho(Dims d, const double *__restrict__ rho, double *fx, double *fy,
-                                 double *fz, unsigned *err) {
-    i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
-    double rc = rho[c];
-    if (!good_positive(rc)) atomicOr(err, 1u);
-    double vx = 0.0, vy = 0.0, vz = 0.0;
-    if (i > 0) vx = inv_harmonic(rho[c - 1], rc);
-    if (j > 0) vy = inv_harmonic(rho[c - d.nx], rc);
-    if (k > 0) vz = inv_harmonic(rho[c - d.nxy], rc);
-    fx[c] = vx;
-    fy[c] = vy;
-    fz[c] = vz;
+// beta on the low faces: 1 / harmonic mean of the two densities = (s_L + s_R) / 2; blocks take
+// rows (grid y, strided), threads the cells of a row
+__global__ void k_faces_from_s(Dims d, const double *__restrict__ sv, double *fx, double *fy, double *fz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.nx) return;
+    const i64 rows = (i64)d.ny * d.nz;
+    for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = (int)(row % d.ny), k = (int)(row / d.ny);
+        const i64 c = row * d.nx + i;
+        const double sc = sv[c];
+        fx[c] = i > 0 ? 0.5 * (sv[c - 1] + sc) : 0.0;
+        fy[c] = j > 0 ? 0.5 * (sv[c - d.nx] + sc) : 0.0;
+        fz[c] = k > 0 ? 0.5 * (sv[c - d.nxy] + sc) : 0.0;
+    }
 }
 
 __global__ void k_faces_from_api(Dims d, const double *__restrict__ bx, const double *__restrict__ by,
@@ -104,7 +112,7 @@ __global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *_
     if (j < d.ny - 1) s += fy[c + d.nx];
     s += fz[c];
     if (k < d.nz - 1) s += fz[c + d.nxy];
-    if (invd64) invd64[c] = 1.0 / s;
+    if (invd64) invd64[c] = recip64(s);
     if (diag) diag[c] = s;
 }
 
@@ -269,10 +277,13 @@ void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
     k_density<<<blocks_for(n), kThreads, 0, s>>>(n, a, rho);
 }
 
-void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *fx, double *fy,
+void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *sinv, double *fx, double *fy,
                            double *fz, unsigned *err) {
-    count_launch();
-    k_faces_from_rho<<<blocks_for(d.n), kThreads, 0, s>>>(d, rho, fx, fy, fz, err);
+    count_launch(2);
+    k_inv_rho<<<blocks_for(d.n), kThreads, 0, s>>>(d.n, rho, sinv, err);
+    const i64 rows = (i64)d.ny * d.nz;
+    const dim3 grd((unsigned)((d.nx + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
+    k_faces_from_s<<<grd, 128, 0, s>>>(d, sinv, fx, fy, fz);
 }
 
 void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const double *by,
@@ -289,6 +300,7 @@ void launch_faces_to_api(cudaStream_t s, Dims d, const double *fx, const double 
 
 void launch_invdiag(cudaStream_t s, Dims d, const double *fx, const double *fy, const double *fz,
                     double *invd64, double *diag) {
+    if (!invd64 && !diag) return;
     count_launch();
     k_invdiag<<<blocks_for(d.n), kThreads, 0, s>>>(d, fx, fy, fz, invd64, diag);
 }

@@ -99,19 +99,6 @@ __global__ void k_half_any(Lay L, float h2, Coef32 cf, const float *__restrict__
     xv[sto(L, x, y, z)] = __fdividef(hh * b[sto(L, x, y, z)] + num, den);
 }
 
-// FP32 -> FP64 exactly with integer operations (FP32 subnormals become zero); keeps the
-// widening off GB300's low-rate FP64 pipe (binary32: 1 sign, 8 exponent (bias 127), 23
-// fraction bits; binary64: 1, 11 (bias 1023), 52)
-__device__ __forceinline__ double widen(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u;
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned m = u & 0x7fffffu;
-    if (e == 0) return __hiloint2double((int)sign, 0);
-    const unsigned ed = (e == 0xffu) ? 0x7ffu : (e - 127u + 1023u);
-    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
-}
-
 struct Upd {
     double *p;      // natural FP64 solution of the finest level (UPDATE 1)
     float2 *p2;     // natural double-float solution of the finest level (UPDATE 2)
@@ -265,7 +252,7 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
             const double2 pv = pvs[v];
             const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];  // cells 2(k0+v) and 2(k0+v)+1
             *reinterpret_cast<double2 *>(pr + 2 * v) =
-                make_double2(pv.x + widen(fmaf(al, e0, -sh)), pv.y + widen(fmaf(al, e1, -sh)));
+                make_double2(pv.x + f2d_exact(fmaf(al, e0, -sh)), pv.y + f2d_exact(fmaf(al, e1, -sh)));
         }
     }
 }
@@ -427,7 +414,7 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
                         const double2 pv = pvs[v];
                         const float e0 = p ? bk[v] : out[v], e1 = p ? out[v] : bk[v];
                         *reinterpret_cast<double2 *>(pr + 2 * v) =
-                            make_double2(pv.x + widen(fmaf(al, e0, -sh)), pv.y + widen(fmaf(al, e1, -sh)));
+                            make_double2(pv.x + f2d_exact(fmaf(al, e0, -sh)), pv.y + f2d_exact(fmaf(al, e1, -sh)));
                     }
                 }
             }
@@ -806,24 +793,30 @@ __global__ void k_unpack(Lay L, const float *__restrict__ st, float *nat) {
     const i64 row = t / L.nx;
     nat[t] = st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))];
 }
+// FP64 natural -> FP32 level storage, rounded to nearest; blocks take rows (grid y, strided)
 __global__ void k_pack64(Lay L, const double *__restrict__ nat, float *st) {
-    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.n) return;
-    const int x = (int)(t % L.nx);
-    const i64 row = t / L.nx;
-    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = (float)nat[t];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.nx) return;
+    const i64 rows = (i64)L.ny * L.nz;
+    for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+        st[sto(L, x, y, z)] = d2f_rn(nat[row * L.nx + x]);
+    }
 }
-// s = 1/rho: FP32 in the level's layout, and optionally as a double-float pair (hi, lo) in the
-// natural layout for the double-float outer residual
-__global__ void k_pack_inv64(Lay L, const double *__restrict__ rho, float *st, float2 *s2) {
-    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.n) return;
-    const int x = (int)(t % L.nx);
-    const i64 row = t / L.nx;
-    const double v = 1.0 / rho[t];
-    const float hi = (float)v;
-    st[sto(L, x, (int)(row % L.ny), (int)(row / L.ny))] = hi;
-    if (s2) s2[t] = make_float2(hi, (float)(v - (double)hi));
+// s = 1/rho (FP64, natural): FP32 in the level's layout, and optionally as a pair (hi, lo) of
+// FP32 numbers with hi + lo = s to about 2^-48 (natural layout) for the double-float residual
+__global__ void k_pack_inv64(Lay L, const double *__restrict__ sinv, float *st, float2 *s2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.nx) return;
+    const i64 rows = (i64)L.ny * L.nz;
+    for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+        const i64 t = row * L.nx + x;
+        const double v = sinv[t];
+        const float hi = d2f_rn(v);
+        st[sto(L, x, y, z)] = hi;
+        if (s2) s2[t] = make_float2(hi, d2f_rn(v - f2d_exact(hi)));
+    }
 }
 
 }  // namespace
@@ -948,11 +941,15 @@ void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat) {
 }
 void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st) {
     count_launch();
-    k_pack64<<<blocks_for(L.n), kThreads, 0, s>>>(L, nat, st);
+    const i64 rows = (i64)L.ny * L.nz;
+    const dim3 grd((unsigned)((L.nx + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
+    k_pack64<<<grd, 128, 0, s>>>(L, nat, st);
 }
-void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st, float2 *s2) {
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *sinv, float *st, float2 *s2) {
     count_launch();
-    k_pack_inv64<<<blocks_for(L.n), kThreads, 0, s>>>(L, rho, st, s2);
+    const i64 rows = (i64)L.ny * L.nz;
+    const dim3 grd((unsigned)((L.nx + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
+    k_pack_inv64<<<grd, 128, 0, s>>>(L, sinv, st, s2);
 }
 
 }  // namespace mg

@@ -278,7 +278,7 @@ int finish_operator(mg_handle *h) {
     for (int l = 0; l < h->nlev; ++l) {
         Level &L = h->lv[l];
         mg::launch_invdiag(s, L.d, L.fx64, L.fy64, L.fz64, L.invd64, L.d64);
-        if (mixed) {
+        if (mixed && !(l == 0 && h->sform0)) {  // the s-form finest level has no FP32 faces
             mg::launch_pack64to32(s, L.lay, L.fx64, L.fx32);
             mg::launch_pack64to32(s, L.lay, L.fy64, L.fy32);
             mg::launch_pack64to32(s, L.lay, L.fz64, L.fz32);
@@ -533,7 +533,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         add((void **)&L.fx64, 8 * n);
         add((void **)&L.fy64, 8 * n);
         add((void **)&L.fz64, 8 * n);
-        add((void **)&L.invd64, 8 * n);
+        if (!mixed) add((void **)&L.invd64, 8 * n);  // only the FP64 smoother divides by the diagonal
         if (l == 0 || !mixed) add((void **)&L.d64, 8 * n);  // FP64 cycle: diagonal-form restriction
         if (mixed) {
             add((void **)&L.fx32, 4 * n);
@@ -641,9 +641,10 @@ int mg_set_density(mg_handle *h, const double *rho) {
     h->have_op = 0;
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
-    mg::launch_faces_from_rho(h->s, F.d, rho, F.fx64, F.fy64, F.fz64, h->err);
+    // s = 1/rho goes through the RHS buffer, which holds nothing between calls
+    mg::launch_faces_from_rho(h->s, F.d, rho, h->bt, F.fx64, F.fy64, F.fz64, h->err);
     h->sform0 = h->o.precision != MG_FP64;
-    if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, rho, F.s32, h->o.precision == MG_MIXED_DF ? F.s2 : nullptr);
+    if (h->sform0) mg::launch_pack_inv_rho(h->s, F.lay, h->bt, F.s32, h->o.precision == MG_MIXED_DF ? F.s2 : nullptr);
     return finish_operator(h);
 }
 

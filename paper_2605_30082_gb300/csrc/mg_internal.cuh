@@ -49,6 +49,76 @@ struct Coef {
     const T *invd;          // 1 / sum of the cell's interior face coefficients (FP64 only)
 };
 
+#ifdef __CUDACC__
+// ---- IEEE-754 conversions and the FP64 reciprocal, with few FP64-pipe instructions --------
+// GB300 runs FP64 arithmetic and FP64<->FP32 conversions at a small fraction of its FP32
+// rate, so the hot kernels convert by integer operations on the IEEE-754 fields
+// (binary64: 1 sign, 11 exponent (bias 1023), 52 fraction bits; binary32: 1, 8 (bias 127), 23).
+
+// FP64 -> FP32 by truncating the IEEE-754 fields with integer operations (the
+// binary64 layout: 1 sign, 11 exponent (bias 1023), 52 fraction bits; binary32:
+// 1, 8 (bias 127), 23).  Rounds toward zero; results below the FP32 normal range
+// become zero, above it infinity; NaN stays NaN.  Keeps the conversion off the
+// FP64 pipe, which GB300 runs at a small fraction of the FP32 rate.
+__device__ __forceinline__ float d2f_trunc(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) return __uint_as_float(sign);
+    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)e32 << 23) | frac);
+}
+
+// FP32 -> FP64 exactly with integer operations (FP32 subnormals become zero)
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned ed = (e == 0xffu) ? 0x7ffu : (e - 127u + 1023u);
+    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// FP64 -> FP32 rounded to nearest, ties to even, with integer operations on the IEEE-754
+// fields: the 29 dropped fraction bits decide the rounding; a carry out of the fraction
+// increments the exponent (up to infinity).  Results below the FP32 normal range become
+// (signed) zero; NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned frac = (unsigned)((u >> 29) & 0x7fffffu);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((u << 12) != 0ull) ? 0x400000u : 0u));
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) return __uint_as_float(sign);
+    if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const unsigned rest = (unsigned)(u & 0x1fffffffull);  // the 29 dropped bits
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
+    const unsigned mag = ((unsigned)e32 << 23) + frac + up;  // a carry moves into the exponent
+    return __uint_as_float(sign | (mag >= 0x7f800000u ? 0x7f800000u : mag));
+}
+
+// 1 / x for positive x.  Seed: the FP32 reciprocal (round to nearest) of x rounded to FP32,
+// relative error <= 2^-23; then two Newton-Raphson steps y <- y + y (1 - x y) in FP64, each
+// squaring the relative error (2^-46, then below FP64 rounding), so the result is within one
+// unit in the last place of 1/x.  Outside [2^-100, 2^100] (where the FP32 seed could leave
+// the FP32 range) it divides.
+__device__ __forceinline__ double recip64(double x) {
+    if (!(x >= 7.888609052210118e-31 && x <= 1.2676506002282294e30)) return 1.0 / x;
+    double y = f2d_exact(__frcp_rn(d2f_rn(x)));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+#endif
+
 // process-wide count of kernel launches (read through mg_kernel_launches)
 void count_launch(int k = 1);
 
@@ -59,7 +129,8 @@ constexpr int kReduceThreads = 256;
 // ---- setup kernels (FP64) -------------------------------------------------------
 void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
                     const double *rho_phase, double *rho);
-void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *fx, double *fy,
+// s = 1/rho per cell into `sinv` (validated: err |= 1 on a bad density), then the FP64 low faces
+void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *sinv, double *fx, double *fy,
                            double *fz, unsigned *err);
 void launch_faces_from_api(cudaStream_t s, Dims d, const double *bx, const double *by,
                            const double *bz, double *fx, double *fy, double *fz, unsigned *err);
@@ -125,7 +196,8 @@ void launch_coarse_matvec32(cudaStream_t s, Lay L, const double *pinv, const flo
 void launch_pack32(cudaStream_t s, Lay L, const float *nat, float *st);
 void launch_unpack32(cudaStream_t s, Lay L, const float *st, float *nat);
 void launch_pack64to32(cudaStream_t s, Lay L, const double *nat, float *st);
-void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *rho, float *st, float2 *s2);
+// s (FP64, natural) -> FP32 in the level layout, and optionally FP32 pairs (natural)
+void launch_pack_inv_rho(cudaStream_t s, Lay L, const double *sinv, float *st, float2 *s2);
 // FP64 red-black half sweep of one colour, in place
 // FP64 red-only residual + restriction in diagonal form (dg = sum of the cell's face betas)
 void launch_rr_red_diag64(cudaStream_t s, Dims fine, double h2, Coef<double> c, const double *dg,

@@ -50,13 +50,21 @@ def rnd(shape, seed):
 
 
 @pytest.mark.parametrize("dims", DIMS)
-def test_levels_and_faces_match_oracle(dims):
-    s, M = make(dims, "fp64")
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_levels_and_faces_match_oracle(dims, precision):
+    """The device forms beta = (s_L + s_R)/2 from s = 1/rho (a Newton reciprocal from an FP32
+    seed), the oracle (rho_L + rho_R)/(2 rho_L rho_R): both within 2 FP64 roundings of the same
+    number, so every face agrees to 1e-15 relative."""
+    s, M = make(dims, precision)
     assert s.num_levels == M.nlevels
     for l in range(M.nlevels):
         assert s.level_dims(l) == M.level_dims(l)
         for g, o in zip(s.level_faces(l), M.level_faces(l)):
-            assert rel(host(g), o) < 1e-15
+            g = host(g)
+            assert rel(g, o) < 1e-15
+            nz = o != 0
+            assert np.array_equal(g != 0, nz)
+            assert np.max(np.abs(g[nz] - o[nz]) / o[nz]) <= 1e-15
 
 
 def test_density_from_fractions_and_face_round_trip():
