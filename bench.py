@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 
 METRIC = "time-to-1e-10 residual & fine-grid GLUP/s at 512^3, FP64 vs mixed; HBM GB/s"
 RHO_PHASE = (998.0, 880.0, 1.2)
+SIGMA = 0.03  # interfacial tension of the CSF term (--csf)
 # FP32 V-cycles per outer FP64 residual and update in the timed configuration
 INNER = 2
 # Algorithmic bytes per grid cell of the finest-level FP32 half sweep (colour-split storage,
@@ -50,6 +51,12 @@ FP64_PEAK_TFLOPS = 1.25
 FP64_FLOPS_PER_CELL = {"smooth": 7.5, "resid_restrict": 8.0, "prolong": 8.0, "fine_residual": 14.0}
 
 
+# algorithmic bytes per fine grid cell of one launch of each profiled class (the smoother's
+# mix of regular and from-zero sweeps is computed from the launch counts instead)
+CLASS_BYTES = {"resid_restrict": 10.5, "prolong": 4.5, "update": 26.0, "fine_residual": 52.0,
+               "adjoint_grad": 28.0}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,6 +67,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the comparison solves (FP64, other modes)")
+    ap.add_argument("--csf", action="store_true",
+                    help="add the CSF term sigma D(beta kappa G f_drop), sigma = 0.03, to the RHS and dL/dsigma "
+                         "to the adjoint (the 1024^3 workload: --n 1024 --csf --no-e2e)")
     return ap.parse_args()
 
 
@@ -183,9 +193,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     n = args.n
     geom = D.scaled_geometry(n)
-    fd, ff = D.fractions_ramp(geom, device=dev)
-    u = D.face_velocities(n, seed=0, device=dev)
-    w = D.normal_weights((n, n, n), seed=1, device=dev)
+    fd, ff = D.fractions_ramp(geom, device=dev, z_chunk=32)
+    u = D.face_velocities(n, seed=0, device=dev, z_chunk=32)
+    w = D.normal_weights((n, n, n), seed=1, device=dev, chunk=1 << 26)
     torch.cuda.synchronize()
 
     s = Solver((n, n, n), precision="mixed", coarsest=8, rtol=1e-10, max_cycles=200, inner_cycles=INNER)
@@ -195,14 +205,18 @@ def run_ours(args):
     lam = torch.empty_like(rho)
     stats = {}
 
+    sigma = SIGMA if args.csf else 0.0
+
     def step(fd_, ff_, u_, w_, p_=p, lam_=lam):
         s.density_from_fractions([fd_, ff_], RHO_PHASE, out=rho)
         s.set_density(rho)
-        s.rhs(u=u_, out=b)
+        csf = s.csf_faces(fd_, D.curvature_band(fd_, geom)) if args.csf else None
+        s.rhs(u=u_, csf=csf, sigma=sigma, out=b)
         s.solve(b, p_)
         stats["fwd"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms)
-        _, g, _ = s.adjoint(w_, p_, lam=lam_)
+        _, g, dlds = s.adjoint(w_, p_, csf=csf, sigma=sigma, lam=lam_)
         stats["adj"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms)
+        stats["dlds"] = dlds
         return g
 
     def barrier():
@@ -282,6 +296,9 @@ def run_ours(args):
         s64.close()
         s.solve(b, p)  # restore p for the gradient pass below
 
+    # with the CSF term the gradient pass also reads the CSF faces and the face coefficients
+    class_bytes = dict(CLASS_BYTES, adjoint_grad=CLASS_BYTES["adjoint_grad"] + (48.0 if args.csf else 0.0))
+
     # ---- rooflines: finest-level FP32 half sweep (HBM) and FP64 outer residual (FP64 ALU)
     cells = n**3
     n_sm, ms_sm = prof["smooth"]
@@ -318,7 +335,7 @@ def run_ours(args):
     out = {
         "metric": METRIC,
         "value": round(value, 4),
-        "unit": "Gcell/s (512^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
+        "unit": f"Gcell/s ({n}^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -329,7 +346,8 @@ def run_ours(args):
         "dtype": "f32 inner V-cycle / f64 outer residual, update, coarse solve",
         "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
         "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, mixed V(2,2) with {INNER} "
-                               f"FP32 V-cycles per FP64 outer residual, coarsest 8^3, rtol 1e-10, forward + adjoint",
+                               f"FP32 V-cycles per FP64 outer residual, coarsest 8^3, rtol 1e-10, forward + adjoint"
+                               + (f", CSF term sigma {SIGMA} with dL/dsigma" if args.csf else ""),
                    "cells": cells, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
         "breakdown": {
@@ -348,6 +366,10 @@ def run_ours(args):
             "roofline_smoother": roof_sm,
             "roofline_fp64_residual": roof_fr,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+            "kernel_hbm_gbs": {**{k: (round(class_bytes[k] * cells * v[0] / (v[1] * 1e-3) / 1e9, 1)
+                                      if v[1] > 0 and k in class_bytes else None) for k, v in prof.items()},
+                               "smooth": round(gbs_sm, 1)},
+            "dL_dsigma": stats.get("dlds") if args.csf else None,
             "kernel_launches_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         },
         "roofline": roofline,
@@ -479,7 +501,7 @@ def run_reference(args):
         "impl": "reference",
         "metric": METRIC,
         "value": round(v, 6),
-        "unit": "Gcell/s (512^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
+        "unit": f"Gcell/s ({n}^3 cells per step / step time; step = set-up + mixed solve to 1e-10 + adjoint)",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,

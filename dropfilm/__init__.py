@@ -171,12 +171,13 @@ def fractions_ramp(geom: Geometry, width: float = 1.5, device="cpu", z_chunk: in
     return f_drop, f_film
 
 
-def face_velocities(n: int, seed: int = 0, device="cpu"):
+def face_velocities(n: int, seed: int = 0, device="cpu", z_chunk: int = None):
     """Random face velocities u ~ U[-1, 1] on interior faces, 0 on the walls.
 
     Shapes: ux (n, n, n+1), uy (n, n+1, n), uz (n+1, n, n) -- face index i of
     ux lies between cells i-1 and i.  One SplitMix64 stream per seed, read in
     C order of ux, then uy, then uz (wall entries consume a number too).
+    ``z_chunk`` generates that many z-slices at a time (same values, bounded temporaries).
     """
     shapes = [(n, n, n + 1), (n, n + 1, n), (n + 1, n, n)]
     out = []
@@ -185,9 +186,14 @@ def face_velocities(n: int, seed: int = 0, device="cpu"):
         cnt = 1
         for s in shp:
             cnt *= s
-        ctr = torch.arange(base, base + cnt, device=device, dtype=torch.int64).view(shp)
-        u = 2.0 * uniform53(seed, ctr) - 1.0
-        del ctr
+        slab = shp[1] * shp[2]
+        u = torch.empty(shp, dtype=torch.float64, device=device)
+        step = shp[0] if z_chunk is None else z_chunk
+        for z0 in range(0, shp[0], step):
+            z1 = min(shp[0], z0 + step)
+            ctr = torch.arange(base + z0 * slab, base + z1 * slab, device=device, dtype=torch.int64)
+            u[z0:z1] = (2.0 * uniform53(seed, ctr) - 1.0).view(z1 - z0, shp[1], shp[2])
+            del ctr
         # walls: first and last face along the face-normal axis
         if axis == 0:
             u[:, :, 0] = 0.0
@@ -203,18 +209,22 @@ def face_velocities(n: int, seed: int = 0, device="cpu"):
     return tuple(out)
 
 
-def normal_weights(shape, seed: int = 1, device="cpu"):
+def normal_weights(shape, seed: int = 1, device="cpu", chunk: int = None):
     """w ~ N(0, 1) by Box-Muller on consecutive SplitMix64 pairs (cos branch).
 
     Element m uses counters 2m (u1, mapped to (0, 1] as 1 - U) and 2m+1 (u2).
+    ``chunk`` generates that many elements at a time (same values, bounded temporaries).
     """
     cnt = 1
     for s in shape:
         cnt *= s
-    m = torch.arange(cnt, device=device, dtype=torch.int64)
-    u1 = 1.0 - uniform53(seed, 2 * m)
-    u2 = uniform53(seed, 2 * m + 1)
-    w = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos((2.0 * math.pi) * u2)
+    w = torch.empty(cnt, dtype=torch.float64, device=device)
+    step = cnt if chunk is None else chunk
+    for a in range(0, cnt, step):
+        m = torch.arange(a, min(cnt, a + step), device=device, dtype=torch.int64)
+        u1 = 1.0 - uniform53(seed, 2 * m)
+        u2 = uniform53(seed, 2 * m + 1)
+        w[a:a + m.numel()] = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos((2.0 * math.pi) * u2)
     return w.view(*shape)
 
 
@@ -225,5 +235,8 @@ def curvature_band(f_drop: torch.Tensor, geom: Geometry) -> torch.Tensor:
     the smeared interface band and is 0 elsewhere.
     """
     kappa = 2.0 / (geom.radius / geom.n)
-    band = (f_drop > 0.0) & (f_drop < 1.0)
-    return torch.where(band, torch.full_like(f_drop, kappa), torch.zeros_like(f_drop))
+    out = torch.zeros_like(f_drop)
+    for z0 in range(0, f_drop.shape[0], 64):  # bounded temporaries at large n
+        f = f_drop[z0:z0 + 64]
+        out[z0:z0 + 64].masked_fill_((f > 0.0) & (f < 1.0), kappa)
+    return out
