@@ -428,6 +428,125 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
     }
 }
 
+// Prefetching form of k_half_z for the s-form regular sweep (the finest level's dominant
+// kernel).  At plane z a thread first issues the loads of plane z+1 (rows y +- 1 of the other
+// colour, its own s and b, the window scalars of its warp's edge lanes) and the other colour's
+// row y of plane z+2, then computes plane z from values loaded one plane earlier: two planes of
+// loads are in flight per thread instead of one.  The other colour is only read in a half
+// sweep, so loading it early reads the same values.  Arithmetic as k_half_z.
+struct PlaneLoads {
+    float4 ym, yp, s2, s3, sc, bb;
+    float xl, xr, sl, sr;  // window scalars, used by lanes 0 and 31 only
+};
+
+template <int ZC, int MINB>
+__global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const float *__restrict__ sv,
+                                                       const float *__restrict__ b, float *xv, int col) {
+    const int hx = L.hx, kv = hx >> 2;
+    const int kvi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int yi = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = kvi < kv && yi < L.ny;
+    const int k0 = min(kvi, kv - 1) << 2;
+    const int y = min(yi, L.ny - 1);
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, L.nz);
+    const int lane = threadIdx.x & 31;
+    const i64 dy = hx, dz = (i64)L.ny * hx;
+    const bool hy0 = y > 0, hy1 = y < L.ny - 1;
+    const bool kl = k0 > 0, kr = k0 + 4 < hx;
+    const i64 row0 = ((i64)z0 * L.ny + y) * hx + k0;
+    i64 opp = (i64)(1 - col) * L.half + row0;
+    i64 own = (i64)col * L.half + row0;
+    const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
+    auto load_plane = [&](i64 o, i64 w, PlaneLoads &P) {
+        P.ym = hy0 ? ld(xv, o - dy) : f0;
+        P.yp = hy1 ? ld(xv, o + dy) : f0;
+        P.s2 = hy0 ? ld(sv, o - dy) : f0;
+        P.s3 = hy1 ? ld(sv, o + dy) : f0;
+        P.sc = ld(sv, w);
+        P.bb = ld(b, w);
+        P.xl = P.sl = P.xr = P.sr = 0.f;
+        if (lane == 0 && kl) {
+            P.xl = xv[o - 1];
+            P.sl = sv[o - 1];
+        }
+        if (lane == 31 && kr) {
+            P.xr = xv[o + 4];
+            P.sr = sv[o + 4];
+        }
+    };
+    // other colour, row y: planes z-1, z, z+1 (rolling)
+    float4 xzm = z0 > 0 ? ld(xv, opp - dz) : f0, xzc = ld(xv, opp);
+    float4 szm = z0 > 0 ? ld(sv, opp - dz) : f0, szc = ld(sv, opp);
+    float4 xzp = z0 + 1 < L.nz ? ld(xv, opp + dz) : f0, szp = z0 + 1 < L.nz ? ld(sv, opp + dz) : f0;
+    PlaneLoads cur, nxt;
+    load_plane(opp, own, cur);
+    const float hh = 2.f * h2;
+    for (int z = z0; z < z1; ++z) {
+        // loads for the next plane first
+        float4 xzpp = f0, szpp = f0;
+        if (z + 1 < z1) {
+            load_plane(opp + dz, own + dz, nxt);
+            if (z + 2 < L.nz) {
+                xzpp = ld(xv, opp + 2 * dz);
+                szpp = ld(sv, opp + 2 * dz);
+            }
+        }
+        const bool hz0 = z > 0, hz1 = z < L.nz - 1;
+        const int p = (col + y + z) & 1;  // x = 2k + p
+        const bool xw0 = (p == 0 && !kl), xw1 = (p == 1 && !kr);
+        float sl = __shfl_up_sync(0xffffffffu, szc.w, 1), sr = __shfl_down_sync(0xffffffffu, szc.x, 1);
+        float xl = __shfl_up_sync(0xffffffffu, xzc.w, 1), xr = __shfl_down_sync(0xffffffffu, xzc.x, 1);
+        if (lane == 0) {
+            sl = cur.sl;
+            xl = cur.xl;
+        }
+        if (lane == 31) {
+            sr = cur.sr;
+            xr = cur.xr;
+        }
+        const float so[4] = {szc.x, szc.y, szc.z, szc.w}, sc[4] = {cur.sc.x, cur.sc.y, cur.sc.z, cur.sc.w};
+        const float s2v[4] = {cur.s2.x, cur.s2.y, cur.s2.z, cur.s2.w}, s3v[4] = {cur.s3.x, cur.s3.y, cur.s3.z, cur.s3.w};
+        const float s4v[4] = {szm.x, szm.y, szm.z, szm.w}, s5v[4] = {szp.x, szp.y, szp.z, szp.w};
+        const float xov[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
+        const float ymv[4] = {cur.ym.x, cur.ym.y, cur.ym.z, cur.ym.w}, ypv[4] = {cur.yp.x, cur.yp.y, cur.yp.z, cur.yp.w};
+        const float zmv[4] = {xzm.x, xzm.y, xzm.z, xzm.w}, zpv[4] = {xzp.x, xzp.y, xzp.z, xzp.w};
+        const float bv[4] = {cur.bb.x, cur.bb.y, cur.bb.z, cur.bb.w};
+        float out[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float sm = p ? so[v] : (v ? so[v - 1] : sl);
+            const float sp = p ? (v < 3 ? so[v + 1] : sr) : so[v];
+            const float w0 = (v == 0 && xw0) ? 0.f : sc[v] + sm;
+            const float w1 = (v == 3 && xw1) ? 0.f : sc[v] + sp;
+            const float w2 = hy0 ? sc[v] + s2v[v] : 0.f;
+            const float w3 = hy1 ? sc[v] + s3v[v] : 0.f;
+            const float w4 = hz0 ? sc[v] + s4v[v] : 0.f;
+            const float w5 = hz1 ? sc[v] + s5v[v] : 0.f;
+            const float xm = p ? xov[v] : (v ? xov[v - 1] : xl);
+            const float xp = (v == 3 && xw1) ? 0.f : (p ? (v < 3 ? xov[v + 1] : xr) : xov[v]);
+            float num = w0 * xm;
+            num += w1 * xp;
+            num += w2 * ymv[v];
+            num += w3 * ypv[v];
+            num += w4 * zmv[v];
+            num += w5 * zpv[v];
+            const float den = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
+            out[v] = __fdividef(hh * bv[v] + num, den);
+        }
+        if (active) *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+        xzm = xzc;
+        xzc = xzp;
+        xzp = xzpp;
+        szm = szc;
+        szc = szp;
+        szp = szpp;
+        cur = nxt;
+        own += dz;
+        opp += dz;
+    }
+}
+
 bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
 
 // 16 planes per thread where that still gives about 4 waves of 64-thread blocks (12 resident
@@ -440,6 +559,10 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
     const int ry = 64 / vb;                    // rows per block
     const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
     const dim3 blk(vb, ry);
+    if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 8) {
+        k_half_zp<16, 8><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf.s, b, x, col);
+        return;
+    }
     if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 12)
         k_half_z<SFORM, FROM_ZERO, UPDATE, 16><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf, b, x, col, up);
     else
