@@ -57,6 +57,16 @@ CLASS_BYTES = {"resid_restrict": 10.5, "prolong": 4.5, "update": 26.0, "fine_res
                "adjoint_grad": 28.0}
 
 
+def workload_config(n, csf, world):
+    """The `config` of both arms' JSON lines: the workload, whichever implementation solves it."""
+    return {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, V(2,2), coarsest 8^3, rtol 1e-10, "
+                        f"forward + adjoint" + (f", CSF term sigma {SIGMA} with dL/dsigma" if csf else ""),
+            "method": f"mixed: {INNER} FP32 V-cycles per FP64 outer residual and update (reference arm: the "
+                      f"FP64 CPU oracle's V-cycle)",
+            "cells": n**3, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,11 +356,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32 inner V-cycle / f64 outer residual, update, coarse solve",
         "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
-        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, mixed V(2,2) with {INNER} "
-                               f"FP32 V-cycles per FP64 outer residual, coarsest 8^3, rtol 1e-10, forward + adjoint"
-                               + (f", CSF term sigma {SIGMA} with dL/dsigma" if args.csf else ""),
-                   "cells": cells, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(n, args.csf, world),
         "breakdown": {
             "time_to_tol_ms": {"mixed": round(t_mixed, 3),
                                **{k: round(v[0], 3) for k, v in variants.items()},
@@ -512,8 +518,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded drop-on-film fractions, SplitMix64 face velocities and weights)",
-        "config": {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, V(2,2), coarsest 8^3, "
-                               f"rtol 1e-10, forward + adjoint", "cells": n**3},
+        "config": workload_config(n, args.csf, world),
         "cpu_baseline": {"value": round(v, 6), "unit": "Gcell/s", "cores": samples[0]["cores"],
                          "kind": "oracle", "sample": samples[0]["sample"]},
         "e2e": {"value": round(v, 6), "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

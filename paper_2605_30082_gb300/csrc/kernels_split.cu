@@ -572,8 +572,10 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
 // ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
 // The red children of coarse cell (I, J, K) are the red cells at k = I of the 4 fine rows
 // (2J + b, 2K + c); one thread handles coarse cells I0..I0+3 of one coarse row.
+constexpr int kRrThreads = 64;
+
 template <bool SFORM>
-__global__ void k_rr_red_vec(Lay L, Lay Lc, float ih2, Coef32 cf, const float *__restrict__ b,
+__global__ void __launch_bounds__(kRrThreads, 12) k_rr_red_vec(Lay L, Lay Lc, float ih2, Coef32 cf, const float *__restrict__ b,
                              const float *__restrict__ xv, float *bc) {
     const int hx = L.hx, kv = hx >> 2;
     const i64 T = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -730,7 +732,9 @@ __global__ void k_prolong_red_vec(Lay L, Lay Lc, const float *__restrict__ ec, f
 // the red cell at k (x = 2k + p, coarse I = k) gains 3/4 R(I) + 1/4 R(I + 2p - 1), clamped.
 // Each coarse row supplies I = k0 - 1 .. k0 + 8: two float4 (even and odd I, one per colour
 // half) and two scalars.
-__global__ void k_prolong_red8(Lay L, Lay Lc, const float *__restrict__ ec, float *xv) {
+constexpr int kProlThreads = 64;
+
+__global__ void __launch_bounds__(kProlThreads, 10) k_prolong_red8(Lay L, Lay Lc, const float *__restrict__ ec, float *xv) {
     const int hx = L.hx, kv = hx >> 3;  // 8-cell groups per fine row
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 crows = (i64)Lc.ny * Lc.nz;
@@ -1026,8 +1030,9 @@ void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const fl
     count_launch();
     if (red_only && L.split && L.hx % 4 == 0) {
         const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 4);
-        if (sinv) k_rr_red_vec<true><<<blocks_for(work), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
-        else k_rr_red_vec<false><<<blocks_for(work), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        const unsigned nb = (unsigned)((work + kRrThreads - 1) / kRrThreads);
+        if (sinv) k_rr_red_vec<true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        else k_rr_red_vec<false><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         return;
     }
     k_resid_restrict_any<<<blocks_for(Lc.n), kThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc, red_only ? 1 : 0);
@@ -1038,7 +1043,7 @@ void launch_prolong32(cudaStream_t s, Lay L, Lay Lc, const float *ec, float *x, 
     if (only_col == 0 && kind == MG_PROLONG_TRILINEAR && L.split && Lc.split && Lc.nx % 8 == 0 &&
         2 * Lc.nx == L.nx && 2 * Lc.ny == L.ny && 2 * Lc.nz == L.nz) {
         const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 8);
-        k_prolong_red8<<<blocks_for(work), kThreads, 0, s>>>(L, Lc, ec, x);
+        k_prolong_red8<<<(unsigned)((work + kProlThreads - 1) / kProlThreads), kProlThreads, 0, s>>>(L, Lc, ec, x);
         return;
     }
     if (only_col == 0 && L.split && L.hx % 4 == 0) {
