@@ -57,6 +57,19 @@ CLASS_BYTES = {"resid_restrict": 10.5, "prolong": 4.5, "update": 26.0, "fine_res
                "adjoint_grad": 28.0}
 
 
+def max_over_ranks(x, device=None):
+    """The largest of the ranks' values of x (the job's time is its slowest rank's); x itself
+    without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(n, csf, world):
     """The `config` of both arms' JSON lines: the workload, whichever implementation solves it."""
     return {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, V(2,2), coarsest 8^3, rtol 1e-10, "
@@ -260,12 +273,7 @@ def run_ours(args):
         ("update", L.MG_PROF_UPDATE), ("adjoint_grad", L.MG_PROF_ADJOINT_GRAD)]}
     s.profile(False)
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     ms_step = ms_total / args.steps
 
     # ---- time-to-tolerance: mixed vs plain FP64 forward solve (median of 3)
