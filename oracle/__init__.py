@@ -57,6 +57,7 @@ def lib():
             "or_mg_level_faces": (None, [v, i, v, v, v]),
             "or_mg_vcycle": (None, [v, v, v]),
             "or_mg_solve": (i, [v, v, v, d, i, i, i, v, i, C.POINTER(i), C.POINTER(d)]),
+            "or_mg_fcg": (i, [v, v, v, d, i, v, i, C.POINTER(i), C.POINTER(d), v, v, i]),
             "or_adjoint_grads": (None, [i, i, i, d, v, v, v, v, v, v, v, v, d, v, v, v, C.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
@@ -292,6 +293,23 @@ class Multigrid:
         st = lib().or_mg_solve(self._h, _p(b), _p(p), float(rtol), int(max_cycles), int(warm),
                                int(stop_on_stall), _p(hist), hist_len, C.byref(nc), C.byref(rr))
         return p, st, nc.value, rr.value, hist[: min(nc.value + 1, hist_len)].copy()
+
+    def fcg(self, b, rtol=1e-10, max_it=200, hist_len=256, record=0):
+        """Flexible CG preconditioned by one V-cycle (see or_mg_fcg).
+
+        Returns (p, status, iterations, true relres, history[, (r_k, z_k) for k < record])."""
+        b = _f64(b)
+        p = np.zeros_like(b)
+        hist = np.zeros(hist_len)
+        nit = C.c_int(0)
+        rr = C.c_double(0.0)
+        rec_r = np.zeros((record,) + b.shape) if record else None
+        rec_z = np.zeros((record,) + b.shape) if record else None
+        st = lib().or_mg_fcg(self._h, _p(b), _p(p), float(rtol), int(max_it), _p(hist), hist_len,
+                             C.byref(nit), C.byref(rr), _p(rec_r) if record else None,
+                             _p(rec_z) if record else None, int(record))
+        out = (p, st, nit.value, rr.value, hist[: min(nit.value + 1, hist_len)].copy())
+        return out + ((rec_r, rec_z),) if record else out
 
     def solve_exact(self, b, max_cycles=400):
         """The zero-mean discrete solution p* = A^+(b - mean b): V-cycles to stagnation.

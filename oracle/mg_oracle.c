@@ -691,6 +691,98 @@ int or_mg_solve(or_mg *M, const double *b_in, double *p, double rtol, int max_cy
     return OR_ERR_NOT_CONVERGED;
 }
 
+/* ---- flexible preconditioned conjugate gradients ------------------------- */
+/* a . b, summed per z-plane then over planes in order (deterministic at any thread count) */
+static double dot(int nx, int ny, int nz, const double *a, const double *b) {
+    const idx_t nxy = (idx_t)nx * ny;
+    double *ps = (double *)calloc((size_t)nz, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+        double s = 0.0;
+        for (idx_t m = (idx_t)k * nxy; m < (idx_t)(k + 1) * nxy; ++m) s += a[m] * b[m];
+        ps[k] = s;
+    }
+    double s = 0.0;
+    for (int k = 0; k < nz; ++k) s += ps[k];
+    free(ps);
+    return s;
+}
+
+/* Solve A p = b~ (b~ = b - mean b) by conjugate gradients preconditioned with one V-cycle
+ * from zero, z = V(r), in the flexible form: the Polak-Ribiere choice of beta keeps it a
+ * descent method when the preconditioner is not exactly symmetric (trilinear prolongation
+ * with averaging restriction, or a preconditioner applied in lower precision); with a
+ * symmetric preconditioner it is ordinary preconditioned CG.  Starting from p = 0:
+ *     r_0 = b~,  z_0 = V(r_0),  d_0 = z_0
+ *     for k = 0, 1, ...
+ *         q = A d_k,   alpha = (r_k . z_k) / (d_k . q)
+ *         p += alpha d_k,   r_{k+1} = r_k - alpha q        (stop once |r_{k+1}| <= rtol |b~|)
+ *         z_{k+1} = V(r_{k+1})
+ *         beta = z_{k+1} . (r_{k+1} - r_k) / (r_k . z_k) = -alpha (z_{k+1} . q) / (r_k . z_k)
+ *         d_{k+1} = z_{k+1} + beta d_k
+ * hist[k] = |r_k| / |b~| (the updated residual); at exit p gets zero mean and *relres is
+ * the true relative residual |b~ - A p| / |b~|.  rec_r, rec_z (may be NULL) receive r_k
+ * and z_k for k < rec_n, one cell array each. */
+int or_mg_fcg(or_mg *M, const double *b_in, double *p, double rtol, int max_it, double *hist,
+              int hist_len, int *nit, double *relres, double *rec_r, double *rec_z, int rec_n) {
+    or_level *F = &M->lv[0];
+    int nx = F->nx, ny = F->ny, nz = F->nz;
+    idx_t n = (idx_t)nx * ny * nz;
+    double h = F->h;
+    double *b = F->b;
+    double mb = or_mean(nx, ny, nz, b_in);
+    for (idx_t m = 0; m < n; ++m) b[m] = b_in[m] - mb;
+    double nb = or_norm2(nx, ny, nz, b);
+    memset(p, 0, sizeof(double) * (size_t)n);
+    *nit = 0;
+    *relres = 0.0;
+    if (hist && hist_len > 0) hist[0] = nb == 0.0 ? 0.0 : 1.0;
+    if (nb == 0.0) return OR_OK;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *z = (double *)calloc((size_t)n, sizeof(double));
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    memcpy(r, b, sizeof(double) * (size_t)n);
+    vcycle(M, 0, r, z);
+    memcpy(d, z, sizeof(double) * (size_t)n);
+    double rz = dot(nx, ny, nz, r, z);
+    int status = OR_ERR_NOT_CONVERGED;
+    for (int k = 0; k < max_it; ++k) {
+        if (rec_r && k < rec_n) memcpy(rec_r + (idx_t)k * n, r, sizeof(double) * (size_t)n);
+        if (rec_z && k < rec_n) memcpy(rec_z + (idx_t)k * n, z, sizeof(double) * (size_t)n);
+        or_apply(nx, ny, nz, h, F->bx, F->by, F->bz, d, q);
+        double alpha = rz / dot(nx, ny, nz, d, q);
+        for (idx_t m = 0; m < n; ++m) {
+            p[m] += alpha * d[m];
+            r[m] -= alpha * q[m];
+        }
+        double rr = or_norm2(nx, ny, nz, r) / nb;
+        *nit = k + 1;
+        if (hist && k + 1 < hist_len) hist[k + 1] = rr;
+        if (!isfinite(rr)) {
+            status = OR_ERR_DIVERGED;
+            break;
+        }
+        if (rr <= rtol) {
+            status = OR_OK;
+            break;
+        }
+        memset(z, 0, sizeof(double) * (size_t)n);
+        vcycle(M, 0, r, z);
+        double beta = -alpha * dot(nx, ny, nz, z, q) / rz;
+        rz = dot(nx, ny, nz, r, z);
+        for (idx_t m = 0; m < n; ++m) d[m] = z[m] + beta * d[m];
+    }
+    add_const(nx, ny, nz, p, -or_mean(nx, ny, nz, p));
+    or_residual(nx, ny, nz, h, F->bx, F->by, F->bz, b, p, F->r);
+    *relres = or_norm2(nx, ny, nz, F->r) / nb;
+    free(r);
+    free(z);
+    free(d);
+    free(q);
+    return status;
+}
+
 /* ---- adjoint gradients ------------------------------------------------------ */
 /* Given lambda = A^+(w - mean w) and the forward p, write
  *   g_f = -(lambda_L - lambda_R)(p_L - p_R)/h^2 + sigma csf_f (lambda_L - lambda_R)/h

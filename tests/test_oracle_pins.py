@@ -331,6 +331,49 @@ def test_vcycle_solve_matches_dense_solve_8cubed(field, coarsest):
     assert all(hist[1:] < hist[:-1])  # monotone residual decrease
 
 
+@pytest.mark.parametrize("field", ["dropfilm", "random"])
+@pytest.mark.parametrize("prolong", [O.TRILINEAR, O.CONSTANT])
+def test_fcg_solve_matches_dense_solve_8cubed(field, prolong):
+    """Flexible CG preconditioned by the V-cycle reaches the same zero-mean discrete solution."""
+    n, h = 8, 1 / 8
+    if field == "dropfilm":
+        fd, ff = D.fractions_ramp(D.scaled_geometry(8))
+        faces = O.faces_from_density(O.density([fd.numpy(), ff.numpy()], [998.0, 880.0, 1.2]))
+    else:
+        faces, _ = random_faces(n, n, n, seed=13)
+    b = O.divergence([a.numpy() for a in D.face_velocities(n, seed=0)], h)
+    M = O.Multigrid(faces, h, coarsest=2, prolong=prolong)
+    p, st, nit, rr, hist = M.fcg(b, rtol=1e-13)
+    assert st == O.OK and rr <= 1e-12
+    assert abs(p.mean()) < 1e-14 * np.abs(p).max()
+    assert rel(p, _dense_p(faces, b, h)) < 1e-11
+    assert nit < M.solve(b, rtol=1e-13)[2]  # fewer iterations than the plain V-cycle
+
+
+def test_fcg_residuals_are_preconditioner_orthogonal():
+    """With constant prolongation (restriction = P^T / 8, post-smoother the adjoint of the
+    pre-smoother) the V-cycle is a symmetric preconditioner M, and preconditioned CG makes its
+    residuals M^-1-orthogonal: r_j . z_k = 0 for j != k, z_k = M^-1 r_k.  With trilinear
+    prolongation only the flexible method's local condition r_(k+1) . z_k = 0 holds.  A wrong
+    step length or direction update breaks either."""
+    n = 16
+    faces, _ = random_faces(n, n, n, seed=4)
+    b = np.random.default_rng(1).standard_normal((n, n, n))
+
+    def gram(prolong):
+        M = O.Multigrid(faces, 1 / n, coarsest=4, prolong=prolong)
+        R, Z = M.fcg(b, rtol=1e-12, record=6)[5]
+        return np.array([[np.vdot(R[j], Z[k]) / (np.linalg.norm(R[j]) * np.linalg.norm(Z[k])) for k in range(6)]
+                         for j in range(6)])
+
+    G = gram(O.CONSTANT)
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() < 1e-12 and np.diag(G).min() > 0.1
+    G = gram(O.TRILINEAR)
+    assert max(abs(G[k + 1, k]) for k in range(5)) < 1e-12
+    assert np.abs(G - np.diag(np.diag(G))).max() > 1e-6  # not symmetric: the global condition fails
+
+
 def test_solve_cosine_mode_exact_on_dropfilm_free_grid():
     # constant coefficient: b = lambda * p* must return p* (zero mean)
     nx = ny = nz = 32
