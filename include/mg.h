@@ -77,6 +77,7 @@ enum {
 };
 
 enum { MG_FP64 = 0, MG_MIXED = 1, MG_MIXED_DF = 2 };
+enum { MG_METHOD_VCYCLE = 0, MG_METHOD_FCG = 1 }; /* mg_opts.method */
 enum { MG_PROLONG_TRILINEAR = 0, MG_PROLONG_CONSTANT = 1 };
 enum { MG_F64 = 0, MG_F32 = 1 }; /* element type of component-level arrays */
 
@@ -100,7 +101,15 @@ typedef struct {
     int inner_cycles; /* mixed modes: FP32 V-cycles per outer iteration (1..8), the first from
                          zero, the next ones continuing from the previous correction; the
                          FP64 (or double-float) residual and update run once per outer
+                         iteration.  With MG_METHOD_FCG: the flexible-CG iterations per outer
                          iteration.  Must be 1 for MG_FP64. */
+    int method;       /* MG_METHOD_VCYCLE: V-cycle iteration (defect correction in the mixed
+                         modes).  MG_METHOD_FCG: conjugate gradients preconditioned by one
+                         V-cycle, flexible (Polak-Ribiere) form: in MG_FP64 the whole solve, with
+                         FP64 vectors; in the mixed modes the inner solver of each outer
+                         iteration, in FP32 on the finest level (needs nx % 8 == 0).  The
+                         stopping test uses the CG-updated residual in MG_FP64 and the outer
+                         residual in the mixed modes; max_cycles counts V-cycles. */
 } mg_opts;
 
 typedef struct {
@@ -114,7 +123,7 @@ typedef struct {
 } mg_stats;
 
 /* Defaults: 2/2 sweeps, coarsest 4, trilinear, rtol 1e-10, 200 cycles, FP64, cold start,
-   one V-cycle per outer iteration. */
+   one V-cycle per outer iteration, V-cycle iteration (MG_METHOD_VCYCLE). */
 void mg_default_opts(mg_opts *opts);
 
 /* Create a solver for one grid.  `stream` is a cudaStream_t (NULL = legacy

@@ -20,6 +20,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_DENSITY, MG_ERR_NOT_CONVERGED = 0, -1, -2, -3
 MG_ERR_DIVERGED, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_STATE = -4, -5, -6, -7
 MG_FP64, MG_MIXED, MG_MIXED_DF = 0, 1, 2
 MG_PROLONG_TRILINEAR, MG_PROLONG_CONSTANT = 0, 1
+MG_METHOD_VCYCLE, MG_METHOD_FCG = 0, 1
 MG_F64, MG_F32 = 0, 1
 MG_MAX_LEVELS, MG_MAX_COARSE, MG_HIST_LEN = 24, 1024, 256
 MG_NOALLOC_MAX_CELLS = 512
@@ -37,7 +38,8 @@ class mg_opts(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
                 ("precision", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarsest", C.c_int), ("prolong", C.c_int), ("rtol", C.c_double),
-                ("max_cycles", C.c_int), ("warm_start", C.c_int), ("inner_cycles", C.c_int)]
+                ("max_cycles", C.c_int), ("warm_start", C.c_int), ("inner_cycles", C.c_int),
+                ("method", C.c_int)]
 
 
 class mg_stats(C.Structure):

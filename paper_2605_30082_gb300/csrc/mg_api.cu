@@ -54,6 +54,11 @@ struct mg_handle {
     double *bt;        // zero-mean fine RHS (scaled by h^2 in the mixed modes)
     float2 *bt2, *p2;  // MIXED_DF: the RHS and the solution as FP32 pairs
     double *partials;  // reduction partials
+    // flexible CG (MG_METHOD_FCG): FP32 finest-level vectors (mixed; r and x are the level's
+    // b32 and x32), FP64 vectors (MG_FP64), device scalars
+    float *cg_z32, *cg_d32, *cg_q32;
+    double *cg_r64, *cg_z64, *cg_d64, *cg_q64;
+    double *cg_sc;
     double *red;       // device reduction results (16 doubles)
     double *hred;      // pinned host copy of red
     unsigned *err;     // device error word
@@ -317,6 +322,27 @@ int finish_operator(mg_handle *h) {
     return MG_OK;
 }
 
+// ---- flexible CG preconditioned by one V-cycle ------------------------------------------
+// k iterations on the finest FP32 level for A32 x = r from x = 0 (r = the level's b32, the
+// scaled outer residual, overwritten by the updated residual; x = the level's x32).  Every
+// scalar stays on the device (slots of cg_sc); r . z of the current and the previous
+// iteration alternate between two slots.
+void inner_fcg32(mg_handle *h, int k) {
+    Level &F = h->lv[0];
+    cudaStream_t s = h->s;
+    const i64 n = F.d.n;
+    cudaMemsetAsync(F.x32, 0, sizeof(float) * (size_t)n, s);
+    for (int j = 0; j < k; ++j) {
+        const int rz_cur = (j & 1) ? mg::CG_RZ1 : mg::CG_RZ0, rz_prev = (j & 1) ? mg::CG_RZ0 : mg::CG_RZ1;
+        vcycle32(h, 0, F.b32, h->cg_z32);  // z = V(r)
+        mg::launch_cg_dots32(s, n, F.b32, h->cg_z32, h->cg_q32, h->partials, h->cg_sc, rz_cur);
+        mg::launch_cg_dir32(s, n, h->cg_z32, h->cg_d32, h->cg_sc, j == 0, rz_prev);
+        mg::launch_cg_apply32(s, F.lay, F.ih2, sinv32(h, 0), F.fx32, F.fy32, F.fz32, h->cg_d32, h->cg_q32,
+                              h->partials, h->cg_sc);
+        mg::launch_cg_update32(s, n, F.x32, F.b32, h->cg_d32, h->cg_q32, h->cg_sc, rz_cur);
+    }
+}
+
 // ---- one solve A x = b - mean(b), zero-mean x -------------------------------------------
 int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st) {
     cudaStream_t s = h->s;
@@ -342,6 +368,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     int status = MG_OK;
     int cycles = 0, outer = 0;
     const int inner = mixed ? h->o.inner_cycles : 1;
+    const bool fcg = h->o.method == MG_METHOD_FCG;
     double rr = 0.0;
     if (nb == 0.0) {
         MG_CUDA(h, cudaMemsetAsync(p, 0, sizeof(double) * (size_t)n, s));
@@ -386,8 +413,46 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         hist[hist_n++] = rr;
         status = MG_ERR_NOT_CONVERGED;
         if (rr <= h->o.rtol) status = MG_OK;
-        for (int it = 1; cycles + inner <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++it) {
-            if (mixed) {
+        if (!mixed && fcg && status == MG_ERR_NOT_CONVERGED) {
+            // FP64 flexible CG on A p = b~, preconditioned by one FP64 V-cycle; the stopping
+            // test uses the CG-updated residual r, the exit the true residual
+            double *r = h->cg_r64, *z = h->cg_z64, *d = h->cg_d64, *q = h->cg_q64;
+            mg::launch_residual<double>(s, F.d, F.ih2, coef<double>(F), h->bt, p, r);
+            for (int j = 0; j < h->o.max_cycles && status == MG_ERR_NOT_CONVERGED; ++j) {
+                const int rz_cur = (j & 1) ? mg::CG_RZ1 : mg::CG_RZ0, rz_prev = (j & 1) ? mg::CG_RZ0 : mg::CG_RZ1;
+                vcycle64(h, 0, r, z, true);
+                mg::launch_cg_dots64(s, n, r, z, q, h->partials, h->cg_sc, rz_cur);
+                mg::launch_cg_dir64(s, n, z, d, h->cg_sc, j == 0, rz_prev);
+                mg::launch_cg_apply64(s, F.d, F.ih2, F.fx64, F.fy64, F.fz64, F.d64, d, q, h->partials, h->cg_sc);
+                mg::launch_cg_update64(s, n, p, r, d, q, h->cg_sc, rz_cur, h->partials);
+                MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->cg_sc + mg::CG_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+                MG_CUDA(h, cudaStreamSynchronize(s));
+                rr = std::sqrt(h->hred[6]) / nb;
+                cycles = outer = j + 1;
+                if (hist_n < MG_HIST_LEN) hist[hist_n++] = rr;
+                if (!std::isfinite(rr) || rr > 1e12) {
+                    status = MG_ERR_DIVERGED;
+                    break;
+                }
+                if (rr <= h->o.rtol) status = MG_OK;
+            }
+            // the true residual of the final iterate
+            rc = residual(false);
+            if (rc) return rc;
+            rr = std::sqrt(h->hred[6]) * F.ih2 / nb;
+            if (status == MG_OK && rr > h->o.rtol) status = MG_ERR_NOT_CONVERGED;
+        }
+        for (int it = 1; !(fcg && !mixed) && cycles + inner <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED;
+             ++it) {
+            if (mixed && fcg) {
+                // inner_cycles flexible-CG iterations in FP32, then the outer update
+                inner_fcg32(h, inner);
+                prof_begin(h, MG_PROF_UPDATE);
+                if (df) mg::launch_update_df(s, F.d, F.lay, h->p2, F.x32, 1.0 / scale, mu);
+                else mg::launch_update(s, F.d, F.lay, p, F.x32, 1.0 / scale, mu);
+                prof_end(h);
+                scale = 1.0 / rn;
+            } else if (mixed) {
                 // inner_cycles FP32 V-cycles on the scaled residual: the first from zero, the
                 // next ones continuing from the previous correction
                 for (int q = 0; q + 1 < inner; ++q) vcycle32(h, 0, F.b32, F.x32, nullptr, q == 0);
@@ -485,6 +550,7 @@ void mg_default_opts(mg_opts *o) {
     o->max_cycles = 200;
     o->warm_start = 0;
     o->inner_cycles = 1;
+    o->method = MG_METHOD_VCYCLE;
 }
 
 int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
@@ -498,7 +564,9 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         o->pre > 64 || o->post > 64 || o->coarsest < 2 ||
         (o->prolong != MG_PROLONG_TRILINEAR && o->prolong != MG_PROLONG_CONSTANT) || !(o->rtol >= 0.0) ||
         o->max_cycles < 0 || o->inner_cycles < 1 || o->inner_cycles > 8 ||
-        (o->precision == MG_FP64 && o->inner_cycles != 1))
+        (o->precision == MG_FP64 && o->inner_cycles != 1) ||
+        (o->method != MG_METHOD_VCYCLE && o->method != MG_METHOD_FCG) ||
+        (o->method == MG_METHOD_FCG && o->precision != MG_FP64 && o->nx % 8 != 0))
         return MG_ERR_ARG;
     int nl = num_levels(o->nx, o->ny, o->nz, o->coarsest);
     if (nl > MG_MAX_LEVELS) return MG_ERR_ARG;
@@ -519,7 +587,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         void **p;
         size_t bytes;
     };
-    Slot slots[16 * MG_MAX_LEVELS + 16];
+    Slot slots[16 * MG_MAX_LEVELS + 32];
     int ns = 0;
     auto add = [&](void **p, size_t bytes) { slots[ns++] = Slot{p, (bytes + 255) & ~(size_t)255}; };
     for (int l = 0; l < nl; ++l) {
@@ -565,6 +633,20 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         add((void **)&h->p2, 8 * (size_t)h->lv[0].d.n);
     }
     add((void **)&h->partials, 16 * (size_t)mg::reduce_blocks(h->lv[0].d.n));
+    add((void **)&h->cg_sc, 8 * mg::CG_NSLOT);
+    if (o->method == MG_METHOD_FCG) {
+        const size_t n0 = (size_t)h->lv[0].d.n;
+        if (mixed) {
+            add((void **)&h->cg_z32, 4 * n0);
+            add((void **)&h->cg_d32, 4 * n0);
+            add((void **)&h->cg_q32, 4 * n0);
+        } else {
+            add((void **)&h->cg_r64, 8 * n0);
+            add((void **)&h->cg_z64, 8 * n0);
+            add((void **)&h->cg_d64, 8 * n0);
+            add((void **)&h->cg_q64, 8 * n0);
+        }
+    }
     add((void **)&h->red, 8 * 16);
     add((void **)&h->err, 256);
     size_t total = 0;

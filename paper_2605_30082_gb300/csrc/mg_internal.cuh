@@ -182,6 +182,25 @@ void launch_resid_df(cudaStream_t s, Dims d, Lay L, const float2 *fx, const floa
 // s-form double-float residual: s2 = 1/rho as FP32 pairs (natural layout), otherwise as launch_resid_df
 void launch_resid_dfs(cudaStream_t s, Dims d, Lay L, const float2 *s2, const float2 *b, const float2 *p,
                       float *r32, float s32, double *partials, double *out);
+// ---- flexible CG (kernels_cg.cu) --------------------------------------------------------
+// slots of the device scalar array: r . z of the current and of the previous iteration
+// alternate between CG_RZ0 and CG_RZ1
+enum { CG_RZ0 = 0, CG_PQ = 1, CG_ALPHA = 2, CG_ZQ = 3, CG_RZ1 = 4, CG_RR = 5, CG_SX = 6, CG_NSLOT = 8 };
+void launch_cg_apply32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
+                       const float *fz, const float *d, float *q, double *partials, double *sc);
+void launch_cg_dots32(cudaStream_t s, i64 n, const float *r, const float *z, const float *q, double *partials,
+                      double *sc, int rz_slot);
+void launch_cg_dir32(cudaStream_t s, i64 n, const float *z, float *d, const double *sc, bool first, int rz_prev);
+void launch_cg_update32(cudaStream_t s, i64 n, float *x, float *r, const float *d, const float *q, double *sc,
+                        int rz_cur);
+void launch_cg_apply64(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy, const double *fz,
+                       const double *dg, const double *dv, double *q, double *partials, double *sc);
+void launch_cg_dots64(cudaStream_t s, i64 n, const double *r, const double *z, const double *q, double *partials,
+                      double *sc, int rz_slot);
+void launch_cg_dir64(cudaStream_t s, i64 n, const double *z, double *d, const double *sc, bool first, int rz_prev);
+void launch_cg_update64(cudaStream_t s, i64 n, double *x, double *r, const double *d, const double *q, double *sc,
+                        int rz_cur, double *partials);
+
 void launch_update_df(cudaStream_t s, Dims d, Lay L, float2 *p, const float *e32, double alpha, double shift);
 // r = b - A x (or r = A x when apply_only)
 void launch_residual32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,

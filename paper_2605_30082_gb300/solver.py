@@ -25,13 +25,14 @@ class Solver:
 
     Parameters mirror ``mg_opts``: dims = (nx, ny, nz), h, precision ('fp64',
     'mixed' or 'mixed_df'), pre/post sweeps, coarsest, prolong ('trilinear' or
-    'constant'), rtol, max_cycles, warm_start, inner_cycles (mixed modes: FP32 V-cycles per
-    outer FP64 residual).
+    'constant'), rtol, max_cycles, warm_start, inner_cycles (mixed modes: FP32 V-cycles, or
+    flexible-CG iterations, per outer FP64 residual), method ('vcycle' or 'fcg': conjugate
+    gradients preconditioned by one V-cycle).
     """
 
     def __init__(self, dims, h=None, precision="mixed", pre=2, post=2, coarsest=None,
                  prolong="trilinear", rtol=1e-10, max_cycles=200, warm_start=False, stream=None,
-                 inner_cycles=1):
+                 inner_cycles=1, method="vcycle"):
         nx, ny, nz = (int(v) for v in dims)
         o = L.mg_default_opts()
         o.nx, o.ny, o.nz = nx, ny, nz
@@ -44,6 +45,7 @@ class Solver:
         o.max_cycles = int(max_cycles)
         o.warm_start = int(bool(warm_start))
         o.inner_cycles = int(inner_cycles)
+        o.method = {"vcycle": L.MG_METHOD_VCYCLE, "fcg": L.MG_METHOD_FCG}[method]
         self.opts = o
         self.dims = (nx, ny, nz)
         self.h = o.h

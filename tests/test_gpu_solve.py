@@ -92,6 +92,54 @@ def test_inner_cycles_reach_exact_32cubed(c32, prec, inner):
     assert all(b < a for a, b in zip(st.history(), st.history()[1:]))
 
 
+@pytest.mark.parametrize("prec,inner", [("fp64", 1), ("mixed", 2), ("mixed", 4), ("mixed_df", 4)])
+def test_fcg_reaches_exact_32cubed(c32, prec, inner):
+    """Conjugate gradients preconditioned by one V-cycle (flexible form): the same discrete
+    solution, in fewer V-cycles than the V-cycle iteration.  The FP64 solve runs the
+    oracle's algorithm (or_mg_fcg) step for step: same iteration count."""
+    s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8, inner_cycles=inner, method="fcg")
+    s.set_density(dev(c32["rho"]))
+    p = s.solve(dev(c32["b"]))
+    st = s.last_stats
+    assert st.relres <= 1e-10
+    assert rel(host(p), c32["exact8"]) < 1e-9
+    assert abs(host(p).mean()) < 1e-14 * np.abs(host(p)).max()
+    nc_v = c32["iter8"][2]
+    assert st.cycles < nc_v
+    if prec == "fp64":
+        M = O.Multigrid(c32["faces"], c32["h"], coarsest=8)
+        p_o, st_o, nit_o, rr_o, hist_o = M.fcg(c32["b"], rtol=1e-10)
+        assert abs(st.cycles - nit_o) <= 1
+        assert rel(host(p), p_o) < 1e-11
+        assert np.allclose(st.history()[: len(hist_o)][:5], hist_o[:5], rtol=1e-6)
+
+
+@pytest.mark.parametrize("dims", [(64, 48, 32), (96, 40, 24)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fcg_ragged_grids_match_exact(dims, prec):
+    nx, ny, nz = dims
+    h = 1.0 / 64
+    rho = random_rho(dims, 5, lo=1.2, hi=998.0)
+    faces = O.faces_from_density(rho)
+    b = np.random.default_rng(7).standard_normal((nz, ny, nx))
+    exact = O.Multigrid(faces, h, coarsest=8).solve_exact(b)[0]
+    s = Solver(dims, h=h, precision=prec, coarsest=8, max_cycles=400, inner_cycles=1 if prec == "fp64" else 3,
+               method="fcg")
+    s.set_density(dev(rho))
+    p = s.solve(dev(b))
+    assert s.last_stats.relres <= 1e-10
+    assert rel(host(p), exact) < 1e-9
+
+
+def test_fcg_limits():
+    with pytest.raises(MgError):
+        Solver((36, 32, 32), precision="mixed", method="fcg")  # mixed FCG needs nx % 8 == 0
+    s = Solver((16, 16, 16), precision="fp64", coarsest=8, rtol=1e-30, max_cycles=3, method="fcg")
+    s.set_density(dev(random_rho((16, 16, 16), 9)))
+    s.solve(dev(np.random.default_rng(3).standard_normal((16, 16, 16))), raise_on_nonconvergence=False)
+    assert s.last_stats.cycles == 3 and s.last_stats.status == MG_ERR_NOT_CONVERGED
+
+
 def test_inner_cycles_limits():
     with pytest.raises(MgError):
         Solver((16, 16, 16), precision="fp64", inner_cycles=2)
