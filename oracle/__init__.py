@@ -58,6 +58,8 @@ def lib():
             "or_mg_vcycle": (None, [v, v, v]),
             "or_mg_solve": (i, [v, v, v, d, i, i, i, v, i, C.POINTER(i), C.POINTER(d)]),
             "or_mg_fcg": (i, [v, v, v, d, i, v, i, C.POINTER(i), C.POINTER(d), v, v, i]),
+            "or_project": (None, [i, i, i, d, v, v, v, v, v, v, v, d, v, v, v]),
+            "or_density_grads": (None, [i, i, i, v, v, v, v, v, i, v, v]),
             "or_adjoint_grads": (None, [i, i, i, d, v, v, v, v, v, v, v, v, d, v, v, v, C.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
@@ -240,6 +242,35 @@ def adjoint_grads(faces, lam, p, h, csf=None, sigma=0.0):
                            _p(cs[0]), _p(cs[1]), _p(cs[2]), float(sigma),
                            _p(gx), _p(gy), _p(gz), C.byref(ds))
     return (gx, gy, gz), ds.value
+
+
+def project(u, faces, p, h, csf=None, sigma=0.0):
+    """The corrected face velocities u + beta (G p + sigma csf) (copies; walls unchanged)."""
+    ux, uy, uz = (_f64(a).copy() for a in u)
+    bx, by, bz = (_f64(f) for f in faces)
+    p = _f64(p)
+    nx, ny, nz = _dims(p)
+    cs = [None, None, None] if csf is None else [_f64(a) for a in csf]
+    lib().or_project(nx, ny, nz, float(h), _p(bx), _p(by), _p(bz), _p(p), _p(cs[0]), _p(cs[1]), _p(cs[2]),
+                     float(sigma), _p(ux), _p(uy), _p(uz))
+    return ux, uy, uz
+
+
+def density_grads(rho, grads, rho_phase=None):
+    """dL/drho from the face gradients dL/dbeta; with rho_phase (nfrac + 1 densities) also the
+    fraction gradients dL/df_q.  Returns drho or (drho, [dfrac_q])."""
+    rho = _f64(rho)
+    gx, gy, gz = (_f64(g) for g in grads)
+    nx, ny, nz = _dims(rho)
+    drho = np.empty_like(rho)
+    if rho_phase is None:
+        lib().or_density_grads(nx, ny, nz, _p(rho), _p(gx), _p(gy), _p(gz), _p(drho), 0, None, None)
+        return drho
+    ph = np.ascontiguousarray(rho_phase, dtype=np.float64)
+    nfrac = len(ph) - 1
+    dfrac = np.empty((nfrac,) + rho.shape)
+    lib().or_density_grads(nx, ny, nz, _p(rho), _p(gx), _p(gy), _p(gz), _p(drho), nfrac, _p(ph), _p(dfrac))
+    return drho, list(dfrac)
 
 
 class Multigrid:

@@ -691,6 +691,72 @@ int or_mg_solve(or_mg *M, const double *b_in, double *p, double rtol, int max_cy
     return OR_ERR_NOT_CONVERGED;
 }
 
+/* ---- projection: the velocity correction ---------------------------------- */
+/* With b = D u + sigma D(beta csf) and A p = b (A = -D diag(beta) G), the corrected face
+ * velocities u + beta (G p + sigma csf) have zero discrete divergence: on every interior face
+ *     u_f += beta_f ((p_R - p_L) / h + sigma csf_f),
+ * wall faces unchanged.  csf pointers may be NULL (no surface term). */
+void or_project(int nx, int ny, int nz, double h, const double *bx, const double *by, const double *bz,
+                const double *p, const double *csfx, const double *csfy, const double *csfz, double sigma,
+                double *ux, double *uy, double *uz) {
+    const double ih = 1.0 / h;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                if (i > 0 && i < nx) {
+                    idx_t f = ((idx_t)k * ny + j) * (nx + 1) + i;
+                    idx_t c = ((idx_t)k * ny + j) * nx + i;
+                    ux[f] += bx[f] * ((p[c] - p[c - 1]) * ih + (csfx ? sigma * csfx[f] : 0.0));
+                }
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t f = ((idx_t)k * (ny + 1) + j) * nx + i;
+                idx_t c = ((idx_t)k * ny + j) * nx + i;
+                uy[f] += by[f] * ((p[c] - p[c - nx]) * ih + (csfy ? sigma * csfy[f] : 0.0));
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t f = ((idx_t)k * ny + j) * nx + i;
+                idx_t c = f;
+                uz[f] += bz[f] * ((p[c] - p[c - (idx_t)nx * ny]) * ih + (csfz ? sigma * csfz[f] : 0.0));
+            }
+}
+
+/* ---- density adjoint -------------------------------------------------------- */
+/* beta_f = (1/rho_L + 1/rho_R) / 2, so d beta_f / d rho_c = -1 / (2 rho_c^2) for the faces of c:
+ *     dL/drho_c = -1/(2 rho_c^2) * sum over the interior faces f of c of dL/dbeta_f.
+ * With rho = sum_q rho_q f_q + rho_last (1 - sum_q f_q) (Eq. (5) for nfrac fractions),
+ *     dL/df_q = dL/drho * (rho_q - rho_last)   (dfrac: nfrac cell arrays, may be NULL). */
+void or_density_grads(int nx, int ny, int nz, const double *rho, const double *gx, const double *gy,
+                      const double *gz, double *drho, int nfrac, const double *rho_phase, double *dfrac) {
+    const idx_t n = (idx_t)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = ((idx_t)k * ny + j) * nx + i;
+                idx_t fx = ((idx_t)k * ny + j) * (nx + 1) + i;
+                idx_t fy = ((idx_t)k * (ny + 1) + j) * nx + i;
+                double g = 0.0;
+                if (i > 0) g += gx[fx];
+                if (i < nx - 1) g += gx[fx + 1];
+                if (j > 0) g += gy[fy];
+                if (j < ny - 1) g += gy[fy + nx];
+                if (k > 0) g += gz[c];
+                if (k < nz - 1) g += gz[c + (idx_t)nx * ny];
+                double d = -g / (2.0 * rho[c] * rho[c]);
+                drho[c] = d;
+                if (dfrac)
+                    for (int q = 0; q < nfrac; ++q) dfrac[q * n + c] = d * (rho_phase[q] - rho_phase[nfrac]);
+            }
+}
+
 /* ---- flexible preconditioned conjugate gradients ------------------------- */
 /* a . b, summed per z-plane then over planes in order (deterministic at any thread count) */
 static double dot(int nx, int ny, int nz, const double *a, const double *b) {

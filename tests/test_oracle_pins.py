@@ -452,3 +452,64 @@ def test_adjoint_gradients_vs_central_differences_8cubed():
     v = rng.standard_normal((n, n, n))
     fdb = (loss(faces, sigma, 1e-3 * v) - loss(faces, sigma, -1e-3 * v)) / 2e-3
     assert abs(fdb - (lam * v).sum()) <= 1e-8 * abs(fdb)
+
+
+def _dropfilm8_with_csf():
+    n, h = 8, 1 / 8
+    g = D.scaled_geometry(8)
+    fd, ff = D.fractions_ramp(g)
+    kappa = D.curvature_band(fd, g).numpy()
+    csf = O.csf_faces(fd.numpy(), kappa, h)
+    u = [a.numpy() for a in D.face_velocities(n, seed=0)]
+    return n, h, fd.numpy(), ff.numpy(), csf, u
+
+
+def test_projection_removes_the_divergence_8cubed():
+    """u + beta (G p + sigma csf) with p the exact solution of A p = D u + sigma D(beta csf)
+    has zero discrete divergence (A = -D diag(beta) G); walls are unchanged; p = 0 without a
+    surface term leaves u as it is."""
+    n, h, fd, ff, csf, u = _dropfilm8_with_csf()
+    faces = O.faces_from_density(O.density([fd, ff], [998.0, 880.0, 1.2]))
+    b = O.rhs(u, faces, h, csf=csf, sigma=0.03)
+    p = _dense_p(faces, b, h)
+    un = O.project(u, faces, p, h, csf=csf, sigma=0.03)
+    assert np.abs(O.divergence(un, h)).max() <= 1e-10 * np.abs(b).max()
+    assert np.all(un[0][:, :, [0, -1]] == u[0][:, :, [0, -1]])
+    assert np.all(un[1][:, [0, -1], :] == u[1][:, [0, -1], :])
+    assert np.all(un[2][[0, -1]] == u[2][[0, -1]])
+    same = O.project(u, faces, np.zeros_like(p), h)
+    assert all(np.array_equal(a, c) for a, c in zip(same, u))
+
+
+def test_density_and_fraction_gradients_vs_central_differences_8cubed():
+    """dL/drho and dL/df_q (L = sum w p, b = D u + sigma D(beta(rho) csf)) against central
+    differences of dense solves, rho from the fractions by Eq. (5)."""
+    n, h, fd, ff, csf, u = _dropfilm8_with_csf()
+    phase = [998.0, 880.0, 1.2]
+    w = D.normal_weights((n, n, n), seed=1).numpy()
+    sigma = 0.03
+
+    def loss_rho(rho):
+        faces = O.faces_from_density(rho)
+        return float((w * _dense_p(faces, O.rhs(u, faces, h, csf=csf, sigma=sigma), h)).sum())
+
+    rho = O.density([fd, ff], phase)
+    faces = O.faces_from_density(rho)
+    b = O.rhs(u, faces, h, csf=csf, sigma=sigma)
+    p = _dense_p(faces, b, h)
+    lam = _dense_p(faces, w, h)
+    g, _ = O.adjoint_grads(faces, lam, p, h, csf=csf, sigma=sigma)
+    drho, (dfd, dff) = O.density_grads(rho, g, phase)
+    rng = np.random.default_rng(3)
+    cells = [tuple(rng.integers(0, n, 3)) for _ in range(6)] + [(2, 3, 4)]
+    for c in cells:
+        # step 1e-3 rho: truncation ~1e-6 relative, while the dense solves' rounding (~1e-14 of
+        # L ~ 300) stays far below the difference quotient
+        e = 1e-3 * rho[c]
+        rp, rm = rho.copy(), rho.copy()
+        rp[c] += e
+        rm[c] -= e
+        fdiff = (loss_rho(rp) - loss_rho(rm)) / (2 * e)
+        assert abs(fdiff - drho[c]) <= 1e-5 * max(abs(drho[c]), 1e-3 * np.abs(drho).max()), (c, fdiff, drho[c])
+        # fraction of the drop: rho changes by (998 - 1.2) per unit f_drop
+        assert dfd[c] == drho[c] * (998.0 - 1.2) and dff[c] == drho[c] * (880.0 - 1.2)
