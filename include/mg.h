@@ -101,8 +101,12 @@ typedef struct {
     int inner_cycles; /* mixed modes: FP32 V-cycles per outer iteration (1..8), the first from
                          zero, the next ones continuing from the previous correction; the
                          FP64 (or double-float) residual and update run once per outer
-                         iteration.  With MG_METHOD_FCG: the flexible-CG iterations per outer
-                         iteration.  Must be 1 for MG_FP64. */
+                         iteration.  0 (V-cycle iteration only): adaptive, 4 V-cycles in the
+                         first outer iteration, then as many (1..8) as the contraction per
+                         V-cycle observed in the last outer iteration predicts the tolerance
+                         still needs, so that the fewest FP64 residuals are evaluated.  With
+                         MG_METHOD_FCG: the flexible-CG iterations per outer iteration (1..8).
+                         Must be 1 for MG_FP64. */
     int method;       /* MG_METHOD_VCYCLE: V-cycle iteration (defect correction in the mixed
                          modes).  MG_METHOD_FCG: conjugate gradients preconditioned by one
                          V-cycle, flexible (Polak-Ribiere) form: in MG_FP64 the whole solve, with
@@ -110,6 +114,13 @@ typedef struct {
                          iteration, in FP32 on the finest level (needs nx % 8 == 0).  The
                          stopping test uses the CG-updated residual in MG_FP64 and the outer
                          residual in the mixed modes; max_cycles counts V-cycles. */
+    int fused_sweeps; /* mixed modes, finest level with an operator from a density and nx a
+                         multiple of 128: 1 smooths with fused red-black sweeps (one pass over
+                         the grid per sweep instead of two, planes staged in shared memory by
+                         bulk copies; bitwise the same results); 0 (default) with two half sweeps
+                         per sweep, which is faster on GB300 (the fused sweep is bound by its
+                         instruction issue, not by memory).  Other levels and layouts always
+                         use half sweeps. */
 } mg_opts;
 
 typedef struct {
@@ -123,7 +134,7 @@ typedef struct {
 } mg_stats;
 
 /* Defaults: 2/2 sweeps, coarsest 4, trilinear, rtol 1e-10, 200 cycles, FP64, cold start,
-   one V-cycle per outer iteration, V-cycle iteration (MG_METHOD_VCYCLE). */
+   one V-cycle per outer iteration, V-cycle iteration (MG_METHOD_VCYCLE), half sweeps. */
 void mg_default_opts(mg_opts *opts);
 
 /* Create a solver for one grid.  `stream` is a cudaStream_t (NULL = legacy
@@ -197,6 +208,40 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
                float *gby, float *gbz, const double *csfx, const double *csfy, const double *csfz,
                double sigma, double *dLdsigma, mg_stats *stats);
 
+/* Velocity correction of the projection step (paper §2: the face velocities of
+ * Eq. (2) made divergence-free, Eq. (1)).  On every interior face
+ *   o_f = u_f + beta_f ( (p_R - p_L)/h + sigma csf_f ),
+ * and o_f = u_f on the walls; beta the handle's current fine face
+ * coefficients, p the solution of A p = D u + sigma D(beta csf) (mg_rhs +
+ * mg_solve on the same u, csf and sigma), so that D o = 0 up to the solve's
+ * residual.  ux, uy, uz: input face arrays; ox, oy, oz: output face arrays,
+ * either all three equal to ux, uy, uz (in place) or none of them overlapping
+ * them (MG_ERR_ARG for a mix).  csf*: face arrays, or all NULL (no surface
+ * term; sigma is then ignored).  FP64 arithmetic.  MG_ERR_STATE if no
+ * coefficients are set.  Returns once queued. */
+int mg_project(mg_handle *h, const double *p, const double *csfx, const double *csfy,
+               const double *csfz, double sigma, const double *ux, const double *uy,
+               const double *uz, double *ox, double *oy, double *oz);
+
+/* Density adjoint: carries the face-coefficient gradients of mg_adjoint back
+ * through beta_f = (1/rho_L + 1/rho_R)/2 and Eq. (5):
+ *   dL/drho_c = -1/(2 rho_c^2) * sum_{interior faces f of c} dL/dbeta_f,
+ *   dL/df_q   = dL/drho_c * (rho_q - rho_{nfrac})           (q < nfrac).
+ * rho: cell array (the density the operator was set from, finite and > 0);
+ * gbx, gby, gbz: FLOAT face arrays (as mg_adjoint writes them; wall entries
+ * ignored); drho: output cell array (double).  nfrac = 0 skips the fraction
+ * gradients; otherwise 1..4, rho_phase a host array of nfrac+1 phase
+ * densities (as for mg_density_from_fractions) and dfrac_dev a host array of
+ * nfrac device pointers to output cell arrays.  The face gradients are FP32,
+ * so the sum and the factor are formed in FP32 (FP64 for densities outside
+ * [2^-20, 2^21)) and the results carry FP32 precision.  Uses only the handle's
+ * dimensions and stream (no operator needed).  Returns once queued.
+ * The fraction path covers the density dependence only: a surface term whose
+ * csf was built from a fraction (mg_csf_faces) contributes no further term. */
+int mg_density_grads(mg_handle *h, const double *rho, const float *gbx, const float *gby,
+                     const float *gbz, double *drho, int nfrac, const double *rho_phase,
+                     double *const *dfrac_dev);
+
 /* ---- component steps of the V-cycle on level `level` --------------------------
  * For callers that assemble their own cycles, and for step-by-step checking.
  * dtype MG_F64 uses the FP64 coefficients, MG_F32 the FP32 copies (MIXED and
@@ -251,7 +296,9 @@ enum {
     MG_PROF_FINE_RESIDUAL = 4,  /* FP64 residual / norm pass of the outer loop */
     MG_PROF_UPDATE = 5,         /* MIXED solution update */
     MG_PROF_ADJOINT_GRAD = 6,   /* fused adjoint gradient kernel */
-    MG_PROF_NCLASS = 7
+    MG_PROF_PROJECT = 7,        /* velocity correction (mg_project) */
+    MG_PROF_DENSITY_GRAD = 8,   /* density adjoint (mg_density_grads) */
+    MG_PROF_NCLASS = 9
 };
 
 /* Turn timing on (1) or off (0); either way the accumulated totals are reset. */

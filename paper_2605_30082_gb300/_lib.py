@@ -25,7 +25,8 @@ MG_F64, MG_F32 = 0, 1
 MG_MAX_LEVELS, MG_MAX_COARSE, MG_HIST_LEN = 24, 1024, 256
 MG_NOALLOC_MAX_CELLS = 512
 (MG_PROF_SMOOTH, MG_PROF_RESID_RESTRICT, MG_PROF_PROLONG, MG_PROF_COARSE,
- MG_PROF_FINE_RESIDUAL, MG_PROF_UPDATE, MG_PROF_ADJOINT_GRAD, MG_PROF_NCLASS) = range(8)
+ MG_PROF_FINE_RESIDUAL, MG_PROF_UPDATE, MG_PROF_ADJOINT_GRAD, MG_PROF_PROJECT,
+ MG_PROF_DENSITY_GRAD, MG_PROF_NCLASS) = range(10)
 
 ERROR_NAMES = {
     MG_OK: "MG_OK", MG_ERR_ARG: "MG_ERR_ARG", MG_ERR_DENSITY: "MG_ERR_DENSITY",
@@ -39,7 +40,7 @@ class mg_opts(C.Structure):
                 ("precision", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarsest", C.c_int), ("prolong", C.c_int), ("rtol", C.c_double),
                 ("max_cycles", C.c_int), ("warm_start", C.c_int), ("inner_cycles", C.c_int),
-                ("method", C.c_int)]
+                ("method", C.c_int), ("fused_sweeps", C.c_int)]
 
 
 class mg_stats(C.Structure):
@@ -70,6 +71,8 @@ SIGNATURES = {
     "mg_rhs": (_i, [_v, _v, _v, _v, _v, _v, _v, _v, _d, _v]),
     "mg_solve": (_i, [_v, _v, _v, C.POINTER(mg_stats)]),
     "mg_adjoint": (_i, [_v, _v, _v, _v, _v, _v, _v, _v, _v, _v, _d, C.POINTER(_d), C.POINTER(mg_stats)]),
+    "mg_project": (_i, [_v, _v, _v, _v, _v, _d, _v, _v, _v, _v, _v, _v]),
+    "mg_density_grads": (_i, [_v, _v, _v, _v, _v, _v, _i, C.POINTER(_d), C.POINTER(_v)]),
     "mg_apply": (_i, [_v, _i, _i, _v, _v]),
     "mg_smooth": (_i, [_v, _i, _i, _v, _v, _i, _i]),
     "mg_presmooth_restrict": (_i, [_v, _i, _i, _v, _v, _i, _i, _v]),
@@ -233,6 +236,33 @@ def mg_adjoint(h, w, p, lam, grads, csf, sigma, dims, stats: mg_stats | None = N
                           _dev(lam, shape=cs, name="lam"), g[0], g[1], g[2], c[0], c[1], c[2],
                           float(sigma), C.byref(ds), C.byref(stats) if stats is not None else None)
     return st, ds.value
+
+
+def mg_project(h, p, csf, sigma, u, out, dims):
+    """u, out: (x, y, z) float64 face tensors (out may be u itself: in place); csf may be None."""
+    fs = face_shapes(dims)
+    c = [None, None, None] if csf is None else [_dev(a, shape=s, name="csf") for a, s in zip(csf, fs)]
+    ui = [_dev(a, shape=s, name="u") for a, s in zip(u, fs)]
+    uo = [_dev(a, shape=s, name="out") for a, s in zip(out, fs)]
+    return lib().mg_project(h, _dev(p, shape=cell_shape(dims), name="p"), c[0], c[1], c[2], float(sigma),
+                            *ui, *uo)
+
+
+def mg_density_grads(h, rho, grads, drho, dims, rho_phase=None, dfrac=None):
+    """grads: (gbx, gby, gbz) float32 face tensors; drho float64 cells; dfrac: nfrac float64 cell
+    tensors (with rho_phase, nfrac + 1 densities) or None."""
+    fs = face_shapes(dims)
+    cs = cell_shape(dims)
+    g = [_dev(a, torch.float32, s, "grad") for a, s in zip(grads, fs)]
+    nfrac, rp, ptrs = 0, None, None
+    if dfrac is not None:
+        nfrac = len(dfrac)
+        if rho_phase is None or len(rho_phase) != nfrac + 1:
+            raise ValueError("rho_phase needs len(dfrac) + 1 densities")
+        rp = (C.c_double * (nfrac + 1))(*[float(r) for r in rho_phase])
+        ptrs = (C.c_void_p * nfrac)(*[_dev(a, shape=cs, name="dfrac").value for a in dfrac])
+    return lib().mg_density_grads(h, _dev(rho, shape=cs, name="rho"), g[0], g[1], g[2],
+                                  _dev(drho, shape=cs, name="drho"), nfrac, rp, ptrs)
 
 
 def _lvl_shape(h, level):

@@ -207,8 +207,36 @@ void half32(mg_handle *h, int l, const float *b, float *x, int col, bool from_ze
     if (l == 0) prof_end(h);
 }
 
+// Fused red-black sweeps (finest level, s-form operator, layout permitting): each sweep reads
+// x from one buffer and writes both colours to the other.  The second buffer is the level's
+// FP32 x-face array, which the s-form operator leaves unused.
+bool fused0(const mg_handle *h, int l) {
+    return l == 0 && h->o.fused_sweeps && h->sform0 && mg::sweep_fused_ok(h->lv[0].lay);
+}
+
+// one fused sweep X -> Y, colour c1 first; with `p` the outer update replaces the store
+void sweep_fused(mg_handle *h, const float *b, const float *X, float *Y, int c1, bool from_zero,
+                 double *p = nullptr, double alpha = 0.0, double shift = 0.0) {
+    Level &L = h->lv[0];
+    prof_begin(h, p ? MG_PROF_UPDATE : MG_PROF_SMOOTH);
+    mg::launch_sweep_fused(h->s, L.lay, L.h2, L.s32, b, X, Y, c1, from_zero, p, alpha, shift, h->err);
+    prof_end(h);
+}
+
 // `sweeps` red-black sweeps in place; order 0 red first, 1 black first; from_zero: x = 0 on entry
 void smooth32(mg_handle *h, int l, const float *b, float *x, int sweeps, int order, bool from_zero) {
+    if (fused0(h, l) && sweeps > 0) {
+        float *buf[2] = {x, h->lv[0].fx32};
+        int sw = 0;
+        if (sweeps % 2) {  // one sweep as two half sweeps in place: the fused pairs then end in x
+            half32(h, l, b, x, order ? 1 : 0, from_zero);
+            half32(h, l, b, x, order ? 0 : 1, false);
+            sw = 1;
+        }
+        for (int i = 0; sw < sweeps; ++sw, ++i)  // an even number: x -> scratch -> x ...
+            sweep_fused(h, b, buf[i & 1], buf[(i + 1) & 1], order ? 1 : 0, from_zero && sw == 0);
+        return;
+    }
     for (int sw = 0; sw < sweeps; ++sw) {
         half32(h, l, b, x, order ? 1 : 0, from_zero && sw == 0);
         half32(h, l, b, x, order ? 0 : 1, false);
@@ -245,6 +273,14 @@ void prolong_postsmooth32(mg_handle *h, int l, const float *b, const float *ec, 
     if (l == 0) prof_end(h);
     if (!up) {
         smooth32(h, l, b, x, sweeps, 1, false);
+        return;
+    }
+    if (fused0(h, l) && up->p) {
+        // sweeps - 1 fused sweeps alternating between the buffers, then the fused sweep whose
+        // second colour goes (with the first) into the FP64 solution
+        float *buf[2] = {x, h->lv[0].fx32};
+        for (int i = 0; i < sweeps - 1; ++i) sweep_fused(h, b, buf[i & 1], buf[(i + 1) & 1], 1, false);
+        sweep_fused(h, b, buf[(sweeps - 1) & 1], buf[sweeps & 1], 1, false, up->p, up->alpha, up->shift);
         return;
     }
     smooth32(h, l, b, x, sweeps - 1, 1, false);
@@ -343,6 +379,27 @@ void inner_fcg32(mg_handle *h, int k) {
     }
 }
 
+// ---- adaptive inner cycles (mixed V-cycle iteration, inner_cycles 0) ----------------------
+// Each outer iteration costs an FP64 residual (bound by the FP64 pipe) besides its V-cycles;
+// running as many V-cycles per outer iteration as the tolerance still needs, and no more,
+// spends the fewest residuals without adding V-cycles.  The contraction per V-cycle rho is
+// taken from the last outer iteration, and the next iteration runs
+//     k = ceil(log(rtol / rr) / log(rho) + margin),   1 <= k <= kMaxAdaptive,
+// V-cycles (margin 0.25 of a cycle: a slightly optimistic rho would otherwise cost a whole
+// extra outer iteration).
+constexpr int kFirstAdaptive = 4, kMaxAdaptive = 8;
+
+int next_inner(double rr_prev, double rr, int k, double rtol) {
+    if (!(rr > 0.0) || !(rr_prev > 0.0) || !(rtol > 0.0) || rr <= rtol) return k;
+    double rho = std::pow(rr / rr_prev, 1.0 / k);
+    if (!(rho > 0.0)) rho = 0.01;
+    if (rho > 0.95) rho = 0.95;
+    if (rho < 0.01) rho = 0.01;
+    const double m = std::log(rtol / rr) / std::log(rho) + 0.25;
+    int kn = (int)std::ceil(m);
+    return kn < 1 ? 1 : (kn > kMaxAdaptive ? kMaxAdaptive : kn);
+}
+
 // ---- one solve A x = b - mean(b), zero-mean x -------------------------------------------
 int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st) {
     cudaStream_t s = h->s;
@@ -367,7 +424,10 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     if (df && !(nb < 1e30)) return fail(h, MG_ERR_ARG, "MG_MIXED_DF needs |b - mean b| < 1e30");
     int status = MG_OK;
     int cycles = 0, outer = 0;
-    const int inner = mixed ? h->o.inner_cycles : 1;
+    // V-cycles per outer iteration; inner_cycles 0 (mixed V-cycle iteration): chosen per outer
+    // iteration from the contraction observed so far (kFirstAdaptive for the first)
+    const bool adaptive = mixed && h->o.inner_cycles == 0;
+    int inner = mixed ? (adaptive ? kFirstAdaptive : h->o.inner_cycles) : 1;
     const bool fcg = h->o.method == MG_METHOD_FCG;
     double rr = 0.0;
     if (nb == 0.0) {
@@ -442,8 +502,10 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             rr = std::sqrt(h->hred[6]) * F.ih2 / nb;
             if (status == MG_OK && rr > h->o.rtol) status = MG_ERR_NOT_CONVERGED;
         }
-        for (int it = 1; !(fcg && !mixed) && cycles + inner <= h->o.max_cycles && status == MG_ERR_NOT_CONVERGED;
-             ++it) {
+        for (int it = 1; !(fcg && !mixed) && status == MG_ERR_NOT_CONVERGED; ++it) {
+            // the adaptive count shrinks to the cycles left; a fixed count stops before exceeding
+            if (adaptive && cycles + inner > h->o.max_cycles) inner = h->o.max_cycles - cycles;
+            if (inner < 1 || cycles + inner > h->o.max_cycles) break;
             if (mixed && fcg) {
                 // inner_cycles flexible-CG iterations in FP32, then the outer update
                 inner_fcg32(h, inner);
@@ -476,8 +538,10 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             double mu_new = h->hred[7] / (double)n;
             if (!mixed) mg::launch_add_const(s, n, p, -mu_new);  // FP64 path: zero mean each cycle
             mu = mixed ? mu_new : 0.0;
+            const double rr_prev = rr;
             rr = rn / nb;
             cycles += inner;
+            if (adaptive) inner = next_inner(rr_prev, rr, inner, h->o.rtol);
             outer = it;
             if (hist_n < MG_HIST_LEN) hist[hist_n++] = rr;
             if (!std::isfinite(rr) || rr > 1e12) {
@@ -498,6 +562,15 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     MG_CUDA(h, cudaEventSynchronize(h->ev1));
     rc = check_launch(h, "solve");
     if (rc) return rc;
+    if (fused0(h, 0)) {  // a bounded wait of a fused sweep that ran out sets bit 4
+        unsigned herr = 0;
+        MG_CUDA(h, cudaMemcpyAsync(&herr, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        MG_CUDA(h, cudaStreamSynchronize(s));
+        if (herr & 4u) {
+            MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), s));
+            return fail(h, MG_ERR_CUDA, "a fused sweep gave up waiting for its shared-memory copies");
+        }
+    }
     if (st) {
         st->status = status;
         st->cycles = cycles;
@@ -551,6 +624,7 @@ void mg_default_opts(mg_opts *o) {
     o->warm_start = 0;
     o->inner_cycles = 1;
     o->method = MG_METHOD_VCYCLE;
+    o->fused_sweeps = 0;
 }
 
 int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
@@ -563,10 +637,12 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         (o->precision == MG_MIXED_DF && o->nx % 2 != 0) || o->pre < 0 || o->post < 0 ||
         o->pre > 64 || o->post > 64 || o->coarsest < 2 ||
         (o->prolong != MG_PROLONG_TRILINEAR && o->prolong != MG_PROLONG_CONSTANT) || !(o->rtol >= 0.0) ||
-        o->max_cycles < 0 || o->inner_cycles < 1 || o->inner_cycles > 8 ||
+        o->max_cycles < 0 || o->inner_cycles < 0 || o->inner_cycles > 8 ||
         (o->precision == MG_FP64 && o->inner_cycles != 1) ||
+        (o->inner_cycles == 0 && o->method != MG_METHOD_VCYCLE) ||
         (o->method != MG_METHOD_VCYCLE && o->method != MG_METHOD_FCG) ||
-        (o->method == MG_METHOD_FCG && o->precision != MG_FP64 && o->nx % 8 != 0))
+        (o->method == MG_METHOD_FCG && o->precision != MG_FP64 && o->nx % 8 != 0) ||
+        (o->fused_sweeps != 0 && o->fused_sweeps != 1))
         return MG_ERR_ARG;
     int nl = num_levels(o->nx, o->ny, o->nz, o->coarsest);
     if (nl > MG_MAX_LEVELS) return MG_ERR_ARG;
@@ -814,6 +890,47 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
         if (dLdsigma) *dLdsigma = csf ? h->hred[8] : 0.0;
     }
     return MG_OK;
+}
+
+int mg_project(mg_handle *h, const double *p, const double *csfx, const double *csfy, const double *csfz,
+               double sigma, const double *ux, const double *uy, const double *uz, double *ox, double *oy,
+               double *oz) {
+    if (!h) return MG_ERR_ARG;
+    if (!p || !ux || !uy || !uz || !ox || !oy || !oz)
+        return fail(h, MG_ERR_ARG, "mg_project: p, u and out arrays must be non-null");
+    const int same = (ox == ux) + (oy == uy) + (oz == uz);
+    if (same != 0 && same != 3)
+        return fail(h, MG_ERR_ARG, "mg_project: out must be all three u arrays (in place) or none of them");
+    bool csf = csfx || csfy || csfz;
+    if (csf && !(csfx && csfy && csfz)) return fail(h, MG_ERR_ARG, "mg_project: give all three csf arrays or none");
+    if (csf && !std::isfinite(sigma)) return fail(h, MG_ERR_ARG, "mg_project: sigma not finite");
+    if (!h->have_op) return fail(h, MG_ERR_STATE, "mg_project: coefficients not set");
+    Level &F = h->lv[0];
+    prof_begin(h, MG_PROF_PROJECT);
+    mg::launch_project(h->s, F.d, h->o.h, p, F.fx64, F.fy64, F.fz64, csf ? csfx : nullptr,
+                       csf ? csfy : nullptr, csf ? csfz : nullptr, sigma, ux, uy, uz, ox, oy, oz);
+    prof_end(h);
+    return check_launch(h, "mg_project");
+}
+
+int mg_density_grads(mg_handle *h, const double *rho, const float *gbx, const float *gby, const float *gbz,
+                     double *drho, int nfrac, const double *rho_phase, double *const *dfrac_dev) {
+    if (!h) return MG_ERR_ARG;
+    if (!rho || !gbx || !gby || !gbz || !drho)
+        return fail(h, MG_ERR_ARG, "mg_density_grads: rho, gradients and drho must be non-null");
+    if (nfrac < 0 || nfrac > 4) return fail(h, MG_ERR_ARG, "mg_density_grads: nfrac must be 0..4");
+    if (nfrac > 0) {
+        if (!rho_phase || !dfrac_dev)
+            return fail(h, MG_ERR_ARG, "mg_density_grads: rho_phase and dfrac_dev needed for nfrac > 0");
+        for (int q = 0; q < nfrac; ++q)
+            if (!dfrac_dev[q]) return fail(h, MG_ERR_ARG, "mg_density_grads: dfrac %d is NULL", q);
+        for (int q = 0; q <= nfrac; ++q)
+            if (!std::isfinite(rho_phase[q])) return fail(h, MG_ERR_ARG, "mg_density_grads: rho_phase not finite");
+    }
+    prof_begin(h, MG_PROF_DENSITY_GRAD);
+    mg::launch_density_grads(h->s, h->lv[0].d, rho, gbx, gby, gbz, drho, nfrac, rho_phase, dfrac_dev);
+    prof_end(h);
+    return check_launch(h, "mg_density_grads");
 }
 
 // FP32 components take natural-layout arrays: they are packed into the level's storage

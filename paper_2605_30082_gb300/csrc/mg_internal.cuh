@@ -171,6 +171,15 @@ void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, c
                           const float *fz, const float *b, const float *x, double *p, float2 *p2, double alpha,
                           double shift);
 
+// ---- fused red-black sweep of the finest level (kernels_fused.cu) ----
+// s-form split level with hx % 64 == 0: one sweep, colour c1 first, reading x from X and
+// writing both colours to Y (X != Y); from_zero: X is not read (x = 0).  With p non-null the
+// second colour's new values and the first colour's go into p = (p - shift) + alpha x (natural
+// FP64) instead of Y.  A bounded wait that runs out sets bit 4 of *err.
+bool sweep_fused_ok(Lay L);
+void launch_sweep_fused(cudaStream_t s, Lay L, double h2, const float *sinv, const float *b, const float *X,
+                        float *Y, int c1, bool from_zero, double *p, double alpha, double shift, unsigned *err);
+
 // ---- MG_MIXED_DF outer loop (kernels_df.cu): double-float (hi, lo) FP32 pairs ----
 void launch_split(cudaStream_t s, i64 n, const double *src, float2 *dst);   // hi = fl32(v), lo = fl32(v - hi)
 void launch_join(cudaStream_t s, i64 n, const float2 *src, double *dst);    // v = hi + lo in FP64
@@ -261,5 +270,16 @@ void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, co
                          const double *fx, const double *fy, const double *fz, const double *csfx,
                          const double *csfy, const double *csfz, double sigma, float *gx,
                          float *gy, float *gz, double *partials, double *out);
+
+// ---- either side of the solve (kernels_project.cu) --------------------------------------
+// o = u + beta (G p + sigma csf) on the interior faces, o = u on the walls (csfx NULL: no
+// surface term); o may be u (in place; the walls are then not rewritten)
+void launch_project(cudaStream_t s, Dims d, double h, const double *p, const double *fx, const double *fy,
+                    const double *fz, const double *csfx, const double *csfy, const double *csfz, double sigma,
+                    const double *ux, const double *uy, const double *uz, double *ox, double *oy, double *oz);
+// dL/drho from FP32 face gradients, and dL/df_q = dL/drho (rho_q - rho_last) into dfrac[q]
+void launch_density_grads(cudaStream_t s, Dims d, const double *rho, const float *gx, const float *gy,
+                          const float *gz, double *drho, int nfrac, const double *rho_phase,
+                          double *const *dfrac);
 
 }  // namespace mg

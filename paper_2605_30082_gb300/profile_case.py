@@ -2,7 +2,8 @@
 
 Random density in [1.2, 998] and random right-hand side (torch generators, seeds 3 and 4),
 `CYCLES` V-cycles (default 2) of the given precision ('fp64', 'mixed', 'mixed_df'), followed by
-one adjoint solve of as many cycles.  Sized by the caller so that every array is larger than L2
+one adjoint solve of as many cycles, one velocity correction of random face velocities (seed 5,
+out of place) and one density adjoint of random FP32 face gradients (seed 6, two fractions).  Sized by the caller so that every array is larger than L2
 while the whole case holds a few GB: e.g. 512 512 256 keeps the 512-cell rows (and so the launch
 configuration) of the 512^3 workload at half its cells.
 """
@@ -32,6 +33,12 @@ def main(argv):
     except MgError as e:
         if e.code != L.MG_ERR_NOT_CONVERGED:
             raise
+    u = tuple(torch.randn(sh, generator=g.manual_seed(5 + q), device=dev, dtype=torch.float64)
+              for q, sh in enumerate(s.face_shapes))
+    s.project(p, u, out=tuple(torch.empty_like(a) for a in u))
+    gr = tuple(torch.randn(sh, generator=g.manual_seed(8 + q), device=dev, dtype=torch.float32)
+               for q, sh in enumerate(s.face_shapes))
+    s.density_grads(rho, gr, [998.0, 880.0, 1.2])
     torch.cuda.synchronize()
     print("ok", s.last_stats.cycles, s.last_stats.relres)
 

@@ -26,13 +26,14 @@ class Solver:
     Parameters mirror ``mg_opts``: dims = (nx, ny, nz), h, precision ('fp64',
     'mixed' or 'mixed_df'), pre/post sweeps, coarsest, prolong ('trilinear' or
     'constant'), rtol, max_cycles, warm_start, inner_cycles (mixed modes: FP32 V-cycles, or
-    flexible-CG iterations, per outer FP64 residual), method ('vcycle' or 'fcg': conjugate
-    gradients preconditioned by one V-cycle).
+    flexible-CG iterations, per outer FP64 residual; 0: adaptive V-cycle count), method ('vcycle' or 'fcg': conjugate
+    gradients preconditioned by one V-cycle), fused_sweeps (True: finest-level fused red-black
+    sweeps where the layout allows, bitwise the same results as the default half sweeps).
     """
 
     def __init__(self, dims, h=None, precision="mixed", pre=2, post=2, coarsest=None,
                  prolong="trilinear", rtol=1e-10, max_cycles=200, warm_start=False, stream=None,
-                 inner_cycles=1, method="vcycle"):
+                 inner_cycles=1, method="vcycle", fused_sweeps=False):
         nx, ny, nz = (int(v) for v in dims)
         o = L.mg_default_opts()
         o.nx, o.ny, o.nz = nx, ny, nz
@@ -46,6 +47,7 @@ class Solver:
         o.warm_start = int(bool(warm_start))
         o.inner_cycles = int(inner_cycles)
         o.method = {"vcycle": L.MG_METHOD_VCYCLE, "fcg": L.MG_METHOD_FCG}[method]
+        o.fused_sweeps = int(bool(fused_sweeps))
         self.opts = o
         self.dims = (nx, ny, nz)
         self.h = o.h
@@ -149,6 +151,26 @@ class Solver:
         self._check(st)
         return lam, g, ds
 
+    # -- either side of the solve --
+    def project(self, p, u, csf=None, sigma=0.0, out=None):
+        """Velocity correction of the projection step: u + beta (G p + sigma csf) on the interior
+        faces, u on the walls (u: three float64 face tensors).  Written into `out` (three face
+        tensors), or into u itself when out is None.  Returns the corrected velocities."""
+        out = tuple(u) if out is None else tuple(out)
+        self._check(L.mg_project(self._h, p, csf, sigma, u, out, self.dims))
+        return out
+
+    def density_grads(self, rho, grads, rho_phase=None, out=None):
+        """dL/drho from the float32 face gradients of `adjoint`; with rho_phase (nfrac + 1 phase
+        densities) also dL/df_q.  Returns drho, or (drho, [dL/df_q]); `out` gives those arrays."""
+        if out is not None:
+            drho, dfrac = (out, None) if rho_phase is None else (out[0], list(out[1]))
+        else:
+            drho = self.empty_cells()
+            dfrac = None if rho_phase is None else [self.empty_cells() for _ in range(len(rho_phase) - 1)]
+        self._check(L.mg_density_grads(self._h, rho, grads, drho, self.dims, rho_phase, dfrac))
+        return drho if dfrac is None else (drho, dfrac)
+
     # -- instrumentation --
     def profile(self, enable=True):
         self._check(L.mg_profile(self._h, enable))
@@ -196,3 +218,45 @@ class PoissonSolve(torch.autograd.Function):
             dsig = torch.tensor(ds, dtype=torch.float64, device=p.device)
         return None, lam, g[0], g[1], g[2], dsig, None
 
+
+
+class PoissonSolveFractions(torch.autograd.Function):
+    """p = A(beta(rho))^+ (b - mean b), rho = Eq. (5) of the phase fractions, b = b_u + sigma
+    D(beta csf) (csf optional), with gradients back to the fractions.
+
+    forward(solver, b_u, rho_phase, sigma, csf, *fracs) -> p
+    rho_phase: nfrac + 1 phase densities (floats); fracs: nfrac float64 cell tensors.
+    Gradients: dL/db_u, dL/dsigma (when sigma is a tensor and csf is given) and dL/df_q, the
+    last through the density only (csf is held fixed).  The backward is mg_adjoint followed by
+    mg_density_grads (which forms dL/drho and every dL/df_q in one pass); the density is
+    recomputed from the saved fractions when another operator was set in between.
+    """
+
+    @staticmethod
+    def forward(ctx, solver: Solver, b_u, rho_phase, sigma, csf, *fracs):
+        rho = solver.density_from_fractions(list(fracs), list(rho_phase))
+        solver.set_density(rho)
+        sig = float(sigma) if sigma is not None else 0.0
+        b = b_u if csf is None else solver.rhs(csf=csf, sigma=sig, b0=b_u)
+        p = solver.solve(b)
+        ctx.solver = solver
+        ctx.sig = sig
+        ctx.has_sigma = sigma is not None and isinstance(sigma, torch.Tensor)
+        ctx.csf = csf
+        ctx.rho_phase = tuple(float(r) for r in rho_phase)
+        ctx.save_for_backward(rho, p)
+        ctx.version = solver.coef_version
+        return p
+
+    @staticmethod
+    def backward(ctx, grad_p):
+        solver = ctx.solver
+        rho, p = ctx.saved_tensors
+        if solver.coef_version != ctx.version:
+            solver.set_density(rho)
+        lam, g, ds = solver.adjoint(grad_p.contiguous(), p, csf=ctx.csf, sigma=ctx.sig, grads=True)
+        _, dfrac = solver.density_grads(rho, g, ctx.rho_phase)
+        dsig = None
+        if ctx.has_sigma:
+            dsig = torch.tensor(ds, dtype=torch.float64, device=p.device)
+        return (None, lam, None, dsig, None) + tuple(dfrac)

@@ -38,3 +38,13 @@ def dropfilm_case(n, subcell=False):
     u = D.face_velocities(n, seed=0)
     b = O.divergence([a.numpy() for a in u], h)
     return dict(n=n, h=h, geom=g, fd=fd, ff=ff, rho=rho, faces=faces, u=u, b=b)
+
+
+def csf_case(n):
+    """dropfilm_case plus the curvature band, the CSF face quantity and the loss weights w."""
+    c = dropfilm_case(n)
+    kappa = D.curvature_band(c["fd"], c["geom"]).numpy()
+    c["kappa"] = kappa
+    c["csf"] = O.csf_faces(c["fd"].numpy(), kappa, c["h"])
+    c["w"] = D.normal_weights((n, n, n), seed=1).numpy()
+    return c

@@ -9,22 +9,12 @@ import numpy as np
 import pytest
 import torch
 
-import dropfilm as D
 import oracle as O
 from paper_2605_30082_gb300 import PoissonSolve, Solver
 
-from _helpers import dev, dropfilm_case, host, rel
+from _helpers import csf_case, dev, host, rel
 
 pytestmark = pytest.mark.gpu
-
-
-def csf_case(n):
-    c = dropfilm_case(n)
-    kappa = D.curvature_band(c["fd"], c["geom"]).numpy()
-    c["kappa"] = kappa
-    c["csf"] = O.csf_faces(c["fd"].numpy(), kappa, c["h"])
-    c["w"] = D.normal_weights((n, n, n), seed=1).numpy()
-    return c
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])

@@ -73,6 +73,8 @@ def test_256_fp64_reproduces_oracle_iteration(c256):
 
 @pytest.mark.parametrize("prec,inner,method", [("mixed", 1, "vcycle"), ("mixed_df", 1, "vcycle"),
                                                ("mixed", 2, "vcycle"), ("mixed_df", 2, "vcycle"),
+                                               ("mixed", 4, "vcycle"), ("mixed_df", 4, "vcycle"),
+                                               ("mixed", 0, "vcycle"), ("mixed_df", 0, "vcycle"),
                                                ("mixed", 4, "fcg"), ("mixed_df", 4, "fcg")])
 def test_256_mixed_reaches_exact_solution(c256, prec, inner, method):
     s, _ = gpu_solver(c256, prec, 1e-11, inner, method)
@@ -85,9 +87,10 @@ def test_256_mixed_reaches_exact_solution(c256, prec, inner, method):
     s, _ = gpu_solver(c256, prec, 1e-10, inner, method)
     p = host(s.solve(s.rhs(u=c256["u"])))
     p_o, _, nc_o, _, _ = c256["iter"]
-    if method == "vcycle":  # the same iteration as the oracle's, to 1e-9
-        assert nc_o - 1 <= s.last_stats.cycles <= nc_o + inner
-        assert rel(p, p_o) <= 1e-9
+    if method == "vcycle":  # the same iteration as the oracle's
+        assert nc_o - 1 <= s.last_stats.cycles <= nc_o + (inner if inner else 2)
+        if s.last_stats.cycles <= nc_o + 1:  # stopped at the oracle's cycle (or one later): its iterate
+            assert rel(p, p_o) <= 1e-9
     else:  # another iteration: fewer V-cycles, its own iterate
         assert s.last_stats.cycles < nc_o
     assert rel(p, c256["exact"]) <= 3e-9
@@ -142,7 +145,8 @@ def test_512_level0_sweep_on_subboxes(prec, dtype):
 
 @pytest.mark.parametrize("prec,inner,method", [("mixed", 1, "vcycle"), ("mixed_df", 1, "vcycle"),
                                                ("mixed", 2, "vcycle"), ("mixed_df", 2, "vcycle"),
-                                               ("mixed", 4, "fcg"), ("fp64", 1, "fcg")])
+                                               ("mixed", 4, "vcycle"), ("mixed", 0, "vcycle"), ("mixed", 4, "fcg"),
+                                               ("fp64", 1, "fcg")])
 def test_512_benchmark_solve_and_adjoint(prec, inner, method):
     c = fields(512)
     h = c["h"]
@@ -163,3 +167,37 @@ def test_512_benchmark_solve_and_adjoint(prec, inner, method):
     g_o, _ = O.adjoint_grads(c["faces"], lh, ph, h)
     for gg, go in zip(g, g_o):
         assert rel(host(gg), go) < 1e-6
+
+
+def test_512_projection_and_density_adjoint():
+    """The benchmark's step at 512^3 (mixed, adaptive inner cycles) followed by the velocity correction
+    and the density adjoint, compared with the oracle on every face and cell: the projection
+    to 1e-14 of the largest velocity, with zero divergence up to the solve's residual; dL/drho
+    and dL/df_q within the FP32 rounding bound of the same gradients (tests/test_gpu_project.py
+    derives it)."""
+    from test_gpu_project import _density_bound
+
+    c = fields(512)
+    h = c["h"]
+    s, rho = gpu_solver(c, "mixed", 1e-10, 0)
+    b = s.rhs(u=c["u"])
+    p = s.solve(b)
+    u_h = [host(a) for a in c["u"]]
+    s.project(p, c["u"])
+    want = O.project(u_h, c["faces"], host(p), h)
+    for a, wnt in zip(c["u"], want):
+        assert np.abs(host(a) - wnt).max() <= 1e-14 * np.abs(wnt).max()
+    del want
+    div = O.divergence([host(a) for a in c["u"]], h)
+    nb = np.linalg.norm(c["b"] - c["b"].mean())
+    assert np.linalg.norm(div - c["b"].mean()) <= 1.05 * s.last_stats.relres * nb + 1e-12 * nb
+    del div
+    w = D.normal_weights((512,) * 3, seed=1, device=torch.device("cuda"))
+    _, g, _ = s.adjoint(w, p)
+    drho, dfrac = s.density_grads(rho, g, RHO_PHASE)
+    gh = [host(a) for a in g]
+    rh = c["rho"]
+    d_o, f_o = O.density_grads(rh, gh, RHO_PHASE)
+    assert np.all(np.abs(host(drho) - d_o) <= _density_bound(rh, gh))
+    for got, want_q, dr in zip(dfrac, f_o, (998.0 - 1.2, 880.0 - 1.2)):
+        assert np.all(np.abs(host(got) - want_q) <= _density_bound(rh, gh, 2.0) * dr)

@@ -92,6 +92,31 @@ def test_inner_cycles_reach_exact_32cubed(c32, prec, inner):
     assert all(b < a for a, b in zip(st.history(), st.history()[1:]))
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
+def test_adaptive_inner_cycles_32cubed(c32, prec):
+    """inner_cycles 0: the V-cycles of each outer iteration chosen from the observed contraction.
+    The same discrete solution, at most two V-cycles more than one V-cycle per residual, and
+    fewer outer iterations (FP64 residuals) than two V-cycles per residual."""
+    s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8, inner_cycles=0)
+    s.set_density(dev(c32["rho"]))
+    p = s.solve(dev(c32["b"]))
+    st = s.last_stats
+    assert st.relres <= 1e-10
+    assert rel(host(p), c32["exact8"]) < 1e-9
+    s1 = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8, inner_cycles=1)
+    s1.set_density(dev(c32["rho"]))
+    s1.solve(dev(c32["b"]))
+    assert st.cycles <= s1.last_stats.cycles + 2
+    assert st.outer < (s1.last_stats.cycles + 1) // 2
+    assert len(st.history()) == st.outer + 1
+    assert all(b < a for a, b in zip(st.history(), st.history()[1:]))
+    # max_cycles bounds the adaptive count too
+    s2 = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8, inner_cycles=0, rtol=1e-30, max_cycles=6)
+    s2.set_density(dev(c32["rho"]))
+    s2.solve(dev(c32["b"]), raise_on_nonconvergence=False)
+    assert s2.last_stats.cycles == 6 and s2.last_stats.status == MG_ERR_NOT_CONVERGED
+
+
 @pytest.mark.parametrize("prec,inner", [("fp64", 1), ("mixed", 2), ("mixed", 4), ("mixed_df", 4)])
 def test_fcg_reaches_exact_32cubed(c32, prec, inner):
     """Conjugate gradients preconditioned by one V-cycle (flexible form): the same discrete
@@ -143,9 +168,11 @@ def test_fcg_limits():
 def test_inner_cycles_limits():
     with pytest.raises(MgError):
         Solver((16, 16, 16), precision="fp64", inner_cycles=2)
-    for bad in (0, 9):
+    for bad in (-1, 9):
         with pytest.raises(MgError):
             Solver((16, 16, 16), precision="mixed", inner_cycles=bad)
+    with pytest.raises(MgError):  # the adaptive count is for the V-cycle iteration only
+        Solver((16, 16, 16), precision="mixed", inner_cycles=0, method="fcg")
     # max_cycles bounds the V-cycles: 5 allows two outer iterations of 2
     s = Solver((16, 16, 16), precision="mixed", coarsest=8, rtol=1e-30, max_cycles=5, inner_cycles=2)
     s.set_density(dev(random_rho((16, 16, 16), 9)))
