@@ -101,10 +101,11 @@ typedef struct {
     int inner_cycles; /* mixed modes: FP32 V-cycles per outer iteration (1..8), the first from
                          zero, the next ones continuing from the previous correction; the
                          FP64 (or double-float) residual and update run once per outer
-                         iteration.  0 (V-cycle iteration only): adaptive, 4 V-cycles in the
-                         first outer iteration, then as many (1..8) as the contraction per
+                         iteration.  0 (V-cycle iteration only): adaptive, 5 V-cycles in the
+                         first outer iteration, then as many (1..5) as the contraction per
                          V-cycle observed in the last outer iteration predicts the tolerance
-                         still needs, so that the fewest FP64 residuals are evaluated.  With
+                         still needs, so that few FP64 residuals are evaluated without adding
+                         V-cycles.  With
                          MG_METHOD_FCG: the flexible-CG iterations per outer iteration (1..8).
                          Must be 1 for MG_FP64. */
     int method;       /* MG_METHOD_VCYCLE: V-cycle iteration (defect correction in the mixed

@@ -18,11 +18,13 @@ constexpr int kThreads = 256;
 
 inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// (i, j, k) of cell c; cells number at most 2e9 < 2^32, so 32-bit divisions (64-bit ones cost
+// several times as many instructions)
 __device__ __forceinline__ void cell_ijk(const Dims &d, i64 c, int &i, int &j, int &k) {
-    i = (int)(c % d.nx);
-    i64 r = c / d.nx;
-    j = (int)(r % d.ny);
-    k = (int)(r / d.ny);
+    const unsigned cu = (unsigned)c, r = cu / (unsigned)d.nx;
+    i = (int)(cu - r * (unsigned)d.nx);
+    j = (int)(r % (unsigned)d.ny);
+    k = (int)(r / (unsigned)d.ny);
 }
 
 // sum_f beta_f x_nb in the order x-, x+, y-, y+, z-, z+
@@ -64,9 +66,10 @@ __global__ void k_rbgs_half(Dims d, T h2, Coef<T> cf, const T *__restrict__ b, T
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 rows = (i64)d.ny * d.nz;
     if (t >= rows * half) return;
-    const i64 row = t / half;
-    const int m = (int)(t - row * half);
-    const int j = (int)(row % d.ny), k = (int)(row / d.ny);
+    const unsigned tu = (unsigned)t, rowu = tu / (unsigned)half;  // t < 2^31: 32-bit divisions
+    const i64 row = rowu;
+    const int m = (int)(tu - rowu * (unsigned)half);
+    const int j = (int)(rowu % (unsigned)d.ny), k = (int)(rowu / (unsigned)d.ny);
     const int i = 2 * m + ((colour + j + k) & 1);
     if (i >= d.nx) return;
     const i64 c = row * d.nx + i;
@@ -186,7 +189,7 @@ __global__ void k_prolong_col(Dims cd, Dims f, const T *__restrict__ ec, T *e, i
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const i64 rows = (i64)f.ny * f.nz;
     for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int j = (int)(row % f.ny), k = (int)(row / f.ny);
+        const int j = (int)((unsigned)row % (unsigned)f.ny), k = (int)((unsigned)row / (unsigned)f.ny);
         const int i = 2 * m + ((col + j + k) & 1);
         if (i >= f.nx) continue;
         const int I = i >> 1, J = j >> 1, K = k >> 1;

@@ -255,7 +255,9 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
     const int nx = d.nx, ny = d.ny;
     const i64 nxy = d.nxy, rows = (i64)ny * d.nz;
     for (i64 row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = (int)(row % ny), k = (int)(row / ny);
+        // rows = ny * nz < 2^31: 32-bit division (a 64-bit one costs several times as many
+        // instructions per row)
+        const int r32 = (int)row, j = r32 % ny, k = r32 / ny;
         const i64 c0 = row * nx;
         const i64 ax0 = row * (nx + 1);                        // x faces: (nz, ny, nx + 1)
         const i64 ay0 = ((i64)k * (ny + 1) + j) * nx;          // y faces: (nz, ny + 1, nx)

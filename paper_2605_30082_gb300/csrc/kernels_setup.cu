@@ -52,7 +52,7 @@ __global__ void k_faces_from_s(Dims d, const double *__restrict__ sv, double *fx
     if (i >= d.nx) return;
     const i64 rows = (i64)d.ny * d.nz;
     for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int j = (int)(row % d.ny), k = (int)(row / d.ny);
+        const int j = (int)((unsigned)row % (unsigned)d.ny), k = (int)((unsigned)row / (unsigned)d.ny);  // rows < 2^31
         const i64 c = row * d.nx + i;
         const double sc = sv[c];
         fx[c] = i > 0 ? 0.5 * (sv[c - 1] + sc) : 0.0;
@@ -66,9 +66,10 @@ __global__ void k_faces_from_api(Dims d, const double *__restrict__ bx, const do
                                  unsigned *err) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     double vx = 0.0, vy = 0.0, vz = 0.0;
     if (i > 0) vx = bx[((i64)k * d.ny + j) * (d.nx + 1) + i];
     if (j > 0) vy = by[((i64)k * (d.ny + 1) + j) * d.nx + i];
@@ -85,9 +86,10 @@ __global__ void k_faces_to_api(Dims d, const double *__restrict__ fx, const doub
                                const double *__restrict__ fz, double *bx, double *by, double *bz) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
     i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
     bx[ax] = i > 0 ? fx[c] : 0.0;
@@ -102,9 +104,10 @@ __global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *_
                           const double *__restrict__ fz, double *invd64, double *diag) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     // order x-, x+, y-, y+, z-, z+ (low faces of i=0 etc. are stored as 0)
     double s = fx[c];
     if (i < d.nx - 1) s += fx[c + 1];
@@ -147,9 +150,10 @@ __global__ void k_csf_faces(Dims d, double ih, const double *__restrict__ f,
                             const double *__restrict__ kap, double *cx, double *cy, double *cz) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
     i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
     double fc = f[c], kc = kap[c];
@@ -170,9 +174,10 @@ __global__ void k_rhs(Dims d, double ih, const double *b0, const double *__restr
                       double *b) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     i64 ax = ((i64)k * d.ny + j) * (d.nx + 1) + i;
     i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
     double v = b0 ? b0[c] : 0.0;
@@ -206,9 +211,10 @@ __global__ void k_coarse_assemble(Dims d, double ih2, const double *__restrict__
                                   double *M) {
     i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d.n) return;
-    int i = (int)(c % d.nx);
-    int j = (int)((c / d.nx) % d.ny);
-    int k = (int)(c / d.nxy);
+    const unsigned cu_ = (unsigned)c, ru_ = cu_ / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    int i = (int)(cu_ - ru_ * (unsigned)d.nx);
+    int j = (int)(ru_ % (unsigned)d.ny);
+    int k = (int)(ru_ / (unsigned)d.ny);
     double *row = M + c * d.n;
     for (i64 q = 0; q < d.n; ++q) row[q] = 0.0;
     double diag = 0.0, v;

@@ -133,9 +133,12 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 rows = (i64)L.ny * L.nz;
     if (t >= rows * kv) return;
-    const i64 row = t / kv;
-    const int k0 = (int)(t - row * kv) << 2;
-    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    // thread and row indices stay below 2^31 (at most 2e9 cells): 32-bit divisions, several
+    // times cheaper than 64-bit ones
+    const unsigned tu = (unsigned)t, rowu = tu / (unsigned)kv;
+    const i64 row = rowu;
+    const int k0 = (int)(tu - rowu * (unsigned)kv) << 2;
+    const int y = (int)(rowu % (unsigned)L.ny), z = (int)(rowu / (unsigned)L.ny);
     const int p = (col + y + z) & 1;  // x = 2k + p
     const i64 own = col * L.half + row * hx + k0;
     const i64 opp = (1 - col) * L.half + row * hx + k0;
@@ -581,9 +584,11 @@ __global__ void __launch_bounds__(kRrThreads, 12) k_rr_red_vec(Lay L, Lay Lc, fl
     const i64 T = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 crows = (i64)Lc.ny * Lc.nz;
     if (T >= crows * kv) return;
-    const i64 crow = T / kv;
-    const int k0 = (int)(T - crow * kv) << 2;
-    const int J = (int)(crow % Lc.ny), K = (int)(crow / Lc.ny);
+    // thread and row indices stay below 2^31 (at most 2e9 cells): 32-bit divisions, several
+    // times cheaper than 64-bit ones
+    const unsigned Tu = (unsigned)T, crowu = Tu / (unsigned)kv;
+    const int k0 = (int)(Tu - crowu * (unsigned)kv) << 2;
+    const int J = (int)(crowu % (unsigned)Lc.ny), K = (int)(crowu / (unsigned)Lc.ny);
     const i64 dy = hx, dz = (i64)L.ny * hx;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -673,9 +678,12 @@ __global__ void k_prolong_red_vec(Lay L, Lay Lc, const float *__restrict__ ec, f
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 rows = (i64)L.ny * L.nz;
     if (t >= rows * kv) return;
-    const i64 row = t / kv;
-    const int k0 = (int)(t - row * kv) << 2;
-    const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+    // thread and row indices stay below 2^31 (at most 2e9 cells): 32-bit divisions, several
+    // times cheaper than 64-bit ones
+    const unsigned tu = (unsigned)t, rowu = tu / (unsigned)kv;
+    const i64 row = rowu;
+    const int k0 = (int)(tu - rowu * (unsigned)kv) << 2;
+    const int y = (int)(rowu % (unsigned)L.ny), z = (int)(rowu / (unsigned)L.ny);
     const int p = (y + z) & 1;  // red x = 2k + p, coarse I = k
     const int J = y >> 1, K = z >> 1;
     float out[4];
@@ -739,9 +747,11 @@ __global__ void __launch_bounds__(kProlThreads, 10) k_prolong_red8(Lay L, Lay Lc
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 crows = (i64)Lc.ny * Lc.nz;
     if (t >= crows * kv) return;
-    const i64 crow = t / kv;
-    const int k0 = (int)(t - crow * kv) << 3;
-    const int J = (int)(crow % Lc.ny), K = (int)(crow / Lc.ny);
+    // thread and row indices stay below 2^31 (at most 2e9 cells): 32-bit divisions, several
+    // times cheaper than 64-bit ones
+    const unsigned tu = (unsigned)t, crowu = tu / (unsigned)kv;
+    const int k0 = (int)(tu - crowu * (unsigned)kv) << 3;
+    const int J = (int)(crowu % (unsigned)Lc.ny), K = (int)(crowu / (unsigned)Lc.ny);
     const int hxc = Lc.hx, ncx = Lc.nx;
     const int Js[3] = {max(J - 1, 0), J, min(J + 1, Lc.ny - 1)};
     const int Ks[3] = {max(K - 1, 0), K, min(K + 1, Lc.nz - 1)};
