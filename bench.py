@@ -461,6 +461,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def gpu_local_cpus(index):
+    """The CPUs of the GPU's NUMA node that this process may use (from sysfs), or None."""
+    import torch
+
+    try:
+        pr = torch.cuda.get_device_properties(index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        txt = open(f"/sys/bus/pci/devices/{bus}/local_cpulist").read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def _e2e(args, s, step, fd, ff, u, w):
     """The step through the public API with inputs in pinned host memory and results read back.
 
@@ -470,8 +488,27 @@ def _e2e(args, s, step, fd, ff, u, w):
     copies run on a second stream with double-buffered device arrays: step k+1's inputs are
     copied in while step k computes, and step k's results are copied out while step k+1
     computes (the pipelining a user of the library would write).  All buffers are allocated and
-    one pipelined step is run before timing.
+    one pipelined step is run before timing.  The host buffers are allocated, and the host thread
+    runs, on the CPUs of the GPU's own NUMA node where sysfs names them (pinned pages land on the
+    node of the thread that allocates them; copies from the other socket's memory cross the
+    CPU-to-CPU link).
     """
+    import torch
+
+    local = gpu_local_cpus(fd.device.index)
+    old_aff = os.sched_getaffinity(0)
+    if local:
+        os.sched_setaffinity(0, local)
+    try:
+        out = _e2e_pinned(args, s, step, fd, ff, u, w)
+    finally:
+        os.sched_setaffinity(0, old_aff)
+    out["host_cpus"] = (f"{len(local)} CPUs of the GPU's NUMA node" if local else
+                        "unchanged (the GPU's NUMA node is not named in sysfs)")
+    return out
+
+
+def _e2e_pinned(args, s, step, fd, ff, u, w):
     import torch
 
     srcs = (fd, ff, *u, w)

@@ -90,10 +90,11 @@ __global__ void k_cg_apply32(Lay L, float ih2, Coef32c cf, const float *__restri
     double acc = 0.0;
     for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * per_col; t += (i64)gridDim.x * blockDim.x) {
         const int col = t >= per_col;
-        const i64 tt = t - col * per_col;
-        const i64 row = tt / kv;
-        const int k0 = (int)(tt - row * kv) << 2;
-        const int y = (int)(row % L.ny), z = (int)(row / L.ny);
+        // t < n / 4 < 2^31: 32-bit divisions (64-bit ones cost several times as many instructions)
+        const unsigned tt = (unsigned)(t - col * per_col), rowu = tt / (unsigned)kv;
+        const i64 row = rowu;
+        const int k0 = (int)(tt - rowu * (unsigned)kv) << 2;
+        const int y = (int)(rowu % (unsigned)L.ny), z = (int)(rowu / (unsigned)L.ny);
         const int p = (col + y + z) & 1;
         const i64 own = col * L.half + row * hx + k0;
         const i64 opp = (1 - col) * L.half + row * hx + k0;
