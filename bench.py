@@ -461,6 +461,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def parse_cpulist(txt):
+    """The CPU numbers of a sysfs cpulist such as '0-3,8,10-11'."""
+    cpus = set()
+    for part in txt.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
 def gpu_local_cpus(index):
     """The CPUs of the GPU's NUMA node that this process may use (from sysfs), or None."""
     import torch
@@ -468,11 +479,7 @@ def gpu_local_cpus(index):
     try:
         pr = torch.cuda.get_device_properties(index)
         bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
-        txt = open(f"/sys/bus/pci/devices/{bus}/local_cpulist").read().strip()
-        cpus = set()
-        for part in txt.split(","):
-            a, _, b = part.partition("-")
-            cpus.update(range(int(a), int(b or a) + 1))
+        cpus = parse_cpulist(open(f"/sys/bus/pci/devices/{bus}/local_cpulist").read())
         cpus &= os.sched_getaffinity(0)
         return cpus or None
     except Exception:

@@ -30,7 +30,21 @@ __global__ void k_density(i64 n, FracArgs a, double *rho) {
     rho[m] = r + a.rho[a.nfrac] * rest;
 }
 
-__device__ __forceinline__ bool good_positive(double v) { return v > 0.0 && v <= 1.79e308; }
+// 0 < v <= 1.79e308, tested on the bit pattern (positive doubles order like their bits, NaN and
+// infinity lie above the bound, negative values and zero at or below 0): no FP64 comparison
+__device__ __forceinline__ bool good_positive(double v) {
+    const long long u = __double_as_longlong(v);
+    return u > 0 && u <= 0x7fefdcf158adbb99ll;
+}
+
+// v / 2 for v = 0 or normal with a normal result (exponent field above 1): one integer subtraction
+// from the exponent field instead of an FP64 multiplication; otherwise the multiplication
+__device__ __forceinline__ double half_of(double v) {
+    const long long u = __double_as_longlong(v);
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (e > 1 && e < 0x7ff) return __longlong_as_double(u - (1ll << 52));
+    return 0.5 * v;
+}
 
 // s = 1/rho per cell, validating rho (finite and > 0)
 __global__ void k_inv_rho(i64 n, const double *__restrict__ rho, double *sinv, unsigned *err) {
@@ -55,9 +69,9 @@ __global__ void k_faces_from_s(Dims d, const double *__restrict__ sv, double *fx
         const int j = (int)((unsigned)row % (unsigned)d.ny), k = (int)((unsigned)row / (unsigned)d.ny);  // rows < 2^31
         const i64 c = row * d.nx + i;
         const double sc = sv[c];
-        fx[c] = i > 0 ? 0.5 * (sv[c - 1] + sc) : 0.0;
-        fy[c] = j > 0 ? 0.5 * (sv[c - d.nx] + sc) : 0.0;
-        fz[c] = k > 0 ? 0.5 * (sv[c - d.nxy] + sc) : 0.0;
+        fx[c] = i > 0 ? half_of(sv[c - 1] + sc) : 0.0;
+        fy[c] = j > 0 ? half_of(sv[c - d.nx] + sc) : 0.0;
+        fz[c] = k > 0 ? half_of(sv[c - d.nxy] + sc) : 0.0;
     }
 }
 
@@ -182,14 +196,13 @@ __global__ void k_rhs(Dims d, double ih, const double *b0, const double *__restr
     i64 ay = ((i64)k * (d.ny + 1) + j) * d.nx + i;
     double v = b0 ? b0[c] : 0.0;
     if (ux) {
-        double s = 0.0;
-        if (i > 0) s -= ux[ax];
-        if (i < d.nx - 1) s += ux[ax + 1];
-        if (j > 0) s -= uy[ay];
-        if (j < d.ny - 1) s += uy[ay + d.nx];
-        if (k > 0) s -= uz[c];
-        if (k < d.nz - 1) s += uz[c + d.nxy];
-        v += s * ih;
+        // (high - low) per axis, wall faces as 0: five FP64 additions and one fused
+        // multiply-add per cell
+        const double xm = i > 0 ? ux[ax] : 0.0, xp = i < d.nx - 1 ? ux[ax + 1] : 0.0;
+        const double ym = j > 0 ? uy[ay] : 0.0, yp = j < d.ny - 1 ? uy[ay + d.nx] : 0.0;
+        const double zm = k > 0 ? uz[c] : 0.0, zp = k < d.nz - 1 ? uz[c + d.nxy] : 0.0;
+        const double s = ((xp - xm) + (yp - ym)) + (zp - zm);
+        v = fma(s, ih, v);
     }
     if (csx) {
         double t = 0.0;

@@ -110,7 +110,10 @@ __device__ __forceinline__ float d2f_rn(double v) {
 // unit in the last place of 1/x.  Outside [2^-100, 2^100] (where the FP32 seed could leave
 // the FP32 range) it divides.
 __device__ __forceinline__ double recip64(double x) {
-    if (!(x >= 7.888609052210118e-31 && x <= 1.2676506002282294e30)) return 1.0 / x;
+    // the range test on the bit pattern (positive doubles order like their bits): no FP64
+    // comparison on the FP64 pipe
+    const long long xb = __double_as_longlong(x);
+    if (!(xb >= 0x39b0000000000000ll && xb <= 0x4630000000000000ll)) return 1.0 / x;
     double y = f2d_exact(__frcp_rn(d2f_rn(x)));
     double e = fma(-x, y, 1.0);
     y = fma(y, e, y);

@@ -55,3 +55,13 @@ def test_max_over_ranks_without_a_process_group():
     import bench
 
     assert bench.max_over_ranks(4.5) == 4.5
+
+
+def test_cpulist_parsing():
+    """The sysfs cpulist format that places the end-to-end host buffers on the GPU's node."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()

@@ -27,7 +27,7 @@ import dropfilm as D
 import oracle as O
 from paper_2605_30082_gb300 import PoissonSolveFractions, Solver
 
-from _helpers import RHO_PHASE, csf_case, dev, host, rel
+from _helpers import RHO_PHASE, csf_case, dev, host, random_rho, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -198,3 +198,62 @@ def test_fractions_autograd_finite_differences_32cubed():
     bo = O.rhs([a.numpy() for a in c["u"]], c["faces"], h, csf=c["csf"], sigma=0.03)
     _, ds_o = O.adjoint_grads(c["faces"], lam_o, M.solve_exact(bo)[0], h, csf=c["csf"], sigma=0.03)
     assert abs(float(sigma.grad) - ds_o) <= 1e-8 * abs(ds_o)
+
+
+@pytest.mark.parametrize("with_csf", [False, True])
+def test_projection_spacing_not_a_power_of_two(with_csf):
+    """h = 1/48: the velocity correction multiplies by 1/h in FP64 (no exponent scaling)."""
+    c = csf_case(48)
+    h, sigma = c["h"], 0.03
+    s = Solver((48, 48, 48), h=h, precision="mixed", coarsest=8)
+    s.set_density(dev(c["rho"]))
+    csf_h = c["csf"] if with_csf else None
+    csf = tuple(dev(a) for a in csf_h) if with_csf else None
+    u_h = [a.numpy() for a in c["u"]]
+    p = s.solve(s.rhs(u=tuple(dev(a) for a in u_h), csf=csf, sigma=sigma))
+    out = s.project(p, [dev(a) for a in u_h], csf=csf, sigma=sigma,
+                    out=[torch.empty(a.shape, dtype=torch.float64, device="cuda") for a in u_h])
+    want = O.project(u_h, c["faces"], host(p), h, csf=csf_h, sigma=sigma)
+    for a, w in zip(out, want):
+        assert np.abs(host(a) - w).max() <= 1e-14 * np.abs(w).max()
+
+
+@pytest.mark.parametrize("nfrac", [1, 3, 4])
+def test_density_grads_fraction_counts(nfrac):
+    """1, 3 and 4 fractions (Eq. (5) with nfrac + 1 phases), random FP32 face gradients, against
+    the oracle's formula on the same gradients within the FP32 rounding bound."""
+    dims = (24, 20, 16)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(20 + nfrac)
+    phase = list(rng.uniform(1.0, 1000.0, nfrac + 1))
+    rho = random_rho(dims, 30 + nfrac)
+    s = Solver(dims, h=1.0 / 24, precision="mixed", coarsest=8)
+    g = tuple(torch.tensor(rng.standard_normal(sh), dtype=torch.float32, device="cuda") for sh in s.face_shapes)
+    drho, dfrac = s.density_grads(dev(rho), g, phase)
+    assert len(dfrac) == nfrac
+    gh = [host(a) for a in g]
+    d_o, f_o = O.density_grads(rho, gh, phase)
+    assert np.all(np.abs(host(drho) - d_o) <= _density_bound(rho, gh))
+    for q in range(nfrac):
+        dr = abs(phase[q] - phase[nfrac])
+        assert np.all(np.abs(host(dfrac[q]) - f_o[q]) <= _density_bound(rho, gh, 2.0) * dr + 1e-300)
+
+
+def test_density_grads_outside_the_fp32_range_use_fp64():
+    """Densities outside [2^-20, 2^21) take the FP64 formula: tiny and huge densities give the
+    oracle's values to FP32 precision of the summed gradients (no overflow, no underflow)."""
+    dims = (16, 16, 16)
+    rho = random_rho(dims, 41)
+    rho[0, 0, :8] = 1e-9
+    rho[3, 5, :8] = 1e9
+    rho[7, 7, 7] = 2.0 ** -20  # the edge of the FP32 path
+    s = Solver(dims, h=1.0 / 16, precision="mixed", coarsest=8)
+    rng = np.random.default_rng(5)
+    g = tuple(torch.tensor(rng.standard_normal(sh), dtype=torch.float32, device="cuda") for sh in s.face_shapes)
+    drho = s.density_grads(dev(rho), g)
+    gh = [host(a) for a in g]
+    d_o = O.density_grads(rho, gh)
+    got = host(drho)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - d_o) <= _density_bound(rho, gh))
+    assert abs(got[0, 0, 0]) > 1e15  # -sum g / (2 rho^2) with rho = 1e-9
