@@ -14,14 +14,15 @@
 // ZC planes in z.  At step t the tile computes c1 at plane t on rows y0-1 .. y0+TY (one row
 // of halo on each side, and the scalar positions k0-1 and k0+TX) and then c2 at plane t-1
 // on its own rows, from c1 at planes t-2, t-1, t kept in shared memory.  The arrays of one
-// plane (old c2 and s of c2 on rows y0-2 .. y0+TY+1, s and b of c1 on rows y0-1 .. y0+TY, b
-// of c2 on the tile's rows; columns k0-4 .. k0+TX+3) form one stage of a ring of
-// kStages = kAhead + 4 stages: the stage of plane t+1+kAhead is copied in while planes t-2 ..
-// t+1 are in use.  One warp issues the copies (cp.async.bulk, one per row and array,
-// completion counted in bytes on the stage's mbarrier); every thread waits on the mbarrier of
-// the newest plane before computing.  Each wait is bounded: after kSpinLimit polls the block
-// records an error in the device error word, waits (bounded again) for the copies it issued
-// and returns.
+// plane that neighbours read (old c2 and s of c2 on rows y0-2 .. y0+TY+1, s of c1 on rows
+// y0-1 .. y0+TY; columns k0-4 .. k0+TX+3) form one stage of a ring of kStages = kAhead + 4
+// stages: the stage of plane t+1+kAhead is copied in while planes t-2 .. t+1 are in use.
+// b, read only at a thread's own cells, goes to registers one plane ahead.  One warp issues
+// the copies (cp.async.bulk, one per row and array, completion counted in bytes on the
+// stage's mbarrier); every thread waits on the mbarrier of the newest plane before computing.
+// Each wait is bounded (about a second): when one runs out the block records an error in the
+// device error word (bit 4), waits (bounded again) for the copies it issued and returns;
+// blocks that start after that return at once.
 //
 // The per-cell arithmetic is that of the half-sweep kernels, in the same order, so the fused
 // sweep gives bitwise the results of a red and a black half sweep.
@@ -38,9 +39,8 @@ constexpr int ZC = 64;               // planes per tile
 constexpr int W = TX + 8;            // shared-memory row: k0-4 .. k0+TX+3
 constexpr int kAhead = 2;            // planes copied ahead of the newest plane in use
 constexpr int kStages = kAhead + 4;  // planes t-2 .. t+1 in use, kAhead in flight
-constexpr int R_XO = TY + 4, R_S2 = TY + 4, R_S1 = TY + 2, R_B1 = TY + 2, R_B2 = TY;
-constexpr int O_XO = 0, O_S2 = O_XO + R_XO * W, O_S1 = O_S2 + R_S2 * W, O_B1 = O_S1 + R_S1 * W,
-              O_B2 = O_B1 + R_B1 * W, STAGE = O_B2 + R_B2 * W;  // floats per stage
+constexpr int R_XO = TY + 4, R_S2 = TY + 4, R_S1 = TY + 2;
+constexpr int O_XO = 0, O_S2 = O_XO + R_XO * W, O_S1 = O_S2 + R_S2 * W, STAGE = O_S1 + R_S1 * W;  // floats per stage
 constexpr int R_C1 = TY + 2;         // rows of new c1 values kept per plane
 constexpr int C1PLANE = R_C1 * W;
 constexpr int kThreads = 160;        // 10 rows x 16 vectors of c1; warps 0-3 also do c2
@@ -178,8 +178,8 @@ __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0,
     const unsigned rb = (unsigned)(ke - ks) * 4u;
     const int e = ks - (k0 - 4);
     const bool plane_ok = q >= 0 && q < g.nz;
-    // row tasks: XO (R_XO), S2 (R_S2), S1 (R_S1), B1 (R_B1), B2 (R_B2)
-    constexpr int NT = R_XO + R_S2 + R_S1 + R_B1 + R_B2;
+    // row tasks: XO (R_XO), S2 (R_S2), S1 (R_S1)
+    constexpr int NT = R_XO + R_S2 + R_S1;
     const float *srcs[2];
     unsigned dsts[2];
     int cnt = 0;
@@ -191,12 +191,8 @@ __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0,
             r = task; off = O_XO; y = y0 - 2 + r; base = from_zero ? nullptr : X + c2 * g.half;
         } else if (task < R_XO + R_S2) {
             r = task - R_XO; off = O_S2; y = y0 - 2 + r; base = sv + c2 * g.half;
-        } else if (task < R_XO + R_S2 + R_S1) {
-            r = task - R_XO - R_S2; off = O_S1; y = y0 - 1 + r; base = sv + c1 * g.half;
-        } else if (task < R_XO + R_S2 + R_S1 + R_B1) {
-            r = task - R_XO - R_S2 - R_S1; off = O_B1; y = y0 - 1 + r; base = b + c1 * g.half;
         } else {
-            r = task - R_XO - R_S2 - R_S1 - R_B1; off = O_B2; y = y0 + r; base = b + c2 * g.half;
+            r = task - R_XO - R_S2; off = O_S1; y = y0 - 1 + r; base = sv + c1 * g.half;
         }
         if (!plane_ok || base == nullptr || y < 0 || y >= g.ny) continue;
         srcs[cnt] = base + (long long)q * g.dz + (long long)y * g.hx + ks;
@@ -214,7 +210,7 @@ __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0,
 }
 
 template <bool FROM_ZERO, bool UPDATE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_sweep_fused(Geo g, float h2, const float *__restrict__ sv, const float *__restrict__ b, const float *X,
                   float *Y, int c1, FUpd up, unsigned *err) {
     extern __shared__ __align__(16) float sm[];
@@ -260,6 +256,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int r2 = tid / (TX / 4), v2 = tid % (TX / 4);
     const int y2 = y0 + r2;
     const int kv2 = k0 + 4 * v2, e2 = 4 + 4 * v2;
+    // b is read only at a thread's own cells: it bypasses the stages and is loaded into
+    // registers one step ahead (c1 of plane t+1, c2 of plane t, while plane t computes)
+    const bool c1row = y1 >= 0 && y1 < g.ny, hrow = tid < 2 * R_C1 && yh >= 0 && yh < g.ny && kh >= 0 && kh < g.hx;
+    const bool c2row = tid < TY * (TX / 4) && y2 < g.ny;
+    const float *b1p = b + c1 * g.half + (long long)y1 * g.hx + kv1;
+    const float *bhp = b + c1 * g.half + (long long)yh * g.hx + kh;
+    const float *b2p = b + c2 * g.half + (long long)y2 * g.hx + kv2;
+    auto ldb4 = [&](const float *bp, bool row_ok, int q) {
+        return (row_ok && q >= 0 && q < g.nz) ? *reinterpret_cast<const float4 *>(bp + (long long)q * g.dz) : F0;
+    };
+    auto ldb1 = [&](const float *bp, bool row_ok, int q) {
+        return (row_ok && q >= 0 && q < g.nz) ? bp[(long long)q * g.dz] : 0.f;
+    };
+    float4 b1cur = ldb4(b1p, c1row, z0 - 1), b2cur = F0;
+    float bhcur = ldb1(bhp, hrow, z0 - 1);
 
     for (int t = z0 - 1; t <= zend; ++t) {
         // the newest plane in use; the barrier below makes a failed wait everyone's exit
@@ -276,6 +287,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                             lane);
             issued = q;
         }
+        // b for the next step
+        const float4 b1nxt = ldb4(b1p, c1row, t + 1), b2nxt = ldb4(b2p, c2row, t);
+        const float bhnxt = ldb1(bhp, hrow, t + 1);
         const float *Sm = stages + (size_t)stage_of(t - 1 >= qlo ? t - 1 : qlo) * STAGE;  // plane t-1
         const float *Sc = stages + (size_t)stage_of(t) * STAGE;                            // plane t
         const float *Sp = stages + (size_t)stage_of(t + 1 <= qhi ? t + 1 : qhi) * STAGE;  // plane t+1
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float4 s3 = hy1 ? ld4(Sc + O_S2 + (ro + 1) * W + e1) : F0;
                 const float4 s4 = hz0 ? ld4(Sm + O_S2 + ro * W + e1) : F0;
                 const float4 s5 = hz1 ? ld4(Sp + O_S2 + ro * W + e1) : F0;
-                const float4 b4 = ld4(Sc + O_B1 + r1 * W + e1);
+                const float4 b4 = b1cur;
                 float sl, sr;
                 window_ends(so4, Sc + O_S2 + ro * W + e1, lane, kl, kr, sl, sr);
                 float4 xo4 = F0, ym4 = F0, yp4 = F0, zm4 = F0, zp4 = F0;
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float w3 = hy1 ? sc + Sc[O_S2 + (ro + 1) * W + e] : 0.f;
                 const float w4 = hz0 ? sc + Sm[O_S2 + ro * W + e] : 0.f;
                 const float w5 = hz1 ? sc + Sp[O_S2 + ro * W + e] : 0.f;
-                const float bb = Sc[O_B1 + rh * W + e];
+                const float bb = bhcur;
                 float o;
                 if (FROM_ZERO) {
                     o = gs_from_zero(w0, w1, w2, w3, w4, w5, hh, bb);
@@ -372,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float4 s3 = hy1 ? ld4(Tc + O_S1 + (rc + 1) * W + e2) : F0;
             const float4 s4 = hz0 ? ld4(Tm + O_S1 + rc * W + e2) : F0;
             const float4 s5 = hz1 ? ld4(Tp + O_S1 + rc * W + e2) : F0;
-            const float4 b4 = ld4(Tc + O_B2 + r2 * W + e2);
+            const float4 b4 = b2cur;
             const float4 xo4 = ld4(Cc + rc * W + e2);
             const float4 ym4 = hy0 ? ld4(Cc + (rc - 1) * W + e2) : F0;
             const float4 yp4 = hy1 ? ld4(Cc + (rc + 1) * W + e2) : F0;
@@ -405,6 +419,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
             }
         }
+        b1cur = b1nxt;
+        b2cur = b2nxt;
+        bhcur = bhnxt;
     }
     if (abort_flag) {
         // a wait ran out: record it, then wait (bounded) for every copy this block issued

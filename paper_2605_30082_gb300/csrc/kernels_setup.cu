@@ -261,21 +261,88 @@ __global__ void k_coarse_shift(int nc, double *M, double *scal) {
     }
 }
 
-// One Gauss-Jordan sweep on pivot k, out of place.  scal[1] holds 1/pivot;
-// the thread owning the next pivot stores its reciprocal in scal[2] (swapped by the host).
-__global__ void k_gj_step(int nc, int k, const double *__restrict__ A, double *B,
-                          const double *__restrict__ rpiv_in, double *rpiv_out) {
-    i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (i64)nc * nc) return;
-    int i = (int)(e / nc), j = (int)(e % nc);
-    double rp = *rpiv_in;
-    double v;
-    if (i == k && j == k) v = rp;
-    else if (i == k) v = A[(i64)k * nc + j] * rp;
-    else if (j == k) v = -A[(i64)i * nc + k] * rp;
-    else v = A[e] - A[(i64)i * nc + k] * (A[(i64)k * nc + j] * rp);
-    B[e] = v;
-    if (i == k + 1 && j == k + 1 && rpiv_out) *rpiv_out = 1.0 / v;
+// ---- blocked Gauss-Jordan inversion in place (no pivoting: M is symmetric positive definite)
+// Block step on the pivot block K = [kb, kb + bs): P^-1 (one block), the row panel
+// M[K, J] <- P^-1 M[K, J], the trailing update M[I, J] <- M[I, J] - M[I, K] M[K, J], and the
+// column panel M[I, K] <- -M[I, K] P^-1, M[K, K] <- P^-1 (I, J outside K).  The same algebra as
+// the element-wise sweeps, BS pivots per step, so n / BS steps of four launches instead of n.
+constexpr int GJ_BS = 32;
+
+// P^-1 of the bs x bs pivot block by element-wise Gauss-Jordan in shared memory; Pinv (bs x bs,
+// row-major) written to global scratch.  One block of GJ_BS x GJ_BS threads.
+__global__ void k_gj_pivot_inv(int n, int kb, int bs, const double *__restrict__ M, double *Pinv) {
+    __shared__ double P[GJ_BS][GJ_BS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (tx < bs && ty < bs) P[ty][tx] = M[(i64)(kb + ty) * n + kb + tx];
+    __syncthreads();
+    for (int k = 0; k < bs; ++k) {
+        double v = 0.0;
+        if (tx < bs && ty < bs) {
+            const double rp = 1.0 / P[k][k];
+            if (ty == k && tx == k) v = rp;
+            else if (ty == k) v = P[k][tx] * rp;
+            else if (tx == k) v = -P[ty][k] * rp;
+            else v = P[ty][tx] - P[ty][k] * (P[k][tx] * rp);
+        }
+        __syncthreads();
+        if (tx < bs && ty < bs) P[ty][tx] = v;
+        __syncthreads();
+    }
+    if (tx < bs && ty < bs) Pinv[ty * GJ_BS + tx] = P[ty][tx];
+}
+
+// row panel: for the 32-column tile blockIdx.x (skipping K's columns), M[K, J] <- P^-1 M[K, J]
+__global__ void k_gj_row_panel(int n, int kb, int bs, double *M, const double *__restrict__ Pinv) {
+    __shared__ double Pi[GJ_BS][GJ_BS + 1], R[GJ_BS][GJ_BS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int j = blockIdx.x * GJ_BS + tx;
+    const bool colok = j < n && (j < kb || j >= kb + bs);
+    if (ty < bs && tx < bs) Pi[ty][tx] = Pinv[ty * GJ_BS + tx];
+    if (ty < bs) R[ty][tx] = colok ? M[(i64)(kb + ty) * n + j] : 0.0;
+    __syncthreads();
+    if (ty < bs && colok) {
+        double acc = 0.0;
+        for (int t = 0; t < bs; ++t) acc = fma(Pi[ty][t], R[t][tx], acc);
+        M[(i64)(kb + ty) * n + j] = acc;
+    }
+}
+
+// trailing update of the 32 x 32 tile (blockIdx.y rows, blockIdx.x columns), rows and columns
+// outside K: M[i, j] -= sum_t M[i, kb + t] M[kb + t, j] (the row panel already updated)
+__global__ void k_gj_trailing(int n, int kb, int bs, double *M) {
+    __shared__ double C[GJ_BS][GJ_BS + 1], R[GJ_BS][GJ_BS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.y * GJ_BS + ty, j = blockIdx.x * GJ_BS + tx;
+    const bool rowok = i < n && (i < kb || i >= kb + bs), colok = j < n && (j < kb || j >= kb + bs);
+    // C[ty][t] = M[i, kb + t], R[t][tx] = M[kb + t, j]
+    C[ty][tx] = (i < n && tx < bs) ? M[(i64)i * n + kb + tx] : 0.0;
+    R[ty][tx] = (ty < bs && j < n) ? M[(i64)(kb + ty) * n + j] : 0.0;
+    __syncthreads();
+    if (rowok && colok) {
+        double acc = M[(i64)i * n + j];
+        for (int t = 0; t < bs; ++t) acc = fma(-C[ty][t], R[t][tx], acc);
+        M[(i64)i * n + j] = acc;
+    }
+}
+
+// column panel: M[i, K] <- -M[i, K] P^-1 for rows i outside K; the block of rows holding K
+// writes M[K, K] = P^-1
+__global__ void k_gj_col_panel(int n, int kb, int bs, double *M, const double *__restrict__ Pinv) {
+    __shared__ double Pi[GJ_BS][GJ_BS + 1], C[GJ_BS][GJ_BS + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * GJ_BS + ty;
+    if (ty < bs && tx < bs) Pi[ty][tx] = Pinv[ty * GJ_BS + tx];
+    C[ty][tx] = (i < n && tx < bs) ? M[(i64)i * n + kb + tx] : 0.0;
+    __syncthreads();
+    if (i < n && tx < bs) {
+        if (i >= kb && i < kb + bs) {
+            M[(i64)i * n + kb + tx] = Pi[i - kb][tx];
+        } else {
+            double acc = 0.0;
+            for (int t = 0; t < bs; ++t) acc = fma(C[ty][t], Pi[t][tx], acc);
+            M[(i64)i * n + kb + tx] = -acc;
+        }
+    }
 }
 
 __global__ void k_pinv_finish(int nc, double *M, const double *__restrict__ scal) {
@@ -359,12 +426,17 @@ void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx
     k_coarse_shift<<<1, 1024, 0, s>>>((int)d.n, M, scal);
 }
 
-void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mout, double *scal) {
-    // reciprocal pivots alternate between scal[1] and scal[2]
-    const double *rin = scal + 1 + (k & 1);
-    double *rout = (k + 1 < nc) ? scal + 1 + ((k + 1) & 1) : nullptr;
-    count_launch();
-    k_gj_step<<<blocks_for((i64)nc * nc), kThreads, 0, s>>>(nc, k, Min, Mout, rin, rout);
+void launch_gj_blocked(cudaStream_t s, int nc, double *M, double *scratch) {
+    const dim3 blk(GJ_BS, GJ_BS);
+    const int nt = (nc + GJ_BS - 1) / GJ_BS;
+    for (int kb = 0; kb < nc; kb += GJ_BS) {
+        const int bs = nc - kb < GJ_BS ? nc - kb : GJ_BS;
+        count_launch(4);
+        k_gj_pivot_inv<<<1, blk, 0, s>>>(nc, kb, bs, M, scratch);
+        k_gj_row_panel<<<nt, blk, 0, s>>>(nc, kb, bs, M, scratch);
+        k_gj_trailing<<<dim3(nt, nt), blk, 0, s>>>(nc, kb, bs, M);
+        k_gj_col_panel<<<nt, blk, 0, s>>>(nc, kb, bs, M, scratch);
+    }
 }
 
 void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal) {

@@ -334,16 +334,8 @@ int finish_operator(mg_handle *h) {
     }
     // dense pseudo-inverse of the coarsest operator
     Level &C = h->lv[h->nlev - 1];
-    double *A = h->pinv, *B = h->gj_tmp;
-    mg::launch_coarse_assemble(s, C.d, C.ih2, C.fx64, C.fy64, C.fz64, A, h->scal);
-    for (int k = 0; k < h->nc; ++k) {
-        mg::launch_gj_step(s, h->nc, k, A, B, h->scal);
-        double *t = A;
-        A = B;
-        B = t;
-    }
-    if (A != h->pinv) MG_CUDA(h, cudaMemcpyAsync(h->pinv, A, sizeof(double) * (size_t)h->nc * h->nc,
-                                                 cudaMemcpyDeviceToDevice, s));
+    mg::launch_coarse_assemble(s, C.d, C.ih2, C.fx64, C.fy64, C.fz64, h->pinv, h->scal);
+    mg::launch_gj_blocked(s, h->nc, h->pinv, h->gj_tmp);  // in place, 32 pivots per step
     mg::launch_pinv_finish(s, h->nc, h->pinv, h->scal);
     int st = check_launch(h, "operator set-up");
     if (st) return st;

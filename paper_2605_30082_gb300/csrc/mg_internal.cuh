@@ -155,7 +155,8 @@ void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double
 // dense coarse inverse (Gauss-Jordan on A_c + c 1 1^T, then minus 1/(c n^2))
 void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
                             const double *fz, double *M, double *scal);
-void launch_gj_step(cudaStream_t s, int nc, int k, const double *Min, double *Mout, double *scal);
+// Gauss-Jordan inversion in place by blocks of 32 pivots (scratch: 32 x 32 doubles)
+void launch_gj_blocked(cudaStream_t s, int nc, double *M, double *scratch);
 void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 
 // ---- V-cycle kernels --------------------------------------------------------------

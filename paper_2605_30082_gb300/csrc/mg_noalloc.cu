@@ -21,7 +21,8 @@
 namespace {
 
 constexpr int kMaxCells = MG_NOALLOC_MAX_CELLS;
-// layout in doubles: M [kMaxCells^2] | W [kMaxCells^2] | fx, fy, fz [kMaxCells each] | scal [4] | error word
+// layout in doubles: M [kMaxCells^2] | W [kMaxCells^2, of which the inverse of one 32 x 32 pivot
+// block is used] | fx, fy, fz [kMaxCells each] | scal [4] | error word
 constexpr size_t kScratchDoubles = 2 * (size_t)kMaxCells * kMaxCells + 3 * (size_t)kMaxCells + 8;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -80,15 +81,9 @@ extern "C" int mg_dense_solve_noalloc(int nx, int ny, int nz, double h, const do
     mg::launch_faces_from_api(s, d, bx, by, bz, fx, fy, fz, err);
     // every entry of M, W and scal below is written before it is read
     mg::launch_coarse_assemble(s, d, 1.0 / (h * h), fx, fy, fz, M, scal);
-    double *A = M, *B = W;
-    for (int k = 0; k < nc; ++k) {
-        mg::launch_gj_step(s, nc, k, A, B, scal);
-        double *t = A;
-        A = B;
-        B = t;
-    }
-    mg::launch_pinv_finish(s, nc, A, scal);
-    mg::launch_coarse_matvec<double>(s, nc, A, r, e);
+    mg::launch_gj_blocked(s, nc, M, W);  // in place; W holds each pivot block's inverse
+    mg::launch_pinv_finish(s, nc, M, scal);
+    mg::launch_coarse_matvec<double>(s, nc, M, r, e);
     unsigned herr = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

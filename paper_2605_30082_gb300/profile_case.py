@@ -1,11 +1,14 @@
-"""A small solve for kernel profiling: python -m paper_2605_30082_gb300.profile_case NX NY NZ [PRECISION [INNER [CYCLES]]]
+"""A small solve for kernel profiling:
+python -m paper_2605_30082_gb300.profile_case NX NY NZ [PRECISION [INNER [CYCLES [FUSED]]]]
 
 Random density in [1.2, 998] and random right-hand side (torch generators, seeds 3 and 4),
 `CYCLES` V-cycles (default 2) of the given precision ('fp64', 'mixed', 'mixed_df'), followed by
-one adjoint solve of as many cycles, one velocity correction of random face velocities (seed 5,
-out of place) and one density adjoint of random FP32 face gradients (seed 6, two fractions).  Sized by the caller so that every array is larger than L2
-while the whole case holds a few GB: e.g. 512 512 256 keeps the 512-cell rows (and so the launch
-configuration) of the 512^3 workload at half its cells.
+one adjoint solve of as many cycles, one velocity correction of random face velocities (seeds
+5-7, out of place) and one density adjoint of random FP32 face gradients (seeds 8-10, two
+fractions).  Sized by the caller so that every array is larger than L2 while the whole case
+holds a few GB: e.g. 512 512 256 keeps the 512-cell rows (and so the launch configuration) of
+the 512^3 workload at half its cells.  FUSED = 1 smooths the finest level with fused red-black
+sweeps (mg_opts.fused_sweeps).
 """
 import sys
 
@@ -20,12 +23,13 @@ def main(argv):
     prec = argv[3] if len(argv) > 3 else "mixed"
     inner = int(argv[4]) if len(argv) > 4 else 1
     cycles = int(argv[5]) if len(argv) > 5 else 2
+    fused = len(argv) > 6 and argv[6] == "1"
     dev = torch.device("cuda")
     g = torch.Generator(device="cuda")
     rho = 1.2 + 996.8 * torch.rand((nz, ny, nx), generator=g.manual_seed(3), device=dev, dtype=torch.float64)
     b = torch.randn((nz, ny, nx), generator=g.manual_seed(4), device=dev, dtype=torch.float64)
     s = Solver((nx, ny, nz), h=1.0 / max(nx, ny, nz), precision=prec, coarsest=8, rtol=1e-30,
-               max_cycles=cycles, inner_cycles=inner if prec != "fp64" else 1)
+               max_cycles=cycles, inner_cycles=inner if prec != "fp64" else 1, fused_sweeps=fused)
     s.set_density(rho)
     p = s.solve(b, raise_on_nonconvergence=False)
     try:

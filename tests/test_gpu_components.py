@@ -182,11 +182,14 @@ def test_coarse_solve_matches_oracle(dims, dtype):
     assert rel(host(e), want) < (1e-11 if dtype == torch.float64 else 1e-6)
 
 
-def test_single_level_grid_is_a_dense_solve():
-    dims = (8, 6, 4)
-    s, M = make(dims, "fp64", coarsest=8)
+@pytest.mark.parametrize("dims", [(8, 6, 4), (7, 5, 3), (9, 9, 9), (31, 1, 1)])
+def test_single_level_grid_is_a_dense_solve(dims):
+    """The dense coarse pseudo-inverse (blocked Gauss-Jordan, 32 pivots per step) on grids of
+    192, 105, 729 and 31 cells: whole blocks, a ragged last block, a single short block."""
+    s, M = make(dims, "fp64", coarsest=max(dims))
     assert s.num_levels == 1 and M.nlevels == 1
-    b = rnd((4, 6, 8), 70)
+    nx, ny, nz = dims
+    b = rnd((nz, ny, nx), 70)
     p = s.solve(dev(b))
     assert s.last_stats.cycles == 1
     want, _, _ = M.solve_exact(b)
