@@ -171,7 +171,7 @@ struct Geo {
 // Copies of plane q for the tile (k0, y0) into stage `st` (floats), by one warp; returns
 // nothing, arrives on the stage's mbarrier with the exact byte count first.
 __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0, int c1, bool from_zero,
-                                            const float *X, const float *sv, const float *b, float *stg,
+                                            const float *X, const float *sv, float *stg,
                                             unsigned bar, int lane) {
     const int c2 = 1 - c1;
     const int ks = k0 - 4 < 0 ? 0 : k0 - 4, ke = k0 + TX + 4 > g.hx ? g.hx : k0 + TX + 4;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (abort_flag) return;
     if (warp == kProducerWarp)
         for (int q = qlo; q <= min(qlo + kAhead + 1, qhi); ++q)
-            issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, b, stages + (size_t)stage_of(q) * STAGE, bar_of(q), lane);
+            issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, stages + (size_t)stage_of(q) * STAGE, bar_of(q), lane);
     int issued = min(qlo + kAhead + 1, qhi);  // newest plane issued
     // planes z0-2 and z0-1 are used from the first step on
     bool ok = mbar_wait(bar_of(qlo), parity_of(qlo)) && mbar_wait(bar_of(qlo + 1), parity_of(qlo + 1));
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         if (issued + 1 <= qhi) {
             const int q = issued + 1;
             if (warp == kProducerWarp)
-                issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, b, stages + (size_t)stage_of(q) * STAGE, bar_of(q),
+                issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, stages + (size_t)stage_of(q) * STAGE, bar_of(q),
                             lane);
             issued = q;
         }

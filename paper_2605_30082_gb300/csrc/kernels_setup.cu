@@ -272,13 +272,17 @@ constexpr int GJ_BS = 32;
 // row-major) written to global scratch.  One block of GJ_BS x GJ_BS threads.
 __global__ void k_gj_pivot_inv(int n, int kb, int bs, const double *__restrict__ M, double *Pinv) {
     __shared__ double P[GJ_BS][GJ_BS + 1];
+    __shared__ double rps;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (tx < bs && ty < bs) P[ty][tx] = M[(i64)(kb + ty) * n + kb + tx];
     __syncthreads();
     for (int k = 0; k < bs; ++k) {
+        // one FP64 division per pivot (by one thread), not one per thread
+        if (tx == 0 && ty == 0) rps = 1.0 / P[k][k];
+        __syncthreads();
         double v = 0.0;
         if (tx < bs && ty < bs) {
-            const double rp = 1.0 / P[k][k];
+            const double rp = rps;
             if (ty == k && tx == k) v = rp;
             else if (ty == k) v = P[k][tx] * rp;
             else if (tx == k) v = -P[ty][k] * rp;
