@@ -461,13 +461,16 @@ __global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const flo
     i64 own = (i64)col * L.half + row0;
     const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
     auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
+    // b is read once per sweep: an evict-first load leaves L2 to the other colour's rows y +- 1,
+    // which the neighbouring rows' blocks read again
+    auto ld_once = [](const float *A, i64 off) { return __ldcs(reinterpret_cast<const float4 *>(A + off)); };
     auto load_plane = [&](i64 o, i64 w, PlaneLoads &P) {
         P.ym = hy0 ? ld(xv, o - dy) : f0;
         P.yp = hy1 ? ld(xv, o + dy) : f0;
         P.s2 = hy0 ? ld(sv, o - dy) : f0;
         P.s3 = hy1 ? ld(sv, o + dy) : f0;
         P.sc = ld(sv, w);
-        P.bb = ld(b, w);
+        P.bb = ld_once(b, w);
         P.xl = P.sl = P.xr = P.sr = 0.f;
         if (lane == 0 && kl) {
             P.xl = xv[o - 1];
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const flo
             const float den = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
             out[v] = __fdividef(hh * bv[v] + num, den);
         }
-        if (active) *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+        if (active) __stcs(reinterpret_cast<float4 *>(xv + own), make_float4(out[0], out[1], out[2], out[3]));  // streaming store
         xzm = xzc;
         xzc = xzp;
         xzp = xzpp;

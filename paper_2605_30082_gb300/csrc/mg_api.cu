@@ -67,6 +67,11 @@ struct mg_handle {
     int have_op;
     int sform0;        // level-0 FP32 kernels use s = 1/rho (operator set from a density)
     cudaEvent_t ev0, ev1;
+    // the V-cycle below the finest level, recorded once at mg_create as a CUDA graph (its
+    // launches use fixed buffers and parameters) and replayed by every cycle; null: launched
+    // kernel by kernel
+    cudaGraphExec_t tail_exec;
+    long long tail_launches;
     // optional per-class timing of level-0 kernels (events recorded around launches)
     int prof_on;
     cudaEvent_t *pev;
@@ -149,6 +154,17 @@ void prof_collect(mg_handle *h) {
     h->pev_used = 0;
 }
 
+// ---- the V-cycle below the finest level as a CUDA graph ------------------------------
+// Levels 1 .. coarsest run many short launches (about 60 per cycle at 512^3, most of a few
+// microseconds); replaying them as one graph removes the per-launch host cost and most of the
+// gaps between them.  The graph is recorded once in mg_create (build_tail_graph) from the
+// same functions the cycle calls, so a replay launches the same kernels with the same
+// arguments in the same order.
+void replay_tail(mg_handle *h) {
+    if (cudaGraphLaunch(h->tail_exec, h->s) == cudaSuccess) mg::count_launch((int)h->tail_launches);
+    // a failed launch leaves its error for the solve's check_launch
+}
+
 // ---- FP64 V-cycle: in-place per-colour half sweeps, standalone transfers --------------
 // (FP64 arithmetic, not bytes, bounds these kernels on GB300, so they do no
 // redundant work; see the fused FP32 passes below for the bandwidth-bound cycle)
@@ -193,7 +209,8 @@ void vcycle64(mg_handle *h, int l, const double *b, double *x, bool x_zero) {
     Level &L = h->lv[l], &C = h->lv[l + 1];
     if (x_zero) cudaMemsetAsync(x, 0, sizeof(double) * (size_t)L.d.n, h->s);
     presmooth_restrict64(h, l, b, x, C.b64, h->o.pre);
-    vcycle64(h, l + 1, C.b64, C.x64, true);
+    if (l == 0 && h->tail_exec) replay_tail(h);
+    else vcycle64(h, l + 1, C.b64, C.x64, true);
     prolong_postsmooth64(h, l, b, C.x64, x, h->o.post);
 }
 
@@ -304,8 +321,41 @@ void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *
     }
     Level &C = h->lv[l + 1];
     presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, from_zero);
-    vcycle32(h, l + 1, C.b32, C.x32);
+    if (l == 0 && h->tail_exec) replay_tail(h);
+    else vcycle32(h, l + 1, C.b32, C.x32);
     prolong_postsmooth32(h, l, b, C.x32, x, h->o.post, up);
+}
+
+// Record levels 1 .. coarsest of one V-cycle (FP64 or FP32, as the handle's cycle) on a private
+// stream under capture; nothing runs.  Without a graph (capture or instantiation refused) the
+// cycle launches the kernels itself.
+void build_tail_graph(mg_handle *h) {
+    h->tail_exec = nullptr;
+    h->tail_launches = 0;
+    if (h->nlev < 2) return;
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaStream_t saved = h->s;
+    h->s = cap;
+    const unsigned long long l0 = mg::launches_total();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        if (h->o.precision == MG_FP64) vcycle64(h, 1, h->lv[1].b64, h->lv[1].x64, true);
+        else vcycle32(h, 1, h->lv[1].b32, h->lv[1].x32);
+        ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && g != nullptr;
+    }
+    const long long n = (long long)(mg::launches_total() - l0);
+    mg::count_launch((int)-n);  // recorded, not run
+    h->s = saved;
+    if (ok && cudaGraphInstantiate(&h->tail_exec, g, 0) != cudaSuccess) h->tail_exec = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    cudaGetLastError();
+    h->tail_launches = h->tail_exec ? n : 0;
 }
 
 // ---- set-up of the operator hierarchy -------------------------------------------------
@@ -745,6 +795,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         mg_destroy(h);
         return MG_ERR_CUDA;
     }
+    build_tail_graph(h);
     h->msg[0] = 0;
     *out = h;
     return MG_OK;
@@ -753,6 +804,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
 int mg_destroy(mg_handle *h) {
     if (!h) return MG_OK;
     cudaStreamSynchronize(h->s);
+    if (h->tail_exec) cudaGraphExecDestroy(h->tail_exec);
     if (h->pev) {
         for (int q = 0; q < kProfEvents; ++q) cudaEventDestroy(h->pev[q]);
         delete[] h->pev;
