@@ -37,11 +37,11 @@ __device__ __forceinline__ double scale_pow2(double v, int m, double s) {
 // is written exactly once.  FP64 arithmetic: the corrected velocity must keep the divergence
 // of the solve's residual, far below FP32 rounding.  Out of place (o* may be u*): with
 // COPY_WALLS the threads of the boundary cells also copy the wall faces from u to o.
-// A thread takes kBatch cells of its row at a time and loads all their inputs before the
+// A thread takes kBatch (2) cells of its row at a time and loads all their inputs before the
 // first store: the output may be the input (in place), so the compiler may not move a later
 // cell's loads above an earlier cell's stores, and cell-by-cell the loads of each cell would
 // wait a full memory latency.
-constexpr int kBatch = 4;
+constexpr int kBatch = 2;
 
 template <bool CSF, bool COPY_WALLS, bool POW2>
 __global__ void k_project(Dims d, double ih, int log2ih, double sigma, const double *__restrict__ p,
