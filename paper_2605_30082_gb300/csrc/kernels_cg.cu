@@ -303,7 +303,9 @@ inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThre
 void launch_cg_apply32(cudaStream_t s, Lay L, double ih2, const float *sinv, const float *fx, const float *fy,
                        const float *fz, const float *d, float *q, double *partials, double *sc) {
     const Coef32c cf{sinv, fx, fy, fz};
-    const int nb = reduce_blocks(L.n / 4);
+    static const int wave_s = wave_blocks((const void *)k_cg_apply32<true>, kThreads);
+    static const int wave_n = wave_blocks((const void *)k_cg_apply32<false>, kThreads);
+    const int nb = fill_blocks(reduce_blocks(L.n / 4), sinv ? wave_s : wave_n);
     count_launch(2);
     if (sinv) k_cg_apply32<true><<<nb, kThreads, 0, s>>>(L, (float)ih2, cf, d, q, partials);
     else k_cg_apply32<false><<<nb, kThreads, 0, s>>>(L, (float)ih2, cf, d, q, partials);
@@ -312,7 +314,8 @@ void launch_cg_apply32(cudaStream_t s, Lay L, double ih2, const float *sinv, con
 
 void launch_cg_dots32(cudaStream_t s, i64 n, const float *r, const float *z, const float *q, double *partials,
                       double *sc, int rz_slot) {
-    const int nb = reduce_blocks(n / 4);
+    static const int wave = wave_blocks((const void *)k_cg_dots32, kThreads);
+    const int nb = fill_blocks(reduce_blocks(n / 4), wave);
     count_launch(2);
     k_cg_dots32<<<nb, kThreads, 0, s>>>(n / 4, reinterpret_cast<const float4 *>(r),
                                         reinterpret_cast<const float4 *>(z), reinterpret_cast<const float4 *>(q),
@@ -338,7 +341,8 @@ void launch_cg_update32(cudaStream_t s, i64 n, float *x, float *r, const float *
 void launch_cg_apply64(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy, const double *fz,
                        const double *dg, const double *dv, double *q, double *partials, double *sc) {
     const i64 rows = (i64)d.ny * d.nz;
-    int nb = reduce_blocks(d.n);
+    static const int wave = wave_blocks((const void *)k_cg_apply64, kThreads);
+    int nb = fill_blocks(reduce_blocks(d.n), wave);
     if (nb > rows) nb = (int)rows;
     count_launch(2);
     k_cg_apply64<<<nb, kThreads, 0, s>>>(d, ih2, fx, fy, fz, dg, dv, q, partials);
@@ -360,7 +364,8 @@ void launch_cg_dir64(cudaStream_t s, i64 n, const double *z, double *d, const do
 
 void launch_cg_update64(cudaStream_t s, i64 n, double *x, double *r, const double *d, const double *q, double *sc,
                         int rz_cur, double *partials) {
-    const int nb = reduce_blocks(n);
+    static const int wave = wave_blocks((const void *)k_cg_update64, kThreads);
+    const int nb = fill_blocks(reduce_blocks(n), wave);
     count_launch(2);
     k_cg_update64<<<nb, kThreads, 0, s>>>(n, x, r, d, q, sc, rz_cur, partials);
     k_cg_final<<<1, 256, 0, s>>>(partials, nb, sc, CG_RR, CG_SX);

@@ -384,7 +384,8 @@ void launch_join(cudaStream_t s, i64 n, const float2 *src, double *dst) {
 void launch_resid_df(cudaStream_t s, Dims d, Lay L, const float2 *fx, const float2 *fy, const float2 *fz,
                      const float2 *diag, const float2 *b, const float2 *p, float *r32, float s32,
                      double *partials, double *out) {
-    const int nb = reduce_blocks(d.n / 2);
+    static const int wave = wave_blocks((const void *)k_resid_df, kReduceThreads);
+    const int nb = fill_blocks(reduce_blocks(d.n / 2), wave);
     count_launch();
     k_resid_df<<<nb, kReduceThreads, 0, s>>>(d, L, fx, fy, fz, diag, b, p, r32, s32, partials);
     count_launch();

@@ -3,9 +3,12 @@
 // scaled FP32 copy that feeds the inner V-cycle), the solution update, and the
 // fused adjoint gradient kernel.
 //
-// Every reduction runs on a grid whose size depends only on n; each block
-// writes one partial (warp shuffles in a fixed pattern), and one block sums
-// the partials in index order, so results are bitwise reproducible.
+// Every reduction runs on a grid whose size depends only on n and the device
+// model (one wave of resident blocks at most); each block writes one partial
+// (warp shuffles in a fixed pattern), and one block sums the partials in index
+// order, so results are bitwise reproducible for the same inputs and device.
+#include <cmath>
+
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -20,6 +23,24 @@ int reduce_blocks(i64 n) {
     i64 b = (n + kReduceThreads - 1) / kReduceThreads;
     const i64 cap = 152 * 8;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+int wave_blocks(const void *kernel, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        sms < 1 || per_sm < 1) {
+        (void)cudaGetLastError();  // the query failed before any launch: keep the full count
+        return 1 << 30;
+    }
+    return sms * per_sm;
+}
+
+int fill_blocks(int nb, int wave) {
+    // a grid-stride loop over nb > wave blocks runs as one full wave and a partly filled one;
+    // with exactly one wave every block does the same share of the work
+    return nb > wave ? wave : nb;
 }
 
 namespace {
@@ -67,24 +88,113 @@ __global__ void k_final(const double *__restrict__ partials, int nb, double *out
     block_sum2(a, b, out);
 }
 
-template <typename T>
+template <typename T> struct Vec16;
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static void get(const double2 &u, double (&v)[4]) { v[0] = u.x; v[1] = u.y; v[2] = v[3] = 0.0; }
+};
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static void get(const float4 &u, double (&v)[4]) { v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; }
+};
+
+inline __device__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// sums of x and, with SQ, of x^2.  A single 8-byte load in flight per thread leaves HBM at
+// about a third of its bandwidth, so a 16-byte-aligned x is read as two 16-byte loads per
+// thread and iteration; the elements past the last whole vector (and an unaligned x) take the
+// scalar loop.  GB300 issues FP64 additions at a small fraction of its FP32 rate, so the
+// gauge sums, which need no squares, take one FP64 addition per element instead of two.
+template <typename T, bool SQ>
 __global__ void k_sum_sumsq(i64 n, const T *__restrict__ x, double *partials) {
+    using V = Vec16<T>;
     double a = 0.0, b = 0.0;
-    for (i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (i64)gridDim.x * blockDim.x) {
+    const i64 tid = (i64)blockIdx.x * blockDim.x + threadIdx.x, nt = (i64)gridDim.x * blockDim.x;
+    i64 m0 = 0;
+    if (aligned16(x)) {
+        const typename V::type *xv = reinterpret_cast<const typename V::type *>(x);
+        const i64 nv = n / V::n;
+        for (i64 m = tid; m < nv; m += 2 * nt) {
+            const typename V::type u0 = xv[m];
+            const bool two = m + nt < nv;
+            typename V::type u1 = u0;
+            if (two) u1 = xv[m + nt];
+            double v[4];
+            V::get(u0, v);
+#pragma unroll
+            for (int q = 0; q < V::n; ++q) {
+                a += v[q];
+                if (SQ) b += v[q] * v[q];
+            }
+            if (two) {
+                V::get(u1, v);
+#pragma unroll
+                for (int q = 0; q < V::n; ++q) {
+                    a += v[q];
+                    if (SQ) b += v[q] * v[q];
+                }
+            }
+        }
+        m0 = nv * V::n;
+    }
+    for (i64 m = m0 + tid; m < n; m += nt) {
         double v = (double)x[m];
         a += v;
-        b += v * v;
+        if (SQ) b += v * v;
     }
     block_sum2(a, b, partials + 2 * blockIdx.x);
 }
 
-// b64 = (b - mean(b)) * scale; partials: sum of b64^2
+// v * 2^m by an integer addition to the IEEE-754 exponent field (binary64: 11 exponent bits
+// from bit 52) when v is normal and stays normal, exact like the multiplication; otherwise
+// (zero, subnormal, a result leaving the normal range, infinity, NaN) v * s, in a function of
+// its own so that the compiler keeps it off the common path.
+__device__ __noinline__ double mul_slow(double v, double s) { return v * s; }
+__device__ __forceinline__ double mul_pow2(double v, int m, double s) {
+    const long long bits = __double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e >= 1 && e <= 2046 && e + m >= 1 && e + m <= 2046) return __longlong_as_double(bits + ((long long)m << 52));
+    return mul_slow(v, s);
+}
+
+// b64 = (b - mean(b)) * scale; partials: sum of b64^2.  16-byte loads and stores, two per
+// thread and iteration, where b and b64 are 16-byte aligned (as k_sum_sumsq).  With POW2
+// (scale = 2^m: 1 in the FP64 mode, h^2 in the mixed modes when h is a power of two) the
+// scaling is an exponent addition: two FP64 operations per element instead of three.
+template <bool POW2>
 __global__ void k_sub_mean(i64 n, const double *__restrict__ b, const double *__restrict__ sum,
-                           double scale, double *b64, double *partials) {
-    double mean = sum[0] / (double)n;
+                           double scale, int m2, double *b64, double *partials) {
+    const double mean = sum[0] / (double)n;
     double q = 0.0;
-    for (i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (i64)gridDim.x * blockDim.x) {
-        double v = (b[m] - mean) * scale;
+    auto f = [&](double u) { return POW2 ? mul_pow2(u - mean, m2, scale) : (u - mean) * scale; };
+    const i64 tid = (i64)blockIdx.x * blockDim.x + threadIdx.x, nt = (i64)gridDim.x * blockDim.x;
+    i64 m0 = 0;
+    if (aligned16(b) && aligned16(b64)) {
+        const double2 *bv = reinterpret_cast<const double2 *>(b);
+        double2 *ov = reinterpret_cast<double2 *>(b64);
+        const i64 nv = n / 2;
+        for (i64 m = tid; m < nv; m += 2 * nt) {
+            const double2 u0 = bv[m];
+            const bool two = m + nt < nv;
+            double2 u1 = u0;
+            if (two) u1 = bv[m + nt];
+            const double2 w0 = make_double2(f(u0.x), f(u0.y));
+            ov[m] = w0;
+            q += w0.x * w0.x;
+            q += w0.y * w0.y;
+            if (two) {
+                const double2 w1 = make_double2(f(u1.x), f(u1.y));
+                ov[m + nt] = w1;
+                q += w1.x * w1.x;
+                q += w1.y * w1.y;
+            }
+        }
+        m0 = nv * 2;
+    }
+    for (i64 m = m0 + tid; m < n; m += nt) {
+        const double v = f(b[m]);
         b64[m] = v;
         q += v * v;
     }
@@ -241,7 +351,8 @@ __global__ void k_add_const(i64 n, double *p, double c) {
 }
 
 // dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R) ih2 + sigma csf_f (lam_L - lam_R) ih on the low
-// faces of each cell (walls 0); partial sums of beta_f csf_f (lam_L - lam_R) ih (= dL/dsigma).
+// faces of each cell (walls 0); partial sums of beta_f csf_f (lam_L - lam_R) ih (= dL/dsigma,
+// one FP64 multiplication and one FMA per face, the factor ih applied once per block).
 // Blocks take whole rows (no 64-bit division per cell).  The differences of lambda and p are
 // formed in FP64 (they cancel); their product, an FP32 output, is formed in FP32 from the
 // differences rounded to nearest.  dL/dsigma is summed in FP64.
@@ -271,7 +382,7 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
                 g0 = -dlf * d2f_rn(p[c - 1] - pc) * ih2;
                 if (csx) {
                     g0 = fmaf(sigma * d2f_rn(csx[ax0 + i]) * ih, dlf, g0);
-                    ds += fx[c] * csx[ax0 + i] * dl * ihd;
+                    ds = fma(fx[c] * csx[ax0 + i], dl, ds);
                 }
             }
             if (j > 0) {
@@ -280,7 +391,7 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
                 g1 = -dlf * d2f_rn(p[c - nx] - pc) * ih2;
                 if (csy) {
                     g1 = fmaf(sigma * d2f_rn(csy[ay0 + i]) * ih, dlf, g1);
-                    ds += fy[c] * csy[ay0 + i] * dl * ihd;
+                    ds = fma(fy[c] * csy[ay0 + i], dl, ds);
                 }
             }
             if (k > 0) {
@@ -289,7 +400,7 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
                 g2 = -dlf * d2f_rn(p[c - nxy] - pc) * ih2;
                 if (csz) {
                     g2 = fmaf(sigma * d2f_rn(csz[c]) * ih, dlf, g2);
-                    ds += fz[c] * csz[c] * dl * ihd;
+                    ds = fma(fz[c] * csz[c], dl, ds);
                 }
             }
             if (gx) {
@@ -302,27 +413,35 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
             }
         }
     }
-    block_sum2(ds, 0.0, partials + 2 * blockIdx.x);
+    block_sum2(ds * ihd, 0.0, partials + 2 * blockIdx.x);
 }
 
 }  // namespace
 
 template <typename T>
-void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out) {
-    int nb = reduce_blocks(n);
+void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out, bool squares) {
+    static const int wave_q = wave_blocks((const void *)k_sum_sumsq<T, true>, kReduceThreads);
+    static const int wave_s = wave_blocks((const void *)k_sum_sumsq<T, false>, kReduceThreads);
+    const int nb = fill_blocks(reduce_blocks(n), squares ? wave_q : wave_s);
     count_launch();
-    k_sum_sumsq<T><<<nb, kReduceThreads, 0, s>>>(n, x, partials);
+    if (squares) k_sum_sumsq<T, true><<<nb, kReduceThreads, 0, s>>>(n, x, partials);
+    else k_sum_sumsq<T, false><<<nb, kReduceThreads, 0, s>>>(n, x, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
-template void launch_sum_sumsq<double>(cudaStream_t, i64, const double *, double *, double *);
-template void launch_sum_sumsq<float>(cudaStream_t, i64, const float *, double *, double *);
+template void launch_sum_sumsq<double>(cudaStream_t, i64, const double *, double *, double *, bool);
+template void launch_sum_sumsq<float>(cudaStream_t, i64, const float *, double *, double *, bool);
 
 void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double scale, double *b64,
                      double *partials, double *out) {
-    int nb = reduce_blocks(n);
+    static const int wave_p = wave_blocks((const void *)k_sub_mean<true>, kReduceThreads);
+    static const int wave_m = wave_blocks((const void *)k_sub_mean<false>, kReduceThreads);
+    int e = 0;
+    const bool pow2 = std::frexp(scale, &e) == 0.5;  // scale = 2^(e - 1)
+    const int nb = fill_blocks(reduce_blocks(n), pow2 ? wave_p : wave_m);
     count_launch();
-    k_sub_mean<<<nb, kReduceThreads, 0, s>>>(n, b, sum, scale, b64, partials);
+    if (pow2) k_sub_mean<true><<<nb, kReduceThreads, 0, s>>>(n, b, sum, scale, e - 1, b64, partials);
+    else k_sub_mean<false><<<nb, kReduceThreads, 0, s>>>(n, b, sum, scale, 0, b64, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }
@@ -330,7 +449,8 @@ void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, 
 void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const double *fx, const double *fy,
                           const double *fz, const double *b, const double *p, float *r32,
                           double scale, double *partials, double *out) {
-    int nb = reduce_blocks(d.n);
+    static const int wave = wave_blocks((const void *)k_fine_residual, kReduceThreads);
+    const int nb = fill_blocks(reduce_blocks(d.n), wave);
     count_launch();
     k_fine_residual<<<nb, kReduceThreads, 0, s>>>(d, L, ih2, fx, fy, fz, b, p, r32, scale, partials);
     count_launch();
@@ -341,7 +461,9 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
                         const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
                         float *r32, float s32, double *partials, double *out) {
     if (d.nx & 1) {
-        int nb = reduce_blocks(d.n);
+        static const int wave_ct = wave_blocks((const void *)k_fine_resid_cell<true>, kReduceThreads);
+        static const int wave_cf = wave_blocks((const void *)k_fine_resid_cell<false>, kReduceThreads);
+        const int nb = fill_blocks(reduce_blocks(d.n), b_scaled ? wave_ct : wave_cf);
         count_launch();
         if (b_scaled) k_fine_resid_cell<true><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
         else k_fine_resid_cell<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
@@ -349,7 +471,9 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
         k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
         return;
     }
-    int nb = reduce_blocks(d.n / 2);
+    static const int wave_pt = wave_blocks((const void *)k_fine_resid_pair<true>, kReduceThreads);
+    static const int wave_pf = wave_blocks((const void *)k_fine_resid_pair<false>, kReduceThreads);
+    const int nb = fill_blocks(reduce_blocks(d.n / 2), b_scaled ? wave_pt : wave_pf);
     count_launch();
     if (b_scaled) k_fine_resid_pair<true><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
     else k_fine_resid_pair<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
@@ -371,7 +495,8 @@ void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, co
                          const double *fx, const double *fy, const double *fz, const double *csfx,
                          const double *csfy, const double *csfz, double sigma, float *gx,
                          float *gy, float *gz, double *partials, double *out) {
-    int nb = reduce_blocks(d.n);
+    static const int wave = wave_blocks((const void *)k_adjoint_grad, kReduceThreads);
+    int nb = fill_blocks(reduce_blocks(d.n), wave);
     count_launch();
     const i64 rows = (i64)d.ny * d.nz;
     if (nb > rows) nb = (int)rows;

@@ -458,7 +458,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     const bool mixed = h->o.precision != MG_FP64;
     const bool df = h->o.precision == MG_MIXED_DF;
     const double bscale = mixed ? F.h2 : 1.0;
-    mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red);
+    mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red, false);
     mg::launch_sub_mean(s, n, b, h->red, bscale, h->bt, h->partials, h->red + 2);
     MG_CUDA(h, cudaMemcpyAsync(h->hred, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     MG_CUDA(h, cudaStreamSynchronize(s));
@@ -480,7 +480,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         hist[hist_n++] = 0.0;
     } else {
         if (warm) {
-            mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 4);
+            mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 4, false);
             MG_CUDA(h, cudaMemcpyAsync(h->hred + 4, h->red + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
             MG_CUDA(h, cudaStreamSynchronize(s));
             mg::launch_add_const(s, n, p, -h->hred[4] / (double)n);
@@ -597,7 +597,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         }
         if (df) mg::launch_join(s, n, h->p2, p);
         // exact zero-mean gauge at exit (the per-iteration shifts use an FP32 sum)
-        mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 12);
+        mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 12, false);
         MG_CUDA(h, cudaMemcpyAsync(h->hred + 12, h->red + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
         MG_CUDA(h, cudaStreamSynchronize(s));
         mg::launch_add_const(s, n, p, -h->hred[12] / (double)n);
@@ -1067,14 +1067,14 @@ int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b
     Level &L = h->lv[level];
     if (dtype == MG_F64) {
         mg::launch_residual<double>(h->s, L.d, L.ih2, coef<double>(L), (const double *)b, (const double *)x, (double *)r);
-        if (norm2) mg::launch_sum_sumsq<double>(h->s, L.d.n, (const double *)r, h->partials, h->red + 10);
+        if (norm2) mg::launch_sum_sumsq<double>(h->s, L.d.n, (const double *)r, h->partials, h->red + 10, true);
     } else {
         mg::launch_pack32(h->s, L.lay, (const float *)x, L.s1_32);
         mg::launch_pack32(h->s, L.lay, (const float *)b, L.s2_32);
         mg::launch_residual32(h->s, L.lay, L.ih2, sinv32(h, level), L.fx32, L.fy32, L.fz32, L.s2_32, L.s1_32,
                               L.x32, false);
         mg::launch_unpack32(h->s, L.lay, L.x32, (float *)r);
-        if (norm2) mg::launch_sum_sumsq<float>(h->s, L.d.n, (const float *)r, h->partials, h->red + 10);
+        if (norm2) mg::launch_sum_sumsq<float>(h->s, L.d.n, (const float *)r, h->partials, h->red + 10, true);
     }
     rc = check_launch(h, "mg_residual");
     if (rc) return rc;

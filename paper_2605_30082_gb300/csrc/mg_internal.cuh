@@ -128,6 +128,12 @@ void count_launch(int k = 1);
 // number of blocks used by every deterministic reduction over n elements
 int reduce_blocks(i64 n);
 constexpr int kReduceThreads = 256;
+// blocks of one full wave of `kernel` at `threads` threads per block on the current device
+// (resident blocks per SM x SMs; 2^30 if the query fails).  Launchers cache it in a function-
+// local static: every device a process uses is of the same model.
+int wave_blocks(const void *kernel, int threads);
+// min(nb, wave): the grid of a grid-stride reduction that needs nb <= reduce_blocks(n) blocks
+int fill_blocks(int nb, int wave);
 
 // ---- setup kernels (FP64) -------------------------------------------------------
 void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
@@ -252,8 +258,9 @@ void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r
 
 // ---- reductions, fine-level FP64 passes, adjoint -----------------------------------
 // partials: reduce_blocks(n) x 2 doubles; out: 2 doubles (deterministic order)
+// out[0] = sum x, out[1] = sum x^2 (0 unless `squares`)
 template <typename T>
-void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out);
+void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out, bool squares);
 // b64 = (b - sum[0]/n) * scale, with the sum of squares of b64 into out[0]
 void launch_sub_mean(cudaStream_t s, i64 n, const double *b, const double *sum, double scale, double *b64,
                      double *partials, double *out);

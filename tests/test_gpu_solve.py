@@ -189,6 +189,35 @@ def test_solve_is_deterministic(c32):
     assert torch.equal(p1, p2)
 
 
+def _off16(a):
+    """A copy of `a` whose data pointer sits 8 bytes past a 16-byte boundary."""
+    buf = torch.empty(a.numel() + 2, dtype=a.dtype, device=a.device)
+    k = 1 if buf.data_ptr() % 16 == 0 else 0
+    v = buf[k:k + a.numel()].view(a.shape)
+    v.copy_(a)
+    assert v.data_ptr() % 16 == 8
+    return v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
+def test_unaligned_rhs_32cubed(c32, prec):
+    """The reductions over b read 16-byte vectors where the pointer allows it and single
+    elements otherwise (b may have any alignment; p must be 16-byte aligned): an RHS 8 bytes
+    off alignment gives the solve of the aligned one."""
+    s = Solver((32, 32, 32), h=c32["h"], precision=prec, coarsest=8)
+    s.set_density(dev(c32["rho"]))
+    b = dev(c32["b"])
+    p_al = s.solve(b).clone()
+    p_un = s.solve(_off16(b))
+    assert s.last_stats.relres <= 1e-10
+    assert rel(host(p_un), host(p_al)) < 1e-12
+    assert rel(host(p_un), c32["exact8"]) < 1e-9
+    # an unaligned solution array is refused before any launch
+    with pytest.raises(MgError) as ei:
+        s.solve(b, p=_off16(torch.zeros_like(b)))
+    assert ei.value.code == MG_ERR_ARG
+
+
 def test_edge_cases():
     n = 16
     s = Solver((n, n, n), precision="mixed", coarsest=8)
