@@ -535,9 +535,17 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
     cs = torch.cuda.Stream()     # host -> device
     cs_out = torch.cuda.Stream()  # device -> host, concurrently (the link carries both directions)
 
+    copy_ms = {"h2d": [], "d2h": []}  # per step, on the copy streams (under the compute's load)
+
+    def timed(st):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(st)
+        return ev
+
     def pipeline(K):
         ev_in = [torch.cuda.Event(), torch.cuda.Event()]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        spans = []
         torch.cuda.synchronize()
         e0.record(cs)
         with torch.cuda.stream(cs):
@@ -545,28 +553,39 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
                 d_.copy_(h_, non_blocking=True)
         ev_in[0].record(cs)
         ev_prev = None
+        ev_read = [None, None]  # result buffers q read back to the host
         for k in range(K):
             q = k % 2
             if k + 1 < K:  # buffers 1 - q were last read by step k - 1
                 if ev_prev is not None:
                     cs.wait_event(ev_prev)
+                a = timed(cs)
                 with torch.cuda.stream(cs):
                     for d_, h_ in zip(din[1 - q], hin):
                         d_.copy_(h_, non_blocking=True)
+                spans.append(("h2d", a, timed(cs)))
                 ev_in[1 - q].record(cs)
             comp.wait_event(ev_in[q])
+            if ev_read[q] is not None:  # step k - 2's results left buffers q
+                comp.wait_event(ev_read[q])
             g = step(din[q][0], din[q][1], tuple(din[q][2:5]), din[q][5], p2[q], lam2[q], un2[q], dens2[q])
             ev_out = torch.cuda.Event()
             ev_out.record(comp)
             cs_out.wait_event(ev_out)
+            a = timed(cs_out)
             with torch.cuda.stream(cs_out):
                 for h_, d_ in zip(hout, (p2[q], lam2[q], *g, *un2[q], *dens2[q][1])):
                     h_.copy_(d_, non_blocking=True)
                 for t in g:
                     t.record_stream(cs_out)
+            spans.append(("d2h", a, timed(cs_out)))
+            ev_read[q] = torch.cuda.Event()
+            ev_read[q].record(cs_out)
             ev_prev = ev_out
         e1.record(cs_out)  # after the last step's results are read back (and so after every step)
         torch.cuda.synchronize()
+        for kind, a, b in spans:
+            copy_ms[kind].append(a.elapsed_time(b))
         return e0.elapsed_time(e1) / K
 
     def copy_rates():
@@ -591,13 +610,19 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
     # at least 10 steps: the first step's input copy and the last step's result copy cannot
     # overlap any compute, and their share falls with the number of steps
     ksteps = max(10, args.steps)
+    for v in copy_ms.values():
+        v.clear()
     ms = pipeline(ksteps)
     n3 = fd.numel()
+    # the first step's input copy runs alone, the last step's read-back too: the median is a
+    # copy that overlapped a step's kernels
+    under = {k: round(sorted(v)[len(v) // 2], 2) if v else None for k, v in copy_ms.items()}
     return {"value": round(n3 / (ms * 1e-3) / 1e9, 4), "unit": "Gcell/s", "ms_per_step": round(ms, 3),
             "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": ksteps,
             "copies": "host-to-device and device-to-host on two streams of their own, double-buffered; every "
                       "step's copies inside the timed region",
-            "copy_gbs_alone": {"h2d": rate_in, "d2h": rate_out}}
+            "copy_gbs_alone": {"h2d": rate_in, "d2h": rate_out},
+            "copy_ms_per_step_under_load": under}
 
 
 def _measured_peak_hbm():

@@ -125,7 +125,8 @@ __device__ __forceinline__ double recip64(double x) {
 // process-wide count of kernel launches (read through mg_kernel_launches)
 void count_launch(int k = 1);
 
-// number of blocks used by every deterministic reduction over n elements
+// the most blocks a deterministic reduction over n elements uses (its partials buffer holds
+// that many pairs); launchers take min(this, one wave of the kernel)
 int reduce_blocks(i64 n);
 constexpr int kReduceThreads = 256;
 // blocks of one full wave of `kernel` at `threads` threads per block on the current device
