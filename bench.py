@@ -356,9 +356,10 @@ def run_ours(args):
     gbs_sm = bytes_sm / (ms_sm * 1e-3) / 1e9
     roof_sm = {"bound": "hbm", "achieved": round(gbs_sm, 1), "peak": peak, "unit": "GB/s",
                "frac": round(gbs_sm / peak, 3),
-               "traffic": _traffic_from_profiles("k_half_zp", cells),
-               "kernel": "k_half_zp<16, 8> (finest-level FP32 red-black half sweep, z-marching, prefetching "
-                         "one plane ahead; the one from-zero sweep per outer iteration is k_half_z)",
+               "traffic": _traffic_from_profiles("k_half_zs", cells),
+               "kernel": "k_half_zs<16, 11> (finest-level FP32 red-black half sweep, z-marching, each plane's "
+                         "loads staged by cp.async two planes ahead; the one from-zero sweep per outer "
+                         "iteration is k_half_z)",
                "launch_ms": round(avg_sm, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     n_fr, ms_fr = prof["fine_residual"]
     avg_fr = ms_fr / max(n_fr, 1)

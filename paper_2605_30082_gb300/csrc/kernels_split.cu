@@ -431,20 +431,35 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
     }
 }
 
-// Prefetching form of k_half_z for the s-form regular sweep (the finest level's dominant
-// kernel).  At plane z a thread first issues the loads of plane z+1 (rows y +- 1 of the other
-// colour, its own s and b, the window scalars of its warp's edge lanes) and the other colour's
-// row y of plane z+2, then computes plane z from values loaded one plane earlier: two planes of
-// loads are in flight per thread instead of one.  The other colour is only read in a half
-// sweep, so loading it early reads the same values.  Arithmetic as k_half_z.
-struct PlaneLoads {
-    float4 ym, yp, s2, s3, sc, bb;
-    float xl, xr, sl, sr;  // window scalars, used by lanes 0 and 31 only
-};
+// Staged form of k_half_z for the s-form regular sweep (the finest level's dominant kernel).
+// The per-plane loads of a thread (the other colour's rows y -+ 1 and their s, its own s and
+// b: six 16-byte vectors) travel by cp.async into a ring of kZsStages planes in shared memory,
+// issued kZsStages - 1 planes ahead of the plane being computed.  In flight they hold no
+// registers (121 registers for one plane held in registers, 80 here), so 11 blocks fit per SM
+// instead of 8, each with two planes of loads under way.  Every thread reads back only its
+// own copies: cp.async.wait_group is its only wait (no barrier, no spin), and a slot is
+// refilled only after the arithmetic that used it.  The other colour's row y (planes z -+ 1
+// and the window) still rolls through registers, the next plane's window scalars of the
+// warp's edge lanes too.  Arithmetic as k_half_z: bitwise the same results.
+constexpr int kZsStages = 3;
+constexpr int kZsFields = 6;  // ym, yp, s2 (= s at y - 1), s3 (y + 1), own s, own b
+constexpr size_t kZsSmem = (size_t)kZsStages * kZsFields * 64 * sizeof(float4);
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 64 threads per block (64 vectors of one row, or 32 of two rows), ZC planes per block
 template <int ZC, int MINB>
-__global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const float *__restrict__ sv,
+__global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const float *__restrict__ sv,
                                                        const float *__restrict__ b, float *xv, int col) {
+    extern __shared__ float4 stg[];  // [kZsStages][kZsFields][64 threads]
+    constexpr int D = kZsStages;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int hx = L.hx, kv = hx >> 2;
     const int kvi = blockIdx.x * blockDim.x + threadIdx.x;
     const int yi = blockIdx.y * blockDim.y + threadIdx.y;
@@ -457,67 +472,90 @@ __global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const flo
     const bool hy0 = y > 0, hy1 = y < L.ny - 1;
     const bool kl = k0 > 0, kr = k0 + 4 < hx;
     const i64 row0 = ((i64)z0 * L.ny + y) * hx + k0;
-    i64 opp = (i64)(1 - col) * L.half + row0;
-    i64 own = (i64)col * L.half + row0;
+    const i64 opp0 = (i64)(1 - col) * L.half + row0;
+    const i64 own0 = (i64)col * L.half + row0;
     const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
     auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
-    // b is read once per sweep: an evict-first load leaves L2 to the other colour's rows y +- 1,
-    // which the neighbouring rows' blocks read again
-    auto ld_once = [](const float *A, i64 off) { return __ldcs(reinterpret_cast<const float4 *>(A + off)); };
-    auto load_plane = [&](i64 o, i64 w, PlaneLoads &P) {
-        P.ym = hy0 ? ld(xv, o - dy) : f0;
-        P.yp = hy1 ? ld(xv, o + dy) : f0;
-        P.s2 = hy0 ? ld(sv, o - dy) : f0;
-        P.s3 = hy1 ? ld(sv, o + dy) : f0;
-        P.sc = ld(sv, w);
-        P.bb = ld_once(b, w);
-        P.xl = P.sl = P.xr = P.sr = 0.f;
+    auto slot = [&](int st, int f) { return stg + (st * kZsFields + f) * 64 + tid; };
+    // plane z0 + t into stage t % D (rows outside the grid are not copied; their slots are
+    // never read)
+    auto issue = [&](int t) {
+        const i64 o = opp0 + (i64)t * dz, w = own0 + (i64)t * dz;
+        const int st = t % D;
+        if (hy0) {
+            cp_async16(slot(st, 0), xv + o - dy);
+            cp_async16(slot(st, 2), sv + o - dy);
+        }
+        if (hy1) {
+            cp_async16(slot(st, 1), xv + o + dy);
+            cp_async16(slot(st, 3), sv + o + dy);
+        }
+        cp_async16(slot(st, 4), sv + w);
+        cp_async16(slot(st, 5), b + w);
+    };
+    // the window scalars beyond the warp's edge lanes (lane 0: x - 1, lane 31: x + 4)
+    auto scalars = [&](i64 o, float &xl, float &sl, float &xr, float &sr) {
+        xl = sl = xr = sr = 0.f;
         if (lane == 0 && kl) {
-            P.xl = xv[o - 1];
-            P.sl = sv[o - 1];
+            xl = xv[o - 1];
+            sl = sv[o - 1];
         }
         if (lane == 31 && kr) {
-            P.xr = xv[o + 4];
-            P.sr = sv[o + 4];
+            xr = xv[o + 4];
+            sr = sv[o + 4];
         }
     };
     // other colour, row y: planes z-1, z, z+1 (rolling)
-    float4 xzm = z0 > 0 ? ld(xv, opp - dz) : f0, xzc = ld(xv, opp);
-    float4 szm = z0 > 0 ? ld(sv, opp - dz) : f0, szc = ld(sv, opp);
-    float4 xzp = z0 + 1 < L.nz ? ld(xv, opp + dz) : f0, szp = z0 + 1 < L.nz ? ld(sv, opp + dz) : f0;
-    PlaneLoads cur, nxt;
-    load_plane(opp, own, cur);
+    float4 xzm = z0 > 0 ? ld(xv, opp0 - dz) : f0, xzc = ld(xv, opp0);
+    float4 szm = z0 > 0 ? ld(sv, opp0 - dz) : f0, szc = ld(sv, opp0);
+    float4 xzp = z0 + 1 < L.nz ? ld(xv, opp0 + dz) : f0, szp = z0 + 1 < L.nz ? ld(sv, opp0 + dz) : f0;
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t) {
+        if (z0 + t < z1) issue(t);
+        cp_async_commit();  // one group per plane, empty past the chunk: the counting stays uniform
+    }
+    float cxl, csl, cxr, csr;
+    scalars(opp0, cxl, csl, cxr, csr);
     const float hh = 2.f * h2;
     for (int z = z0; z < z1; ++z) {
-        // loads for the next plane first
+        const int t = z - z0;
+        if (z + D - 1 < z1) issue(t + D - 1);
+        cp_async_commit();
+        const i64 opp = opp0 + (i64)t * dz, own = own0 + (i64)t * dz;
+        float nxl = 0.f, nsl = 0.f, nxr = 0.f, nsr = 0.f;
         float4 xzpp = f0, szpp = f0;
         if (z + 1 < z1) {
-            load_plane(opp + dz, own + dz, nxt);
+            scalars(opp + dz, nxl, nsl, nxr, nsr);
             if (z + 2 < L.nz) {
                 xzpp = ld(xv, opp + 2 * dz);
                 szpp = ld(sv, opp + 2 * dz);
             }
         }
+        cp_async_wait<D - 1>();  // all but the D - 1 newest groups done: plane z has landed
+        const int st = t % D;
+        const float4 cym = hy0 ? *slot(st, 0) : f0, cyp = hy1 ? *slot(st, 1) : f0;
+        const float4 cs2 = hy0 ? *slot(st, 2) : f0, cs3 = hy1 ? *slot(st, 3) : f0;
+        const float4 csc = *slot(st, 4), cbb = *slot(st, 5);
         const bool hz0 = z > 0, hz1 = z < L.nz - 1;
         const int p = (col + y + z) & 1;  // x = 2k + p
         const bool xw0 = (p == 0 && !kl), xw1 = (p == 1 && !kr);
         float sl = __shfl_up_sync(0xffffffffu, szc.w, 1), sr = __shfl_down_sync(0xffffffffu, szc.x, 1);
         float xl = __shfl_up_sync(0xffffffffu, xzc.w, 1), xr = __shfl_down_sync(0xffffffffu, xzc.x, 1);
         if (lane == 0) {
-            sl = cur.sl;
-            xl = cur.xl;
+            sl = csl;
+            xl = cxl;
         }
         if (lane == 31) {
-            sr = cur.sr;
-            xr = cur.xr;
+            sr = csr;
+            xr = cxr;
         }
-        const float so[4] = {szc.x, szc.y, szc.z, szc.w}, sc[4] = {cur.sc.x, cur.sc.y, cur.sc.z, cur.sc.w};
-        const float s2v[4] = {cur.s2.x, cur.s2.y, cur.s2.z, cur.s2.w}, s3v[4] = {cur.s3.x, cur.s3.y, cur.s3.z, cur.s3.w};
+        const float so[4] = {szc.x, szc.y, szc.z, szc.w}, sc[4] = {csc.x, csc.y, csc.z, csc.w};
+        const float s2v[4] = {cs2.x, cs2.y, cs2.z, cs2.w}, s3v[4] = {cs3.x, cs3.y, cs3.z, cs3.w};
         const float s4v[4] = {szm.x, szm.y, szm.z, szm.w}, s5v[4] = {szp.x, szp.y, szp.z, szp.w};
         const float xov[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
-        const float ymv[4] = {cur.ym.x, cur.ym.y, cur.ym.z, cur.ym.w}, ypv[4] = {cur.yp.x, cur.yp.y, cur.yp.z, cur.yp.w};
+        const float ymv[4] = {cym.x, cym.y, cym.z, cym.w}, ypv[4] = {cyp.x, cyp.y, cyp.z, cyp.w};
         const float zmv[4] = {xzm.x, xzm.y, xzm.z, xzm.w}, zpv[4] = {xzp.x, xzp.y, xzp.z, xzp.w};
-        const float bv[4] = {cur.bb.x, cur.bb.y, cur.bb.z, cur.bb.w};
+        const float bv[4] = {cbb.x, cbb.y, cbb.z, cbb.w};
         float out[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -547,10 +585,12 @@ __global__ void __launch_bounds__(64, MINB) k_half_zp(Lay L, float h2, const flo
         szm = szc;
         szc = szp;
         szp = szpp;
-        cur = nxt;
-        own += dz;
-        opp += dz;
+        cxl = nxl;
+        csl = nsl;
+        cxr = nxr;
+        csr = nsr;
     }
+    cp_async_wait<0>();  // only empty groups can remain; leave none behind
 }
 
 bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
@@ -566,7 +606,16 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
     const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
     const dim3 blk(vb, ry);
     if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 8) {
-        k_half_zp<16, 8><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf.s, b, x, col);
+        // 11 blocks x 18 KB of staging per SM: ask for the largest shared-memory carveout
+        static const bool carveout = [] {
+            // a preference only: the launch is valid either way
+            if (cudaFuncSetAttribute(k_half_zs<16, 11>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                (void)cudaGetLastError();
+            return true;
+        }();
+        (void)carveout;
+        k_half_zs<16, 11><<<dim3(gx, gy, (L.nz + 15) / 16), blk, kZsSmem, s>>>(L, h2, cf.s, b, x, col);
         return;
     }
     if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 12)
