@@ -141,6 +141,24 @@ def test_apply_smooth_residual_match_oracle(dims, dtype, coeffs):
         assert np.abs(rb[black]).max() <= 50 * tol * np.abs(O.apply(faces, host(xs), H)).max()
 
 
+def test_staged_half_sweep_matches_oracle_ragged_rows():
+    """Grids of at least 4 x 152 x 8 z-marching blocks sweep their s-form regular half sweeps
+    with each plane's loads staged in shared memory (the 512^3 workload's kernel).  320 cells
+    per row give 40 four-cell vectors per colour: two rows per 64-thread block and a second
+    block with 8 of its 32 lanes active per row; 192 x 416 rows and planes make 4992 blocks."""
+    dims = (320, 192, 416)
+    s, M = make(dims, "mixed")
+    nx, ny, nz = dims
+    faces = tuple(f.astype(np.float32).astype(np.float64) for f in M.level_faces(0))
+    x = rnd((nz, ny, nx), 31).astype(np.float32)
+    b = rnd((nz, ny, nx), 32).astype(np.float32)
+    xg, bg = dev(x, torch.float32), dev(b, torch.float32)
+    for sweeps, order in ((1, 0), (1, 1), (2, 0)):
+        xs = xg.clone()
+        assert L.mg_smooth(s._h, 0, xs, bg, sweeps, order) == 0
+        assert rel(host(xs), O.rbgs(faces, b, x, s.h, sweeps, order)) < TOL[torch.float32]
+
+
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("prolong", ["trilinear", "constant"])
