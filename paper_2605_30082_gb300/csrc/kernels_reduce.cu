@@ -345,6 +345,14 @@ __global__ void k_update(Dims d, Lay L, double *p, const float *__restrict__ e, 
     p[m] += f2d_exact(c);
 }
 
+// n (<= 32) doubles from src, and with esrc one unsigned, into mapped pinned host memory
+__global__ void k_readback(const double *__restrict__ src, double *dst, int n, const unsigned *esrc,
+                           unsigned *edst) {
+    const int t = threadIdx.x;
+    if (t < n) dst[t] = src[t];
+    if (t == 0 && esrc) *edst = *esrc;
+}
+
 __global__ void k_add_const(i64 n, double *p, double c) {
     i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (m < n) p[m] += c;
@@ -484,6 +492,16 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
 void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift) {
     count_launch();
     k_update<<<blocks_for(d.n), kThreads, 0, s>>>(d, L, p, e32, (float)alpha, (float)shift);
+}
+
+void launch_readback(cudaStream_t s, const double *src, double *dst_mapped, int n) {
+    count_launch();
+    k_readback<<<1, 32, 0, s>>>(src, dst_mapped, n, nullptr, nullptr);
+}
+
+void launch_readback_u32(cudaStream_t s, const unsigned *src, unsigned *dst_mapped) {
+    count_launch();
+    k_readback<<<1, 32, 0, s>>>(nullptr, nullptr, 0, src, dst_mapped);
 }
 
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {

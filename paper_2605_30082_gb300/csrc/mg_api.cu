@@ -60,7 +60,10 @@ struct mg_handle {
     double *cg_r64, *cg_z64, *cg_d64, *cg_q64;
     double *cg_sc;
     double *red;       // device reduction results (16 doubles)
-    double *hred;      // pinned host copy of red
+    double *hred;      // mapped pinned host memory: 16 doubles read back from red (and the CG
+                       // scalars), then the error word as an unsigned
+    double *hred_dev;  // the device-side address of hred
+    unsigned *herr;    // = (unsigned *)(hred + 16), host side
     unsigned *err;     // device error word
     void *arena;
     size_t arena_bytes;
@@ -93,6 +96,19 @@ int fail(mg_handle *h, int code, const char *fmt, ...) {
     }
     return code;
 }
+
+// n device doubles to h->hred[k..k+n) (k = dst - h->hred) by a kernel writing mapped host
+// memory, not by a copy-engine transfer; the caller synchronises the stream before reading
+#define MG_READBACK(h, s, dst, src, n)                                                          \
+    do {                                                                                        \
+        mg::launch_readback((s), (src), (h)->hred_dev + ((dst) - (h)->hred), (n));               \
+        MG_CUDA((h), cudaGetLastError());                                                       \
+    } while (0)
+#define MG_READBACK_ERR(h, s)                                                                   \
+    do {                                                                                        \
+        mg::launch_readback_u32((s), (h)->err, reinterpret_cast<unsigned *>((h)->hred_dev + 16)); \
+        MG_CUDA((h), cudaGetLastError());                                                       \
+    } while (0)
 
 #define MG_CUDA(h, call)                                                                        \
     do {                                                                                        \
@@ -389,9 +405,9 @@ int finish_operator(mg_handle *h) {
     mg::launch_pinv_finish(s, h->nc, h->pinv, h->scal);
     int st = check_launch(h, "operator set-up");
     if (st) return st;
-    unsigned herr = 0;
-    MG_CUDA(h, cudaMemcpyAsync(&herr, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MG_READBACK_ERR(h, s);
     MG_CUDA(h, cudaStreamSynchronize(s));
+    const unsigned herr = *h->herr;
     if (herr) {
         h->have_op = 0;
         return fail(h, MG_ERR_DENSITY, "density / face coefficients must be finite and > 0");
@@ -460,7 +476,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     const double bscale = mixed ? F.h2 : 1.0;
     mg::launch_sum_sumsq<double>(s, n, b, h->partials, h->red, false);
     mg::launch_sub_mean(s, n, b, h->red, bscale, h->bt, h->partials, h->red + 2);
-    MG_CUDA(h, cudaMemcpyAsync(h->hred, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_READBACK(h, s, h->hred, h->red, 4);
     MG_CUDA(h, cudaStreamSynchronize(s));
     int rc = check_launch(h, "rhs preparation");
     if (rc) return rc;
@@ -481,7 +497,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     } else {
         if (warm) {
             mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 4, false);
-            MG_CUDA(h, cudaMemcpyAsync(h->hred + 4, h->red + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+            MG_READBACK(h, s, h->hred + 4, h->red + 4, 1);
             MG_CUDA(h, cudaStreamSynchronize(s));
             mg::launch_add_const(s, n, p, -h->hred[4] / (double)n);
         } else {
@@ -505,7 +521,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
                 mg::launch_fine_resid2(s, F.d, F.lay, F.h2, F.fx64, F.fy64, F.fz64, F.d64, h->bt, mixed, p,
                                        write32 ? F.b32 : nullptr, (float)(F.ih2 * scale), h->partials, h->red + 6);
             prof_end(h);
-            MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->red + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            MG_READBACK(h, s, h->hred + 6, h->red + 6, 2);
             MG_CUDA(h, cudaStreamSynchronize(s));
             prof_collect(h);
             return check_launch(h, "fine residual");
@@ -530,7 +546,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
                 mg::launch_cg_dir64(s, n, z, d, h->cg_sc, j == 0, rz_prev);
                 mg::launch_cg_apply64(s, F.d, F.ih2, F.fx64, F.fy64, F.fz64, F.d64, d, q, h->partials, h->cg_sc);
                 mg::launch_cg_update64(s, n, p, r, d, q, h->cg_sc, rz_cur, h->partials);
-                MG_CUDA(h, cudaMemcpyAsync(h->hred + 6, h->cg_sc + mg::CG_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+                MG_READBACK(h, s, h->hred + 6, h->cg_sc + mg::CG_RR, 1);
                 MG_CUDA(h, cudaStreamSynchronize(s));
                 rr = std::sqrt(h->hred[6]) / nb;
                 cycles = outer = j + 1;
@@ -598,7 +614,7 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
         if (df) mg::launch_join(s, n, h->p2, p);
         // exact zero-mean gauge at exit (the per-iteration shifts use an FP32 sum)
         mg::launch_sum_sumsq<double>(s, n, p, h->partials, h->red + 12, false);
-        MG_CUDA(h, cudaMemcpyAsync(h->hred + 12, h->red + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MG_READBACK(h, s, h->hred + 12, h->red + 12, 1);
         MG_CUDA(h, cudaStreamSynchronize(s));
         mg::launch_add_const(s, n, p, -h->hred[12] / (double)n);
         (void)mu;
@@ -608,9 +624,9 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
     rc = check_launch(h, "solve");
     if (rc) return rc;
     if (fused0(h, 0)) {  // a bounded wait of a fused sweep that ran out sets bit 4
-        unsigned herr = 0;
-        MG_CUDA(h, cudaMemcpyAsync(&herr, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        MG_READBACK_ERR(h, s);
         MG_CUDA(h, cudaStreamSynchronize(s));
+        const unsigned herr = *h->herr;
         if (herr & 4u) {
             MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), s));
             return fail(h, MG_ERR_CUDA, "a fused sweep gave up waiting for its shared-memory copies");
@@ -784,13 +800,16 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         *slots[q].p = cur;
         cur += slots[q].bytes;
     }
-    if (cudaMallocHost((void **)&h->hred, 16 * sizeof(double)) != cudaSuccess ||
+    if (cudaHostAlloc((void **)&h->hred, 17 * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&h->hred_dev, h->hred, 0) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
         cudaGetLastError();
+        if (h->hred) cudaFreeHost(h->hred);
         cudaFree(h->arena);
         delete h;
         return MG_ERR_CUDA;
     }
+    h->herr = reinterpret_cast<unsigned *>(h->hred + 16);
     if (cudaMemsetAsync(h->err, 0, 256, h->s) != cudaSuccess) {
         mg_destroy(h);
         return MG_ERR_CUDA;
@@ -929,7 +948,7 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
                                 csf ? csfx : nullptr, csf ? csfy : nullptr, csf ? csfz : nullptr,
                                 sigma, gbx, gby, gbz, h->partials, h->red + 8);
         prof_end(h);
-        MG_CUDA(h, cudaMemcpyAsync(h->hred + 8, h->red + 8, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        MG_READBACK(h, h->s, h->hred + 8, h->red + 8, 1);
         MG_CUDA(h, cudaStreamSynchronize(h->s));
         prof_collect(h);
         rc = check_launch(h, "adjoint gradient");
@@ -1079,7 +1098,7 @@ int mg_residual(mg_handle *h, int level, int dtype, const void *x, const void *b
     rc = check_launch(h, "mg_residual");
     if (rc) return rc;
     if (norm2) {
-        MG_CUDA(h, cudaMemcpyAsync(h->hred + 10, h->red + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        MG_READBACK(h, h->s, h->hred + 10, h->red + 10, 2);
         MG_CUDA(h, cudaStreamSynchronize(h->s));
         *norm2 = std::sqrt(h->hred[11]);
     }

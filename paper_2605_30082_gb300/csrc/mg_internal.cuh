@@ -259,6 +259,12 @@ void launch_coarse_matvec(cudaStream_t s, int nc, const double *pinv, const T *r
 
 // ---- reductions, fine-level FP64 passes, adjoint -----------------------------------
 // partials: reduce_blocks(n) x 2 doubles; out: 2 doubles (deterministic order)
+// scalars for the host: a one-thread-per-value kernel stores n (<= 32) doubles, or one
+// unsigned, into mapped pinned host memory (device-side address of a cudaHostAllocMapped
+// buffer), so that the host's wait for them never queues behind bulk copies that other
+// streams run on the copy engines
+void launch_readback(cudaStream_t s, const double *src, double *dst_mapped, int n);
+void launch_readback_u32(cudaStream_t s, const unsigned *src, unsigned *dst_mapped);
 // out[0] = sum x, out[1] = sum x^2 (0 unless `squares`)
 template <typename T>
 void launch_sum_sumsq(cudaStream_t s, i64 n, const T *x, double *partials, double *out, bool squares);
