@@ -140,8 +140,10 @@ void mg_default_opts(mg_opts *opts);
 
 /* Create a solver for one grid.  `stream` is a cudaStream_t (NULL = legacy
  * default stream) on the current device.  Allocates every device buffer the
- * handle will use (hierarchy, scratch, coarse inverse): nothing is allocated
- * later.  It also records the levels below the finest of one V-cycle as a
+ * handle will use (hierarchy, scratch, coarse inverse) and a small mapped
+ * pinned host buffer (cudaHostAllocMapped) into which kernels store the
+ * scalars the host waits for, so that those waits never queue behind copies
+ * other streams run on the copy engines: nothing is allocated later.  It also records the levels below the finest of one V-cycle as a
  * CUDA graph (on a private stream; nothing runs), which every cycle replays;
  * where recording is refused the cycles launch those kernels one by one.  On failure *out is NULL and the code says why (MG_ERR_ARG: opts;
  * MG_ERR_OOM; MG_ERR_CUDA). */
