@@ -266,7 +266,7 @@ __global__ void k_coarse_shift(int nc, double *M, double *scal) {
 // M[K, J] <- P^-1 M[K, J], the trailing update M[I, J] <- M[I, J] - M[I, K] M[K, J], and the
 // column panel M[I, K] <- -M[I, K] P^-1, M[K, K] <- P^-1 (I, J outside K).  The same algebra as
 // the element-wise sweeps, BS pivots per step, so n / BS steps of four launches instead of n.
-constexpr int GJ_BS = 32;
+constexpr int GJ_BS = kGjBlock;
 
 // P^-1 of the bs x bs pivot block by element-wise Gauss-Jordan in shared memory; Pinv (bs x bs,
 // row-major) written to global scratch.  One block of GJ_BS x GJ_BS threads.

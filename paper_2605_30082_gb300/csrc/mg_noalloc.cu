@@ -1,19 +1,20 @@
 // Allocation-free dense Neumann solve (mg_dense_solve_noalloc in include/mg.h).
 //
 // Some callers cannot allocate device memory at the moment they need a
-// solve: code recorded into a CUDA graph by stream capture (cudaMalloc is not
-// allowed while a stream is being captured), programs whose device memory is
-// owned by another allocator such as a framework's caching allocator (a raw
-// cudaMalloc from inside can fail or fragment that pool), and loops that must
-// keep a fixed memory budget.  This entry point serves them: it needs no
-// handle and allocates nothing.  Its working memory is one file-scope
-// __device__ array, present on every GPU that loads this library until the
-// process exits.
+// solve: programs whose device memory is owned by another allocator such as a
+// framework's caching allocator (a raw cudaMalloc from inside can fail when
+// that pool has reserved the memory, or fragment it), loops held to a fixed
+// memory budget, and code that cannot pay for the device-wide synchronisation
+// that cudaMalloc and cudaFree may perform.  This entry point serves them: it
+// needs no handle and allocates nothing.  Its working memory is one
+// file-scope __device__ array, present on every GPU that loads this library
+// until the process exits.
 //
 // Host code may not pass the array's name to a kernel (in host code it names a
 // host-side stand-in, not device memory).  The device address is looked up
 // once per device with cudaGetSymbolAddress, with that device current, on the
-// first call made on that device, and cached.
+// first call made on that device, and cached.  The call reads its error word
+// back and synchronises the caller's stream before it returns.
 #include <mutex>
 
 #include "mg_internal.cuh"
@@ -21,9 +22,11 @@
 namespace {
 
 constexpr int kMaxCells = MG_NOALLOC_MAX_CELLS;
-// layout in doubles: M [kMaxCells^2] | W [kMaxCells^2, of which the inverse of one 32 x 32 pivot
-// block is used] | fx, fy, fz [kMaxCells each] | scal [4] | error word
-constexpr size_t kScratchDoubles = 2 * (size_t)kMaxCells * kMaxCells + 3 * (size_t)kMaxCells + 8;
+constexpr size_t kPivotDoubles = (size_t)mg::kGjBlock * mg::kGjBlock;
+// layout in doubles: M [kMaxCells^2] | W [the inverse of one pivot block of the Gauss-Jordan
+// elimination] | fx, fy, fz [kMaxCells each] | scal [4] | error word.  About 2.1 MB in all.
+constexpr size_t kScratchDoubles =
+    (size_t)kMaxCells * kMaxCells + kPivotDoubles + 3 * (size_t)kMaxCells + 8;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -66,7 +69,7 @@ extern "C" int mg_dense_solve_noalloc(int nx, int ny, int nz, double h, const do
     const int nc = (int)n;
     double *M = base;
     double *W = M + (size_t)kMaxCells * kMaxCells;
-    double *fx = W + (size_t)kMaxCells * kMaxCells;
+    double *fx = W + kPivotDoubles;
     double *fy = fx + kMaxCells;
     double *fz = fy + kMaxCells;
     double *scal = fz + kMaxCells;

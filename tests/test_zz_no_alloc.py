@@ -1,10 +1,11 @@
-"""The allocation-free small-grid solve against the handle-based coarse solve.
+"""The allocation-free small-grid solve against the handle-based coarse solve and the oracle.
 
-mg_dense_solve_noalloc serves callers that cannot allocate device memory
-(stream capture, memory owned by another allocator, fixed budgets); it must
-give the same zero-mean solution as mg_coarse_solve on a handle whose single
-level is the same grid.  Two calls in a row check that the shared scratch
-array is reset between calls.  This file is collected last on purpose.
+mg_dense_solve_noalloc serves callers that cannot allocate device memory when they need a
+solve (device memory owned by another allocator, fixed memory budgets, loops that cannot pay
+for the synchronisation of cudaMalloc/cudaFree).  It must give the same zero-mean solution as
+mg_coarse_solve on a handle whose single level is the same grid, and as the oracle's exact
+coarse solve.  Two calls in a row check that the shared scratch array, which keeps the
+previous call's contents, is reset where it must be.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -37,6 +38,9 @@ def test_noalloc_solve_matches_handle_coarse_solve(dims):
         assert st == L.MG_OK, (call, st)
         torch.cuda.synchronize()
         assert rel(host(e), host(e_ref)) < 1e-11, call
+        # and the oracle's exact zero-mean solve on the host
+        e_or = O.coarse_solve([host(f) for f in faces], host(r), h)
+        assert rel(host(e), e_or) < 1e-11, call
 
 
 def test_noalloc_rejects_too_large_and_bad_coefficients():
