@@ -315,13 +315,38 @@ int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 long long mg_kernel_launches(void);
 
+/* Test hook: arm one-shot faults on this handle, for tests of the failure paths (0 disarms).
+ *   MG_INJECT_FUSED_WAIT  the next fused sweep (opts.fused_sweeps, grid with nz >= 3): its first
+ *                         block issues no copies for one plane while still announcing their
+ *                         bytes, so that block's bounded wait runs out (about a second) with no
+ *                         copy in flight to that stage; it sets bit 4 of the device error word,
+ *                         later blocks return at once, and the solve returns MG_ERR_CUDA and
+ *                         clears the error word (the handle stays usable).
+ *   MG_INJECT_DIVERGE     the next outer residual norm the solve reads back (after its first
+ *                         V-cycle or outer iteration) is replaced by infinity on the host: the
+ *                         solve returns MG_ERR_DIVERGED.
+ * Each fault fires once.  MG_ERR_ARG for unknown bits. */
+enum { MG_INJECT_FUSED_WAIT = 1, MG_INJECT_DIVERGE = 2 };
+int mg_debug_inject(mg_handle *h, int faults);
+
+/* FP64 fused multiply-add rate of the current device, for the roofline of the FP64
+ * kernels (no handle needed).  Launches `blocks` blocks of 256 threads, each thread running 8
+ * independent chains of `iters` dependent FP64 FMAs; one short untimed launch, then one timed
+ * launch with CUDA events on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * sink: device array of at least `blocks` doubles (overwritten with per-block sums, so that
+ * no chain is dead code).  *tflops = 2 * FMAs / time (an FMA counts as two flops; an FP64
+ * add or multiply issues at the FMA rate, so one FP64 instruction per second counts half of
+ * this figure); *ms (may be NULL) = the timed launch's duration.  Synchronises `stream`.
+ * MG_ERR_ARG for a null sink/tflops or non-positive sizes; MG_ERR_CUDA if a launch fails. */
+int mg_fp64_fma_rate(void *stream, double *sink, int blocks, int iters, double *tflops, double *ms);
+
 /* ---- allocation-free entry point ----------------------------------------------------
- * The paper has no counterpart to this call; it exists for callers that cannot
- * allocate device memory when they need a solve: code being recorded into a
- * CUDA graph by stream capture (cudaMalloc is not allowed during capture),
- * programs whose device memory belongs to another allocator (a framework's
- * caching pool, where an extra cudaMalloc can fail or fragment the pool), and
- * loops held to a fixed memory budget.
+ * The paper has no counterpart to this call.  It exists for callers that cannot
+ * allocate device memory when they need a solve: programs whose device memory
+ * belongs to another allocator (a framework's caching pool, where an extra
+ * cudaMalloc can fail or fragment the pool), loops held to a fixed memory
+ * budget, and code that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may cause.
  *
  * e = A^+ (r - mean r): the exact zero-mean solution of the cell-centred
  * Neumann operator above on a small grid, for face coefficients bx, by, bz in
@@ -331,13 +356,14 @@ long long mg_kernel_launches(void);
  * call builds the dense pseudo-inverse from scratch and applies it; it needs
  * no handle and calls no cudaMalloc, cudaFree or other allocating routine.
  * Working memory is one fixed array in this library's device image (about
- * 4.2 MB, held on every GPU that loads the library until the process exits),
+ * 2.1 MB, held on every GPU that loads the library until the process exits),
  * so nx*ny*nz must be at most MG_NOALLOC_MAX_CELLS (MG_ERR_ARG otherwise).
  * The first call on each device looks up that array's device address (with
  * that device current); make it before any stream capture.  Every call uses
  * the same array, which keeps the previous call's contents: calls that can
  * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Synchronises `stream` before returning. */
+ * serialised by the caller.  The call reads its error word back to the host
+ * and synchronises `stream` before returning. */
 #define MG_NOALLOC_MAX_CELLS 512
 int mg_dense_solve_noalloc(int nx, int ny, int nz, double h, const double *bx, const double *by,
                            const double *bz, const double *r, double *e, void *stream);

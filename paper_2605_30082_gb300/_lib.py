@@ -24,6 +24,7 @@ MG_METHOD_VCYCLE, MG_METHOD_FCG = 0, 1
 MG_F64, MG_F32 = 0, 1
 MG_MAX_LEVELS, MG_MAX_COARSE, MG_HIST_LEN = 24, 1024, 256
 MG_NOALLOC_MAX_CELLS = 512
+MG_INJECT_FUSED_WAIT, MG_INJECT_DIVERGE = 1, 2
 (MG_PROF_SMOOTH, MG_PROF_RESID_RESTRICT, MG_PROF_PROLONG, MG_PROF_COARSE,
  MG_PROF_FINE_RESIDUAL, MG_PROF_UPDATE, MG_PROF_ADJOINT_GRAD, MG_PROF_PROJECT,
  MG_PROF_DENSITY_GRAD, MG_PROF_NCLASS) = range(10)
@@ -85,6 +86,8 @@ SIGNATURES = {
     "mg_profile_read": (_i, [_v, _i, C.POINTER(_ll), C.POINTER(_d)]),
     "mg_kernel_launches": (_ll, []),
     "mg_dense_solve_noalloc": (_i, [_i, _i, _i, _d, _v, _v, _v, _v, _v, _v]),
+    "mg_fp64_fma_rate": (_i, [_v, _v, _i, _i, C.POINTER(_d), C.POINTER(_d)]),
+    "mg_debug_inject": (_i, [_v, _i]),
 }
 
 
@@ -345,6 +348,11 @@ def mg_kernel_launches():
     return lib().mg_kernel_launches()
 
 
+def mg_debug_inject(h, faults):
+    """Arm one-shot test faults (MG_INJECT_* bits) on the handle; returns the status."""
+    return lib().mg_debug_inject(h, int(faults))
+
+
 def mg_dense_solve_noalloc(dims, h, bx, by, bz, r, e, stream=None):
     """Allocation-free exact small-grid solve (see include/mg.h); returns the status."""
     if stream is None:
@@ -356,3 +364,15 @@ def mg_dense_solve_noalloc(dims, h, bx, by, bz, r, e, stream=None):
                                         _dev(by, shape=fs[1], name="by"), _dev(bz, shape=fs[2], name="bz"),
                                         _dev(r, shape=cs, name="r"), _dev(e, shape=cs, name="e"),
                                         C.c_void_p(stream.cuda_stream))
+
+
+def mg_fp64_fma_rate(sink, iters, stream=None):
+    """FP64 FMA rate of the current device: one timed launch of len(sink) blocks (sink: float64
+    CUDA tensor, overwritten).  Returns (status, TFLOP/s, ms)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    tf = C.c_double(0.0)
+    ms = C.c_double(0.0)
+    st = lib().mg_fp64_fma_rate(C.c_void_p(stream.cuda_stream), _dev(sink, name="sink"), int(sink.numel()),
+                                int(iters), C.byref(tf), C.byref(ms))
+    return st, tf.value, ms.value

@@ -399,7 +399,7 @@ void launch_resid_dfs(cudaStream_t s, Dims d, Lay L, const float2 *s2, const flo
     const dim3 blk(vb, kDfsThreads / vb);
     const int tiles_x = (hx + vb - 1) / vb, tiles_y = (d.ny + (int)blk.y - 1) / (int)blk.y;
     const i64 ntiles = (i64)tiles_x * tiles_y * ((d.nz + kDfsZ - 1) / kDfsZ);
-    i64 nb = 152 * 6;
+    i64 nb = (i64)device_sms() * 6;
     if (nb > ntiles) nb = ntiles;
     if (nb > reduce_blocks(d.n)) nb = reduce_blocks(d.n);  // the partials buffer holds reduce_blocks(n) pairs
     count_launch();

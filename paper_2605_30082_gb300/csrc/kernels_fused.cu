@@ -172,7 +172,7 @@ struct Geo {
 // nothing, arrives on the stage's mbarrier with the exact byte count first.
 __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0, int c1, bool from_zero,
                                             const float *X, const float *sv, float *stg,
-                                            unsigned bar, int lane) {
+                                            unsigned bar, int lane, bool skip = false) {
     const int c2 = 1 - c1;
     const int ks = k0 - 4 < 0 ? 0 : k0 - 4, ke = k0 + TX + 4 > g.hx ? g.hx : k0 + TX + 4;
     const unsigned rb = (unsigned)(ke - ks) * 4u;
@@ -206,13 +206,16 @@ __device__ __forceinline__ void issue_plane(const Geo &g, int q, int k0, int y0,
     for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     if (lane == 0) mbar_expect_tx_arrive(bar, total);
     __syncwarp();
-    for (int i = 0; i < cnt; ++i) bulk_g2s(dsts[i], srcs[i], rb, bar);
+    // skip (a test's fault injection): the bytes are expected but no copy is issued, so the
+    // stage's phase never completes and its wait runs out, with no copy in flight to the stage
+    if (!skip)
+        for (int i = 0; i < cnt; ++i) bulk_g2s(dsts[i], srcs[i], rb, bar);
 }
 
 template <bool FROM_ZERO, bool UPDATE>
 __global__ void __launch_bounds__(kThreads, 3)
     k_sweep_fused(Geo g, float h2, const float *__restrict__ sv, const float *__restrict__ b, const float *X,
-                  float *Y, int c1, FUpd up, unsigned *err) {
+                  float *Y, int c1, FUpd up, unsigned *err, int skip_plane) {
     extern __shared__ __align__(16) float sm[];
     float *stages = sm;
     float *c1n = sm + (size_t)kStages * STAGE;  // 3 planes of new c1 values
@@ -242,6 +245,9 @@ __global__ void __launch_bounds__(kThreads, 3)
         for (int q = qlo; q <= min(qlo + kAhead + 1, qhi); ++q)
             issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, stages + (size_t)stage_of(q) * STAGE, bar_of(q), lane);
     int issued = min(qlo + kAhead + 1, qhi);  // newest plane issued
+    // fault injection (tests only; -1 otherwise): block (0, 0, 0) skips the copies of plane
+    // skip_plane, which it issues inside the loop below
+    const int skip_q = (blockIdx.x | blockIdx.y | blockIdx.z) == 0 ? skip_plane : -1000;
     // planes z0-2 and z0-1 are used from the first step on
     bool ok = mbar_wait(bar_of(qlo), parity_of(qlo)) && mbar_wait(bar_of(qlo + 1), parity_of(qlo + 1));
 
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             const int q = issued + 1;
             if (warp == kProducerWarp)
                 issue_plane(g, q, k0, y0, c1, FROM_ZERO, X, sv, stages + (size_t)stage_of(q) * STAGE, bar_of(q),
-                            lane);
+                            lane, q == skip_q);
             issued = q;
         }
         // b for the next step
@@ -440,7 +446,7 @@ size_t sweep_fused_smem() { return kSmemBytes; }
 
 template <bool FZ, bool UPD>
 void run_fused(cudaStream_t s, dim3 grid, const Geo &g, float h2, const float *sinv, const float *b, const float *X,
-               float *Y, int c1, const FUpd &up, unsigned *err) {
+               float *Y, int c1, const FUpd &up, unsigned *err, int skip_plane) {
     // the dynamic shared-memory opt-in is a per-device attribute of the kernel
     static unsigned long long done = 0;
     int dev = 0;
@@ -449,21 +455,24 @@ void run_fused(cudaStream_t s, dim3 grid, const Geo &g, float h2, const float *s
         cudaFuncSetAttribute(k_sweep_fused<FZ, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (dev >= 0 && dev < 64) done |= 1ull << dev;
     }
-    k_sweep_fused<FZ, UPD><<<grid, kThreads, kSmemBytes, s>>>(g, h2, sinv, b, X, Y, c1, up, err);
+    k_sweep_fused<FZ, UPD><<<grid, kThreads, kSmemBytes, s>>>(g, h2, sinv, b, X, Y, c1, up, err, skip_plane);
 }
 
 void launch_sweep_fused(cudaStream_t s, Lay L, double h2, const float *sinv, const float *b, const float *X,
-                        float *Y, int c1, bool from_zero, double *p, double alpha, double shift, unsigned *err) {
+                        float *Y, int c1, bool from_zero, double *p, double alpha, double shift, unsigned *err,
+                        bool inject_wait) {
     Geo g{L.hx, L.ny, L.nz, (long long)L.half, (long long)L.ny * L.hx};
+    // the first plane block (0, 0, 0) issues inside its loop: kAhead + 2 planes past its first (-2)
+    const int skip_plane = inject_wait ? kAhead : -1;
     const dim3 grid(L.hx / TX, (L.ny + TY - 1) / TY, (L.nz + ZC - 1) / ZC);
     FUpd up{p, (float)alpha, (float)shift};
     count_launch();
     if (p)
-        run_fused<false, true>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err);
+        run_fused<false, true>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err, skip_plane);
     else if (from_zero)
-        run_fused<true, false>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err);
+        run_fused<true, false>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err, skip_plane);
     else
-        run_fused<false, false>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err);
+        run_fused<false, false>(s, grid, g, (float)h2, sinv, b, X, Y, c1, up, err, skip_plane);
 }
 
 }  // namespace mg

@@ -7,6 +7,7 @@
 // model (one wave of resident blocks at most); each block writes one partial
 // (warp shuffles in a fixed pattern), and one block sums the partials in index
 // order, so results are bitwise reproducible for the same inputs and device.
+#include <atomic>
 #include <cmath>
 
 #include "mg_internal.cuh"
@@ -19,9 +20,26 @@ void count_launch(int k) { __atomic_fetch_add(&g_launches, (unsigned long long)k
 
 unsigned long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        (void)cudaGetLastError();
+        dev = -1;
+    }
+    if (dev >= 0 && dev < kMaxDev && (v = cache[dev].load(std::memory_order_relaxed)) > 0) return v;
+    if (dev < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        (void)cudaGetLastError();
+        return 152;  // the query failed: size for GB300 (grid sizes only; results do not depend on it)
+    }
+    if (dev < kMaxDev) cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 int reduce_blocks(i64 n) {
     i64 b = (n + kReduceThreads - 1) / kReduceThreads;
-    const i64 cap = 152 * 8;
+    const i64 cap = (i64)device_sms() * 8;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -424,6 +442,221 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
     block_sum2(ds * ihd, 0.0, partials + 2 * blockIdx.x);
 }
 
+// ---- fused gradient without a surface term: no FP64 arithmetic -------------------------
+// A double v is split into two floats v ~ hi + lo with integer operations on its IEEE-754
+// fields: hi keeps the sign, exponent and top 23 fraction bits (truncation), lo the value of
+// the 29 bits dropped, taken to 23 of them (the low 6 are truncated: |v - hi - lo| <= 2^-46 |v|).
+// lo is formed exactly as the difference of two floats with the same exponent 2^E (E = e - 1046
+// for the double's biased exponent e): (2^E with the dropped bits as its fraction) - 2^E.
+// A difference of two doubles is then (hi_a - hi_b) + (lo_a - lo_b) in FP32: the first term is
+// exact when a and b are within a factor of two (the cancelling case), otherwise rounded once;
+// the result is within about one FP32 unit of the exact difference plus an absolute 2^-45
+// max(|a|, |b|) (the pair holds 47 bits of the 53).  For the FP32 face gradients that is far
+// below their own rounding wherever a - b is not itself within 2^-20 of a's magnitude.
+// |v| below 2^-126 gives 0 (an absolute error under 2^-126); non-finite or |v| >= 2^128 gives
+// hi = +-inf or NaN.
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned h32 = (unsigned)(u >> 32);
+    const unsigned sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    const int e32 = e - 896;  // biased FP32 exponent of v: e - 1023 + 127
+    if (e32 <= 0) {
+        hi = __uint_as_float(sign);
+        lo = 0.f;
+        return;
+    }
+    if (e32 >= 255) {
+        hi = __uint_as_float(sign | 0x7f800000u | ((e == 0x7ff && (u << 12) != 0ull) ? 0x400000u : 0u));
+        lo = 0.f;
+        return;
+    }
+    hi = __uint_as_float(sign | ((unsigned)e32 << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+    const int el = e - 919;  // biased FP32 exponent of 2^(e - 1046)
+    if (el <= 0) {
+        lo = 0.f;
+        return;
+    }
+    const unsigned base = sign | ((unsigned)el << 23);
+    lo = __uint_as_float(base | (unsigned)((u >> 6) & 0x7fffffu)) - __uint_as_float(base);
+}
+
+// dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R)/h^2 on every interior face, FP32, with the
+// differences formed from split_f64 pairs.  Block (32, kGradRows): a warp covers 32 cells of a
+// row and marches kGradPlanes planes in z, keeping the previous plane's pairs in registers (the
+// z face), taking the x-1 pair from the neighbouring lane (lane 0 loads it) and loading the
+// y-1 row (split again; that row was just read by the warp above, so it comes from cache).
+constexpr int kGradRows = 8, kGradPlanes = 32;
+
+__global__ void __launch_bounds__(32 * kGradRows) k_adjoint_grad_split(
+    int nx, int ny, int nz, float ih2, const double *__restrict__ lam, const double *__restrict__ p,
+    float *__restrict__ gx, float *__restrict__ gy, float *__restrict__ gz) {
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * 32 + lane;
+    const int y = blockIdx.y * kGradRows + threadIdx.y;
+    const int z0 = blockIdx.z * kGradPlanes;
+    const int z1 = min(z0 + kGradPlanes, nz);
+    const bool act = x < nx && y < ny;
+    const int nxy = nx * ny;  // < 2^31 (checked by the launcher with nx * ny * (nz + 1))
+    float lzh = 0.f, lzl = 0.f, pzh = 0.f, pzl = 0.f;  // plane z - 1
+    if (act && z0 > 0) {
+        const int c = (z0 - 1) * nxy + y * nx + x;
+        split_f64(lam[c], lzh, lzl);
+        split_f64(p[c], pzh, pzl);
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int c = z * nxy + y * nx + x;
+        float lh = 0.f, ll = 0.f, ph = 0.f, pl = 0.f;
+        double lyd = 0.0, pyd = 0.0;
+        if (act) {
+            const double lc = lam[c], pc = p[c];
+            if (y > 0) {
+                lyd = lam[c - nx];
+                pyd = p[c - nx];
+            }
+            split_f64(lc, lh, ll);
+            split_f64(pc, ph, pl);
+        }
+        // x - 1 pair from the lane to the left (every lane takes part in the shuffles)
+        float lxh = __shfl_up_sync(0xffffffffu, lh, 1), lxl = __shfl_up_sync(0xffffffffu, ll, 1);
+        float pxh = __shfl_up_sync(0xffffffffu, ph, 1), pxl = __shfl_up_sync(0xffffffffu, pl, 1);
+        if (act) {
+            if (lane == 0 && x > 0) {
+                split_f64(lam[c - 1], lxh, lxl);
+                split_f64(p[c - 1], pxh, pxl);
+            }
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            if (x > 0) g0 = -((lxh - lh) + (lxl - ll)) * (((pxh - ph) + (pxl - pl)) * ih2);
+            if (y > 0) {
+                float lyh, lyl, pyh, pyl;
+                split_f64(lyd, lyh, lyl);
+                split_f64(pyd, pyh, pyl);
+                g1 = -((lyh - lh) + (lyl - ll)) * (((pyh - ph) + (pyl - pl)) * ih2);
+            }
+            if (z > 0) g2 = -((lzh - lh) + (lzl - ll)) * (((pzh - ph) + (pzl - pl)) * ih2);
+            const int row = z * ny + y;
+            const int ax = row * (nx + 1) + x;          // x faces: (nz, ny, nx + 1)
+            const int ay = (z * (ny + 1) + y) * nx + x;  // y faces: (nz, ny + 1, nx)
+            __stcs(gx + ax, g0);
+            __stcs(gy + ay, g1);
+            __stcs(gz + c, g2);
+            if (x == nx - 1) gx[ax + 1] = 0.f;
+            if (y == ny - 1) gy[ay + nx] = 0.f;
+            if (z == nz - 1) gz[c + nxy] = 0.f;
+        }
+        lzh = lh;
+        lzl = ll;
+        pzh = ph;
+        pzl = pl;
+    }
+}
+
+// The same for even nx, two cells per thread: 16-byte loads of lam and p (both 16-byte
+// aligned, as the ABI requires), and the next plane's four loads issued before the current
+// plane is computed.  Block (32, kGrad2Rows): a warp covers 64 cells of a row.
+constexpr int kGrad2Rows = 16, kGrad2Planes = 32;
+
+struct Pair4 {
+    float h0, l0, h1, l1;  // split of cells x and x + 1
+};
+__device__ __forceinline__ Pair4 split2(double2 v) {
+    Pair4 r;
+    split_f64(v.x, r.h0, r.l0);
+    split_f64(v.y, r.h1, r.l1);
+    return r;
+}
+// -(la - lb)(pa - pb) ih2 from the split pairs
+__device__ __forceinline__ float grad_face(float lah, float lal, float lbh, float lbl, float pah, float pal,
+                                           float pbh, float pbl, float ih2) {
+    return -((lah - lbh) + (lal - lbl)) * (((pah - pbh) + (pal - pbl)) * ih2);
+}
+
+__global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
+    int nx, int ny, int nz, float ih2, const double *__restrict__ lam, const double *__restrict__ p,
+    float *__restrict__ gx, float *__restrict__ gy, float *__restrict__ gz) {
+    const int lane = threadIdx.x;
+    const int x = 2 * (blockIdx.x * 32 + lane);
+    const int y = blockIdx.y * kGrad2Rows + threadIdx.y;
+    const int z0 = blockIdx.z * kGrad2Planes;
+    const int z1 = min(z0 + kGrad2Planes, nz);
+    const bool act = x < nx && y < ny;  // nx even: x + 1 < nx too
+    const bool hy = act && y > 0;
+    const int nxy = nx * ny;
+    const double2 zero2 = make_double2(0.0, 0.0);
+    Pair4 lz{0.f, 0.f, 0.f, 0.f}, pz{0.f, 0.f, 0.f, 0.f};  // plane z - 1
+    if (act && z0 > 0) {
+        const int c = (z0 - 1) * nxy + y * nx + x;
+        lz = split2(*reinterpret_cast<const double2 *>(lam + c));
+        pz = split2(*reinterpret_cast<const double2 *>(p + c));
+    }
+    // loads of the first plane
+    double2 Lc = zero2, Pc = zero2, Ly = zero2, Py = zero2;
+    {
+        const int c = z0 * nxy + y * nx + x;
+        if (act && z0 < z1) {
+            Lc = *reinterpret_cast<const double2 *>(lam + c);
+            Pc = *reinterpret_cast<const double2 *>(p + c);
+        }
+        if (hy && z0 < z1) {
+            Ly = *reinterpret_cast<const double2 *>(lam + c - nx);
+            Py = *reinterpret_cast<const double2 *>(p + c - nx);
+        }
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int c = z * nxy + y * nx + x;
+        // the next plane's loads, in flight while this plane computes
+        double2 Ln = zero2, Pn = zero2, Lyn = zero2, Pyn = zero2;
+        if (z + 1 < z1) {
+            if (act) {
+                Ln = *reinterpret_cast<const double2 *>(lam + c + nxy);
+                Pn = *reinterpret_cast<const double2 *>(p + c + nxy);
+            }
+            if (hy) {
+                Lyn = *reinterpret_cast<const double2 *>(lam + c + nxy - nx);
+                Pyn = *reinterpret_cast<const double2 *>(p + c + nxy - nx);
+            }
+        }
+        const Pair4 l = split2(Lc), q = split2(Pc);
+        // cell x - 1 is the second cell of the lane to the left (lane 0 loads it)
+        float lxh = __shfl_up_sync(0xffffffffu, l.h1, 1), lxl = __shfl_up_sync(0xffffffffu, l.l1, 1);
+        float pxh = __shfl_up_sync(0xffffffffu, q.h1, 1), pxl = __shfl_up_sync(0xffffffffu, q.l1, 1);
+        if (act) {
+            if (lane == 0 && x > 0) {
+                split_f64(lam[c - 1], lxh, lxl);
+                split_f64(p[c - 1], pxh, pxl);
+            }
+            float a0 = 0.f, a1, b0 = 0.f, b1 = 0.f, e0 = 0.f, e1 = 0.f;
+            if (x > 0) a0 = grad_face(lxh, lxl, l.h0, l.l0, pxh, pxl, q.h0, q.l0, ih2);
+            a1 = grad_face(l.h0, l.l0, l.h1, l.l1, q.h0, q.l0, q.h1, q.l1, ih2);
+            if (y > 0) {
+                const Pair4 ly = split2(Ly), py = split2(Py);
+                b0 = grad_face(ly.h0, ly.l0, l.h0, l.l0, py.h0, py.l0, q.h0, q.l0, ih2);
+                b1 = grad_face(ly.h1, ly.l1, l.h1, l.l1, py.h1, py.l1, q.h1, q.l1, ih2);
+            }
+            if (z > 0) {
+                e0 = grad_face(lz.h0, lz.l0, l.h0, l.l0, pz.h0, pz.l0, q.h0, q.l0, ih2);
+                e1 = grad_face(lz.h1, lz.l1, l.h1, l.l1, pz.h1, pz.l1, q.h1, q.l1, ih2);
+            }
+            const int row = z * ny + y;
+            const int ax = row * (nx + 1) + x;          // x faces: (nz, ny, nx + 1), not 8-byte aligned
+            const int ay = (z * (ny + 1) + y) * nx + x;  // y faces: (nz, ny + 1, nx), even
+            __stcs(gx + ax, a0);
+            __stcs(gx + ax + 1, a1);
+            __stcs(reinterpret_cast<float2 *>(gy + ay), make_float2(b0, b1));
+            __stcs(reinterpret_cast<float2 *>(gz + c), make_float2(e0, e1));
+            if (x + 2 == nx) gx[ax + 2] = 0.f;
+            if (y == ny - 1) *reinterpret_cast<float2 *>(gy + ay + nx) = make_float2(0.f, 0.f);
+            if (z == nz - 1) *reinterpret_cast<float2 *>(gz + c + nxy) = make_float2(0.f, 0.f);
+        }
+        lz = l;
+        pz = q;
+        Lc = Ln;
+        Pc = Pn;
+        Ly = Lyn;
+        Py = Pyn;
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -509,10 +742,30 @@ void launch_add_const(cudaStream_t s, i64 n, double *p, double c) {
     k_add_const<<<blocks_for(n), kThreads, 0, s>>>(n, p, c);
 }
 
+inline bool aligned16h(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+inline bool aligned8h(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 7) == 0; }
+
 void launch_adjoint_grad(cudaStream_t s, Dims d, double h, const double *lam, const double *p,
                          const double *fx, const double *fy, const double *fz, const double *csfx,
                          const double *csfy, const double *csfz, double sigma, float *gx,
                          float *gy, float *gz, double *partials, double *out) {
+    // without a surface term dL/dsigma is 0 (the caller sets it) and the face gradients need no
+    // FP64 arithmetic: the split-FP32 kernel, when the face arrays fit 32-bit indices
+    if (!csfx && gx && (i64)(d.nx + 1) * (d.ny + 1) * (d.nz + 1) < (1ll << 31)) {
+        count_launch();
+        if (d.nx % 2 == 0 && aligned16h(lam) && aligned16h(p) && aligned8h(gy) && aligned8h(gz)) {
+            const dim3 grid((d.nx / 2 + 31) / 32, (d.ny + kGrad2Rows - 1) / kGrad2Rows,
+                            (d.nz + kGrad2Planes - 1) / kGrad2Planes);
+            k_adjoint_grad_split2<<<grid, dim3(32, kGrad2Rows), 0, s>>>(d.nx, d.ny, d.nz, (float)(1.0 / (h * h)),
+                                                                        lam, p, gx, gy, gz);
+            return;
+        }
+        const dim3 grid((d.nx + 31) / 32, (d.ny + kGradRows - 1) / kGradRows,
+                        (d.nz + kGradPlanes - 1) / kGradPlanes);
+        k_adjoint_grad_split<<<grid, dim3(32, kGradRows), 0, s>>>(d.nx, d.ny, d.nz, (float)(1.0 / (h * h)),
+                                                                  lam, p, gx, gy, gz);
+        return;
+    }
     static const int wave = wave_blocks((const void *)k_adjoint_grad, kReduceThreads);
     int nb = fill_blocks(reduce_blocks(d.n), wave);
     count_launch();

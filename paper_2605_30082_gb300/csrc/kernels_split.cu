@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const flo
 bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
 
 // 16 planes per thread where that still gives about 4 waves of 64-thread blocks (12 resident
-// per SM on 152 SMs), else 4
+// per SM, on the device's SM count), else 4
 template <bool SFORM, bool FROM_ZERO, int UPDATE>
 void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
                 const Upd &up) {
@@ -605,7 +605,8 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
     const int ry = 64 / vb;                    // rows per block
     const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
     const dim3 blk(vb, ry);
-    if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 8) {
+    const i64 sms = device_sms();
+    if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 8) {
         // 11 blocks x 18 KB of staging per SM: ask for the largest shared-memory carveout
         static const bool carveout = [] {
             // a preference only: the launch is valid either way
@@ -618,7 +619,7 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
         k_half_zs<16, 11><<<dim3(gx, gy, (L.nz + 15) / 16), blk, kZsSmem, s>>>(L, h2, cf.s, b, x, col);
         return;
     }
-    if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * 152 * 12)
+    if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 12)
         k_half_z<SFORM, FROM_ZERO, UPDATE, 16><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf, b, x, col, up);
     else
         k_half_z<SFORM, FROM_ZERO, UPDATE, 4><<<dim3(gx, gy, (L.nz + 3) / 4), blk, 0, s>>>(L, h2, cf, b, x, col, up);

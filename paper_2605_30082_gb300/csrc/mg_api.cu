@@ -69,6 +69,7 @@ struct mg_handle {
     size_t arena_bytes;
     int have_op;
     int sform0;        // level-0 FP32 kernels use s = 1/rho (operator set from a density)
+    int inject;        // pending one-shot test faults (MG_INJECT_* bits, mg_debug_inject)
     cudaEvent_t ev0, ev1;
     // the V-cycle below the finest level, recorded once at mg_create as a CUDA graph (its
     // launches use fixed buffers and parameters) and replayed by every cycle; null: launched
@@ -252,7 +253,9 @@ void sweep_fused(mg_handle *h, const float *b, const float *X, float *Y, int c1,
                  double *p = nullptr, double alpha = 0.0, double shift = 0.0) {
     Level &L = h->lv[0];
     prof_begin(h, p ? MG_PROF_UPDATE : MG_PROF_SMOOTH);
-    mg::launch_sweep_fused(h->s, L.lay, L.h2, L.s32, b, X, Y, c1, from_zero, p, alpha, shift, h->err);
+    const bool inject = (h->inject & MG_INJECT_FUSED_WAIT) != 0;
+    h->inject &= ~MG_INJECT_FUSED_WAIT;
+    mg::launch_sweep_fused(h->s, L.lay, L.h2, L.s32, b, X, Y, c1, from_zero, p, alpha, shift, h->err, inject);
     prof_end(h);
 }
 
@@ -596,6 +599,10 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             rc = residual(mixed);
             if (rc) return rc;
             rn = std::sqrt(h->hred[6]) * F.ih2;
+            if (h->inject & MG_INJECT_DIVERGE) {  // test fault: the read-back norm is lost
+                h->inject &= ~MG_INJECT_DIVERGE;
+                rn = HUGE_VAL;
+            }
             double mu_new = h->hred[7] / (double)n;
             if (!mixed) mg::launch_add_const(s, n, p, -mu_new);  // FP64 path: zero mean each cycle
             mu = mixed ? mu_new : 0.0;
@@ -762,7 +769,7 @@ int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
         }
     }
     add((void **)&h->pinv, 8 * (size_t)nc * nc);
-    add((void **)&h->gj_tmp, 8 * (size_t)nc * nc);
+    add((void **)&h->gj_tmp, 8 * (size_t)mg::kGjBlock * mg::kGjBlock);
     add((void **)&h->scal, 8 * 4);
     add((void **)&h->bt, 8 * (size_t)h->lv[0].d.n);
     if (dfm) {
@@ -1181,5 +1188,11 @@ int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms) {
 }
 
 long long mg_kernel_launches(void) { return (long long)mg::launches_total(); }
+
+int mg_debug_inject(mg_handle *h, int faults) {
+    if (!h || (faults & ~(MG_INJECT_FUSED_WAIT | MG_INJECT_DIVERGE))) return MG_ERR_ARG;
+    h->inject = faults;
+    return MG_OK;
+}
 
 }  // extern "C"

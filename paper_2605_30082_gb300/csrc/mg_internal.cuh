@@ -128,6 +128,8 @@ void count_launch(int k = 1);
 // the most blocks a deterministic reduction over n elements uses (its partials buffer holds
 // that many pairs); launchers take min(this, one wave of the kernel)
 int reduce_blocks(i64 n);
+// streaming multiprocessors of the current device (queried once per device; 152 on GB300)
+int device_sms();
 constexpr int kReduceThreads = 256;
 // blocks of one full wave of `kernel` at `threads` threads per block on the current device
 // (resident blocks per SM x SMs; 2^30 if the query fails).  Launchers cache it in a function-
@@ -162,7 +164,9 @@ void launch_rhs(cudaStream_t s, Dims d, double h, const double *b0, const double
 // dense coarse inverse (Gauss-Jordan on A_c + c 1 1^T, then minus 1/(c n^2))
 void launch_coarse_assemble(cudaStream_t s, Dims d, double ih2, const double *fx, const double *fy,
                             const double *fz, double *M, double *scal);
-// Gauss-Jordan inversion in place by blocks of 32 pivots (scratch: 32 x 32 doubles)
+// Gauss-Jordan inversion in place by blocks of kGjBlock pivots (scratch: kGjBlock x kGjBlock
+// doubles, the inverse of the current pivot block)
+constexpr int kGjBlock = 32;
 void launch_gj_blocked(cudaStream_t s, int nc, double *M, double *scratch);
 void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 
@@ -186,10 +190,12 @@ void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, c
 // s-form split level with hx % 64 == 0: one sweep, colour c1 first, reading x from X and
 // writing both colours to Y (X != Y); from_zero: X is not read (x = 0).  With p non-null the
 // second colour's new values and the first colour's go into p = (p - shift) + alpha x (natural
-// FP64) instead of Y.  A bounded wait that runs out sets bit 4 of *err.
+// FP64) instead of Y.  A bounded wait that runs out sets bit 4 of *err.  inject_wait (tests
+// only): one block issues no copies for one plane, so that its wait runs out.
 bool sweep_fused_ok(Lay L);
 void launch_sweep_fused(cudaStream_t s, Lay L, double h2, const float *sinv, const float *b, const float *X,
-                        float *Y, int c1, bool from_zero, double *p, double alpha, double shift, unsigned *err);
+                        float *Y, int c1, bool from_zero, double *p, double alpha, double shift, unsigned *err,
+                        bool inject_wait = false);
 
 // ---- MG_MIXED_DF outer loop (kernels_df.cu): double-float (hi, lo) FP32 pairs ----
 void launch_split(cudaStream_t s, i64 n, const double *src, float2 *dst);   // hi = fl32(v), lo = fl32(v - hi)

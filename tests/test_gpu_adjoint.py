@@ -12,7 +12,7 @@ import torch
 import oracle as O
 from paper_2605_30082_gb300 import PoissonSolve, Solver
 
-from _helpers import csf_case, dev, host, rel
+from _helpers import csf_case, dev, host, random_rho, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +40,35 @@ def test_adjoint_matches_oracle_32cubed(prec):
         assert gg.dtype == torch.float32
         assert rel(host(gg), go) < 1e-6
     assert abs(ds - ds_o) <= 1e-8 * abs(ds_o)
+
+
+@pytest.mark.parametrize("dims,prec", [((32, 32, 32), "mixed"), ((48, 40, 72), "mixed"), ((40, 24, 36), "fp64"),
+                                       ((96, 64, 80), "mixed_df"), ((136, 40, 72), "mixed"), ((21, 8, 6), "fp64")])
+def test_face_gradients_without_surface_term_every_face(dims, prec):
+    """Without a CSF term the face gradients come from FP32 pairs (no FP64 arithmetic): every
+    face against the oracle's formula at the GPU's own lambda and p, within a few FP32 units
+    (plus 1e-10 of the largest gradient for the pairs' 47-bit cancellation limit).
+    Grids whose rows are not multiples of the warp's 64 cells (two per lane), of the 16-row
+    tile and of the 32-plane z-run cover the ragged edges; an odd nx takes the one-cell-per-lane
+    kernel."""
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    rho = random_rho(dims, 17)
+    faces = O.faces_from_density(rho)
+    s = Solver(dims, h=h, precision=prec, coarsest=8)
+    s.set_density(dev(rho))
+    rng = np.random.default_rng(3)
+    p = s.solve(dev(rng.standard_normal((nz, ny, nx))))
+    lam, g, ds = s.adjoint(dev(rng.standard_normal((nz, ny, nx))), p)
+    assert ds == 0.0
+    g_o, _ = O.adjoint_grads(faces, host(lam), host(p), h)
+    for gg, go in zip(g, g_o):
+        got = host(gg)
+        scale = np.abs(go).max()
+        assert np.all(np.abs(got - go) <= 6 * 2.0**-24 * np.abs(go) + 1e-10 * scale)
+    # the walls are zero
+    assert not host(g[0])[:, :, [0, -1]].any() and not host(g[1])[:, [0, -1], :].any()
+    assert not host(g[2])[[0, -1]].any()
 
 
 def test_autograd_function_and_finite_differences_64cubed():
