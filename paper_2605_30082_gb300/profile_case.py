@@ -1,5 +1,5 @@
 """A small solve for kernel profiling:
-python -m paper_2605_30082_gb300.profile_case NX NY NZ [PRECISION [INNER [CYCLES [FUSED]]]]
+python -m paper_2605_30082_gb300.profile_case NX NY NZ [PRECISION [INNER [CYCLES [FUSED [RTOL]]]]]
 
 Random density in [1.2, 998] and random right-hand side (torch generators, seeds 3 and 4),
 `CYCLES` V-cycles (default 2) of the given precision ('fp64', 'mixed', 'mixed_df'), followed by
@@ -8,7 +8,8 @@ one adjoint solve of as many cycles, one velocity correction of random face velo
 fractions).  Sized by the caller so that every array is larger than L2 while the whole case
 holds a few GB: e.g. 512 512 256 keeps the 512-cell rows (and so the launch configuration) of
 the 512^3 workload at half its cells.  FUSED = 1 smooths the finest level with fused red-black
-sweeps (mg_opts.fused_sweeps).
+sweeps (mg_opts.fused_sweeps).  RTOL (default 1e-30: the cycle limit ends both solves) set to a
+reachable tolerance lets the adjoint converge, so that its fused gradient kernel runs too.
 """
 import sys
 
@@ -24,11 +25,12 @@ def main(argv):
     inner = int(argv[4]) if len(argv) > 4 else 1
     cycles = int(argv[5]) if len(argv) > 5 else 2
     fused = len(argv) > 6 and argv[6] == "1"
+    rtol = float(argv[7]) if len(argv) > 7 else 1e-30
     dev = torch.device("cuda")
     g = torch.Generator(device="cuda")
     rho = 1.2 + 996.8 * torch.rand((nz, ny, nx), generator=g.manual_seed(3), device=dev, dtype=torch.float64)
     b = torch.randn((nz, ny, nx), generator=g.manual_seed(4), device=dev, dtype=torch.float64)
-    s = Solver((nx, ny, nz), h=1.0 / max(nx, ny, nz), precision=prec, coarsest=8, rtol=1e-30,
+    s = Solver((nx, ny, nz), h=1.0 / max(nx, ny, nz), precision=prec, coarsest=8, rtol=rtol,
                max_cycles=cycles, inner_cycles=inner if prec != "fp64" else 1, fused_sweeps=fused)
     s.set_density(rho)
     p = s.solve(b, raise_on_nonconvergence=False)

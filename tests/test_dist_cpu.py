@@ -67,19 +67,19 @@ def test_cpulist_parsing():
     assert bench.parse_cpulist("") == set()
 
 
-def test_roofline_kernels_have_a_traffic_row():
-    """bench.py fills `traffic` from profiles/traffic.md by kernel name: every kernel its
-    roofline lines name has a row there, scaled by the cell count."""
+def test_roofline_kernels_have_a_traffic_figure():
+    """bench.py fills `traffic` from its table of ncu DRAM bytes per cell by kernel name: every
+    kernel its roofline lines name has a figure there, scaled by the cell count."""
     sys.path.insert(0, ROOT)
     import re
 
     import bench
 
     src = open(os.path.join(ROOT, "bench.py")).read()
-    names = re.findall(r'_traffic_from_profiles\("([A-Za-z0-9_]+)"', src)
+    names = re.findall(r'_traffic\("([A-Za-z0-9_]+)"', src)
     assert names, "no roofline kernel named"
     for k in names:
-        per_cell = bench._traffic_from_profiles(k, 1000)
-        assert per_cell is not None, k
-        assert 1000 <= per_cell <= 1000 * 200, (k, per_cell)  # 1 to 200 bytes per cell
-    assert bench._traffic_from_profiles("no_such_kernel", 1000) is None
+        per_launch = bench._traffic(k, 1000)
+        assert per_launch is not None, k
+        assert 1000 <= per_launch <= 1000 * 200, (k, per_launch)  # 1 to 200 bytes per cell
+    assert bench._traffic("no_such_kernel", 1000) is None
