@@ -453,32 +453,22 @@ __global__ void k_adjoint_grad(Dims d, float ih, float ih2, double ihd, const do
 // the result is within about one FP32 unit of the exact difference plus an absolute 2^-45
 // max(|a|, |b|) (the pair holds 47 bits of the 53).  For the FP32 face gradients that is far
 // below their own rounding wherever a - b is not itself within 2^-20 of a's magnitude.
-// |v| below 2^-126 gives 0 (an absolute error under 2^-126); non-finite or |v| >= 2^128 gives
-// hi = +-inf or NaN.
+// |v| below 2^-126 gives 0 (an absolute error under 2^-126); |v| >= 2^128, infinity and NaN
+// give hi = +-inf, so that a non-finite input still gives a non-finite gradient.
 __device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
+    // branch-free: the FP32 exponent of v is (e - 896) mod 256 = (e & 0xff) ^ 0x80 for the
+    // biased FP64 exponent e in [897, 1150]; outside that range selects give 0 or +-inf/NaN
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const unsigned h32 = (unsigned)(u >> 32);
+    const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+    const unsigned e = (h32 >> 20) & 0x7ffu;
     const unsigned sign = h32 & 0x80000000u;
-    const int e = (int)((h32 >> 20) & 0x7ffu);
-    const int e32 = e - 896;  // biased FP32 exponent of v: e - 1023 + 127
-    if (e32 <= 0) {
-        hi = __uint_as_float(sign);
-        lo = 0.f;
-        return;
-    }
-    if (e32 >= 255) {
-        hi = __uint_as_float(sign | 0x7f800000u | ((e == 0x7ff && (u << 12) != 0ull) ? 0x400000u : 0u));
-        lo = 0.f;
-        return;
-    }
-    hi = __uint_as_float(sign | ((unsigned)e32 << 23) | (unsigned)((u >> 29) & 0x7fffffu));
-    const int el = e - 919;  // biased FP32 exponent of 2^(e - 1046)
-    if (el <= 0) {
-        lo = 0.f;
-        return;
-    }
-    const unsigned base = sign | ((unsigned)el << 23);
-    lo = __uint_as_float(base | (unsigned)((u >> 6) & 0x7fffffu)) - __uint_as_float(base);
+    unsigned hb = (((h32 << 3) & 0x7ffffff8u) ^ 0x40000000u) | sign | (l32 >> 29);
+    if (e - 897u > 253u) hb = e < 897u ? sign : (sign | 0x7f800000u);  // 0, or +-inf (also for NaN)
+    hi = __uint_as_float(hb);
+    // lo: 2^E with the dropped bits as its fraction, minus 2^E, E = hi's exponent - 23 (e >= 920)
+    const unsigned base = (hb & 0xff800000u) - 0x0b800000u;
+    const float l = __uint_as_float(base | ((l32 >> 6) & 0x7fffffu)) - __uint_as_float(base);
+    lo = (e - 920u <= 230u) ? l : 0.f;
 }
 
 // dL/dbeta_f = -(lam_L - lam_R)(p_L - p_R)/h^2 on every interior face, FP32, with the
@@ -552,18 +542,17 @@ __global__ void __launch_bounds__(32 * kGradRows) k_adjoint_grad_split(
 }
 
 // The same for even nx, two cells per thread: 16-byte loads of lam and p (both 16-byte
-// aligned, as the ABI requires), and the next plane's four loads issued before the current
-// plane is computed.  Block (32, kGrad2Rows): a warp covers 64 cells of a row.
+// aligned, as the ABI requires), the next plane's loads issued before the current plane is
+// computed, and the y-1 row's pairs taken from shared memory, where the warp of that row put
+// them (one barrier per plane, double-buffered by plane parity); only each block's first row
+// loads and splits its y-1 row itself.  Block (32, kGrad2Rows): a warp covers 64 cells of a row.
 constexpr int kGrad2Rows = 16, kGrad2Planes = 32;
 
-struct Pair4 {
-    float h0, l0, h1, l1;  // split of cells x and x + 1
-};
-__device__ __forceinline__ Pair4 split2(double2 v) {
-    Pair4 r;
-    split_f64(v.x, r.h0, r.l0);
-    split_f64(v.y, r.h1, r.l1);
-    return r;
+__device__ __forceinline__ float4 split2(double2 v) {
+    float4 r;
+    split_f64(v.x, r.x, r.y);
+    split_f64(v.y, r.z, r.w);
+    return r;  // (hi, lo) of cell x, then of cell x + 1
 }
 // -(la - lb)(pa - pb) ih2 from the split pairs
 __device__ __forceinline__ float grad_face(float lah, float lal, float lbh, float lbl, float pah, float pal,
@@ -574,68 +563,80 @@ __device__ __forceinline__ float grad_face(float lah, float lal, float lbh, floa
 __global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
     int nx, int ny, int nz, float ih2, const double *__restrict__ lam, const double *__restrict__ p,
     float *__restrict__ gx, float *__restrict__ gy, float *__restrict__ gz) {
-    const int lane = threadIdx.x;
+    __shared__ float4 sl[2][kGrad2Rows][32], sp[2][kGrad2Rows][32];
+    const int lane = threadIdx.x, ty = threadIdx.y;
     const int x = 2 * (blockIdx.x * 32 + lane);
-    const int y = blockIdx.y * kGrad2Rows + threadIdx.y;
+    const int y = blockIdx.y * kGrad2Rows + ty;
     const int z0 = blockIdx.z * kGrad2Planes;
     const int z1 = min(z0 + kGrad2Planes, nz);
     const bool act = x < nx && y < ny;  // nx even: x + 1 < nx too
-    const bool hy = act && y > 0;
+    const bool ownrow = act && y > 0 && ty == 0;  // loads its y-1 row from global memory
     const int nxy = nx * ny;
     const double2 zero2 = make_double2(0.0, 0.0);
-    Pair4 lz{0.f, 0.f, 0.f, 0.f}, pz{0.f, 0.f, 0.f, 0.f};  // plane z - 1
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 lz = zero4, pz = zero4;  // plane z - 1
     if (act && z0 > 0) {
         const int c = (z0 - 1) * nxy + y * nx + x;
         lz = split2(*reinterpret_cast<const double2 *>(lam + c));
         pz = split2(*reinterpret_cast<const double2 *>(p + c));
     }
-    // loads of the first plane
     double2 Lc = zero2, Pc = zero2, Ly = zero2, Py = zero2;
-    {
+    if (z0 < z1) {
         const int c = z0 * nxy + y * nx + x;
-        if (act && z0 < z1) {
+        if (act) {
             Lc = *reinterpret_cast<const double2 *>(lam + c);
             Pc = *reinterpret_cast<const double2 *>(p + c);
         }
-        if (hy && z0 < z1) {
+        if (ownrow) {
             Ly = *reinterpret_cast<const double2 *>(lam + c - nx);
             Py = *reinterpret_cast<const double2 *>(p + c - nx);
         }
     }
     for (int z = z0; z < z1; ++z) {
         const int c = z * nxy + y * nx + x;
-        // the next plane's loads, in flight while this plane computes
+        const int buf = z & 1;
         double2 Ln = zero2, Pn = zero2, Lyn = zero2, Pyn = zero2;
         if (z + 1 < z1) {
             if (act) {
                 Ln = *reinterpret_cast<const double2 *>(lam + c + nxy);
                 Pn = *reinterpret_cast<const double2 *>(p + c + nxy);
             }
-            if (hy) {
+            if (ownrow) {
                 Lyn = *reinterpret_cast<const double2 *>(lam + c + nxy - nx);
                 Pyn = *reinterpret_cast<const double2 *>(p + c + nxy - nx);
             }
         }
-        const Pair4 l = split2(Lc), q = split2(Pc);
+        const float4 l = split2(Lc), q = split2(Pc);
+        sl[buf][ty][lane] = l;
+        sp[buf][ty][lane] = q;
+        float4 ly = zero4, py = zero4;
+        if (ownrow) {
+            ly = split2(Ly);
+            py = split2(Py);
+        }
+        __syncthreads();  // buffer `buf` was last read two planes ago, before the previous barrier
+        if (ty > 0) {
+            ly = sl[buf][ty - 1][lane];
+            py = sp[buf][ty - 1][lane];
+        }
         // cell x - 1 is the second cell of the lane to the left (lane 0 loads it)
-        float lxh = __shfl_up_sync(0xffffffffu, l.h1, 1), lxl = __shfl_up_sync(0xffffffffu, l.l1, 1);
-        float pxh = __shfl_up_sync(0xffffffffu, q.h1, 1), pxl = __shfl_up_sync(0xffffffffu, q.l1, 1);
+        float lxh = __shfl_up_sync(0xffffffffu, l.z, 1), lxl = __shfl_up_sync(0xffffffffu, l.w, 1);
+        float pxh = __shfl_up_sync(0xffffffffu, q.z, 1), pxl = __shfl_up_sync(0xffffffffu, q.w, 1);
         if (act) {
             if (lane == 0 && x > 0) {
                 split_f64(lam[c - 1], lxh, lxl);
                 split_f64(p[c - 1], pxh, pxl);
             }
-            float a0 = 0.f, a1, b0 = 0.f, b1 = 0.f, e0 = 0.f, e1 = 0.f;
-            if (x > 0) a0 = grad_face(lxh, lxl, l.h0, l.l0, pxh, pxl, q.h0, q.l0, ih2);
-            a1 = grad_face(l.h0, l.l0, l.h1, l.l1, q.h0, q.l0, q.h1, q.l1, ih2);
+            float a0 = 0.f, b0 = 0.f, b1 = 0.f, e0 = 0.f, e1 = 0.f;
+            if (x > 0) a0 = grad_face(lxh, lxl, l.x, l.y, pxh, pxl, q.x, q.y, ih2);
+            const float a1 = grad_face(l.x, l.y, l.z, l.w, q.x, q.y, q.z, q.w, ih2);
             if (y > 0) {
-                const Pair4 ly = split2(Ly), py = split2(Py);
-                b0 = grad_face(ly.h0, ly.l0, l.h0, l.l0, py.h0, py.l0, q.h0, q.l0, ih2);
-                b1 = grad_face(ly.h1, ly.l1, l.h1, l.l1, py.h1, py.l1, q.h1, q.l1, ih2);
+                b0 = grad_face(ly.x, ly.y, l.x, l.y, py.x, py.y, q.x, q.y, ih2);
+                b1 = grad_face(ly.z, ly.w, l.z, l.w, py.z, py.w, q.z, q.w, ih2);
             }
             if (z > 0) {
-                e0 = grad_face(lz.h0, lz.l0, l.h0, l.l0, pz.h0, pz.l0, q.h0, q.l0, ih2);
-                e1 = grad_face(lz.h1, lz.l1, l.h1, l.l1, pz.h1, pz.l1, q.h1, q.l1, ih2);
+                e0 = grad_face(lz.x, lz.y, l.x, l.y, pz.x, pz.y, q.x, q.y, ih2);
+                e1 = grad_face(lz.z, lz.w, l.z, l.w, pz.z, pz.w, q.z, q.w, ih2);
             }
             const int row = z * ny + y;
             const int ax = row * (nx + 1) + x;          // x faces: (nz, ny, nx + 1), not 8-byte aligned
