@@ -340,6 +340,53 @@ int mg_debug_inject(mg_handle *h, int faults);
  * MG_ERR_ARG for a null sink/tflops or non-positive sizes; MG_ERR_CUDA if a launch fails. */
 int mg_fp64_fma_rate(void *stream, double *sink, int blocks, int iters, double *tflops, double *ms);
 
+/* ---- domain decomposition in z slabs -------------------------------------------------------
+ * The decomposition of the paper's MPI runs (§4.1; the multigrid level switches named as a
+ * scaling cost in §4.3.2) for the FP64 V-cycle, with every rank's slab held as its own buffers
+ * on the current GPU.  Level l of the hierarchy (the levels of mg_create) is cut into `ranks`
+ * slabs of planes[l] = nz_l / ranks planes along z while it is not the coarsest level and every
+ * slab keeps an even number (>= 2) of planes (so that each restriction pair stays inside one
+ * slab), for at most max_decomposed levels (0: as many as allowed).  A slab holds its own
+ * planes plus one ghost plane of x below and above; after every red or black half sweep and
+ * after the prolongation the neighbours' boundary planes are copied into the ghost planes
+ * (the halo exchange).  From switch_level on the hierarchy is held whole by one rank: the
+ * last decomposed level's restriction writes every slab's coarse planes into one array (the
+ * gather), a whole-grid handle runs the rest of the V-cycle, and each slab's prolongation
+ * reads its coarse planes and their neighbours from there.  The norm and the mean of p are
+ * sums of per-slab partial sums.  One V-cycle gives bitwise the whole-grid FP64 V-cycle.
+ * Arrays passed in and out are whole-grid device arrays (cell layout above). */
+#define MG_DD_MAX_RANKS 64
+typedef struct mg_dd mg_dd;
+typedef struct {
+    int ranks;                      /* slabs */
+    int levels;                     /* levels of the hierarchy (as mg_num_levels) */
+    int switch_level;               /* first level held whole; levels below are cut (>= 1) */
+    int nx[MG_MAX_LEVELS], ny[MG_MAX_LEVELS], nz[MG_MAX_LEVELS];  /* whole-grid dims per level */
+    int planes[MG_MAX_LEVELS];      /* planes per slab on the cut levels, 0 from switch_level */
+} mg_dd_plan;
+
+/* The plan alone (host only, no GPU): MG_ERR_ARG if level 0 cannot be cut (nz not a multiple
+ * of 2 * ranks, a single level, bad sizes).  Rank r owns planes [r planes[l], (r+1) planes[l])
+ * of level l; its neighbours are r - 1 and r + 1. */
+int mg_dd_make_plan(int nx, int ny, int nz, int coarsest, int ranks, int max_decomposed, mg_dd_plan *plan);
+
+/* Create a decomposed FP64 solver (opts: precision MG_FP64, method MG_METHOD_VCYCLE,
+ * inner_cycles 1, warm_start 0; other fields as for mg_create).  Allocates every slab's
+ * buffers and the whole-grid handle of the switch level on the current device. */
+int mg_dd_create(const mg_opts *opts, int ranks, int max_decomposed, void *stream, mg_dd **out);
+int mg_dd_destroy(mg_dd *dd);
+const char *mg_dd_last_error(const mg_dd *dd);
+int mg_dd_get_plan(const mg_dd *dd, mg_dd_plan *plan);
+/* Halo exchanges of one V-cycle and the bytes they copy between slabs. */
+int mg_dd_traffic(const mg_dd *dd, long long *exchanges, long long *halo_bytes);
+/* Operator from a whole-grid density (as mg_set_density); each slab takes its faces, the
+ * coarse slabs are coarsened slab by slab.  Synchronises. */
+int mg_dd_set_density(mg_dd *dd, const double *rho);
+/* One V-cycle for A x = b (b as given, no mean removed), x in place.  Synchronises. */
+int mg_dd_vcycle(mg_dd *dd, const double *b, double *x);
+/* As mg_solve in MG_FP64: zero-mean p with A p = b - mean(b) to opts.rtol, from p = 0. */
+int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *stats);
+
 /* ---- allocation-free entry point ----------------------------------------------------
  * The paper has no counterpart to this call.  It exists for callers that cannot
  * allocate device memory when they need a solve: programs whose device memory

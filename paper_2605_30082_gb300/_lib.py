@@ -53,6 +53,15 @@ class mg_stats(C.Structure):
         return list(self.relres_hist[: min(self.outer + 1, MG_HIST_LEN)])
 
 
+MG_DD_MAX_RANKS = 64
+
+
+class mg_dd_plan(C.Structure):
+    _fields_ = [("ranks", C.c_int), ("levels", C.c_int), ("switch_level", C.c_int),
+                ("nx", C.c_int * MG_MAX_LEVELS), ("ny", C.c_int * MG_MAX_LEVELS), ("nz", C.c_int * MG_MAX_LEVELS),
+                ("planes", C.c_int * MG_MAX_LEVELS)]
+
+
 _lib = None
 
 # every exported symbol with (restype, argtypes)
@@ -88,6 +97,15 @@ SIGNATURES = {
     "mg_dense_solve_noalloc": (_i, [_i, _i, _i, _d, _v, _v, _v, _v, _v, _v]),
     "mg_fp64_fma_rate": (_i, [_v, _v, _i, _i, C.POINTER(_d), C.POINTER(_d)]),
     "mg_debug_inject": (_i, [_v, _i]),
+    "mg_dd_make_plan": (_i, [_i, _i, _i, _i, _i, _i, C.POINTER(mg_dd_plan)]),
+    "mg_dd_create": (_i, [C.POINTER(mg_opts), _i, _i, _v, C.POINTER(_v)]),
+    "mg_dd_destroy": (_i, [_v]),
+    "mg_dd_last_error": (C.c_char_p, [_v]),
+    "mg_dd_get_plan": (_i, [_v, C.POINTER(mg_dd_plan)]),
+    "mg_dd_traffic": (_i, [_v, C.POINTER(_ll), C.POINTER(_ll)]),
+    "mg_dd_set_density": (_i, [_v, _v]),
+    "mg_dd_vcycle": (_i, [_v, _v, _v]),
+    "mg_dd_solve": (_i, [_v, _v, _v, C.POINTER(mg_stats)]),
 }
 
 
@@ -376,3 +394,60 @@ def mg_fp64_fma_rate(sink, iters, stream=None):
     st = lib().mg_fp64_fma_rate(C.c_void_p(stream.cuda_stream), _dev(sink, name="sink"), int(sink.numel()),
                                 int(iters), C.byref(tf), C.byref(ms))
     return st, tf.value, ms.value
+
+
+# ---- domain decomposition (z slabs held on one GPU) ----------------------------------------
+
+def mg_dd_make_plan(dims, coarsest, ranks, max_decomposed=0):
+    """Host only: returns (status, mg_dd_plan)."""
+    nx, ny, nz = dims
+    pl = mg_dd_plan()
+    st = lib().mg_dd_make_plan(int(nx), int(ny), int(nz), int(coarsest), int(ranks), int(max_decomposed),
+                               C.byref(pl))
+    return st, pl
+
+
+def mg_dd_create(opts: mg_opts, ranks, max_decomposed=0, stream=None):
+    """Returns (status, dd handle)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = C.c_void_p()
+    st = lib().mg_dd_create(C.byref(opts), int(ranks), int(max_decomposed), C.c_void_p(stream.cuda_stream),
+                            C.byref(h))
+    return st, h
+
+
+def mg_dd_destroy(dd):
+    return lib().mg_dd_destroy(dd)
+
+
+def mg_dd_last_error(dd) -> str:
+    s = lib().mg_dd_last_error(dd)
+    return s.decode() if s else ""
+
+
+def mg_dd_get_plan(dd):
+    pl = mg_dd_plan()
+    st = lib().mg_dd_get_plan(dd, C.byref(pl))
+    return st, pl
+
+
+def mg_dd_traffic(dd):
+    ex, by = C.c_longlong(0), C.c_longlong(0)
+    st = lib().mg_dd_traffic(dd, C.byref(ex), C.byref(by))
+    return st, ex.value, by.value
+
+
+def mg_dd_set_density(dd, rho, dims):
+    return lib().mg_dd_set_density(dd, _dev(rho, shape=cell_shape(dims), name="rho"))
+
+
+def mg_dd_vcycle(dd, b, x, dims):
+    cs = cell_shape(dims)
+    return lib().mg_dd_vcycle(dd, _dev(b, shape=cs, name="b"), _dev(x, shape=cs, name="x"))
+
+
+def mg_dd_solve(dd, b, p, dims, stats: mg_stats | None = None):
+    cs = cell_shape(dims)
+    return lib().mg_dd_solve(dd, _dev(b, shape=cs, name="b"), _dev(p, shape=cs, name="p"),
+                             C.byref(stats) if stats is not None else None)

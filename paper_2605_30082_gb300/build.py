@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libmgpoisson.so")
-SOURCES = ["mg_api.cu", "kernels_setup.cu", "kernels_cycle.cu", "kernels_reduce.cu", "kernels_split.cu", "kernels_df.cu", "kernels_cg.cu", "kernels_project.cu", "kernels_fused.cu", "kernels_peak.cu", "mg_noalloc.cu"]
+SOURCES = ["mg_api.cu", "kernels_setup.cu", "kernels_cycle.cu", "kernels_reduce.cu", "kernels_split.cu", "kernels_df.cu", "kernels_cg.cu", "kernels_project.cu", "kernels_fused.cu", "kernels_peak.cu", "mg_dd.cu", "mg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -36,8 +36,8 @@ __device__ __forceinline__ T nb_sum(const Dims &d, int i, int j, int k, i64 c, c
     if (i < d.nx - 1) s += cf.fx[c + 1] * x[c + 1];
     if (j > 0) s += cf.fy[c] * x[c - d.nx];
     if (j < d.ny - 1) s += cf.fy[c + d.nx] * x[c + d.nx];
-    if (k > 0) s += cf.fz[c] * x[c - d.nxy];
-    if (k < d.nz - 1) s += cf.fz[c + d.nxy] * x[c + d.nxy];
+    if (k > 0 || d.zlo) s += cf.fz[c] * x[c - d.nxy];
+    if (k < d.nz - 1 || d.zhi) s += cf.fz[c + d.nxy] * x[c + d.nxy];
     return s;
 }
 
@@ -51,8 +51,8 @@ __device__ __forceinline__ T flux_sum(const Dims &d, int i, int j, int k, i64 c,
     if (i < d.nx - 1) s += cf.fx[c + 1] * (xc - x[c + 1]);
     if (j > 0) s += cf.fy[c] * (xc - x[c - d.nx]);
     if (j < d.ny - 1) s += cf.fy[c + d.nx] * (xc - x[c + d.nx]);
-    if (k > 0) s += cf.fz[c] * (xc - x[c - d.nxy]);
-    if (k < d.nz - 1) s += cf.fz[c + d.nxy] * (xc - x[c + d.nxy]);
+    if (k > 0 || d.zlo) s += cf.fz[c] * (xc - x[c - d.nxy]);
+    if (k < d.nz - 1 || d.zhi) s += cf.fz[c + d.nxy] * (xc - x[c + d.nxy]);
     return s;
 }
 
@@ -135,7 +135,7 @@ __global__ void k_prolong(Dims cd, Dims f, const T *__restrict__ ec, T *e, int k
         int K2 = (k & 1) ? K + 1 : K - 1;
         if (I2 < 0 || I2 >= cd.nx) I2 = I;
         if (J2 < 0 || J2 >= cd.ny) J2 = J;
-        if (K2 < 0 || K2 >= cd.nz) K2 = K;
+        if ((K2 < 0 && !cd.zlo) || (K2 >= cd.nz && !cd.zhi)) K2 = K;  // a slab's ghost plane counts
         const T w[2] = {T(0.75), T(0.25)};
         int Ii[2] = {I, I2}, Jj[2] = {J, J2}, Kk[2] = {K, K2};
         v = T(0);
@@ -174,8 +174,8 @@ __global__ void k_rr_red_diag64(Dims f, Dims cd, double h2, double ih2_8, Coef<d
             if (i < f.nx - 1) a = fma(cf.fx[c + 1], x[c + 1], a);
             if (j > 0) a = fma(cf.fy[c], x[c - f.nx], a);
             if (j < f.ny - 1) a = fma(cf.fy[c + f.nx], x[c + f.nx], a);
-            if (k > 0) a = fma(cf.fz[c], x[c - f.nxy], a);
-            if (k < f.nz - 1) a = fma(cf.fz[c + f.nxy], x[c + f.nxy], a);
+            if (k > 0 || f.zlo) a = fma(cf.fz[c], x[c - f.nxy], a);
+            if (k < f.nz - 1 || f.zhi) a = fma(cf.fz[c + f.nxy], x[c + f.nxy], a);
             s += fma(-dg[c], x[c], a);
         }
         bc[(i64)cr * cd.nx + I] = s * ih2_8;
@@ -202,7 +202,7 @@ __global__ void k_prolong_col(Dims cd, Dims f, const T *__restrict__ ec, T *e, i
             int K2 = (k & 1) ? K + 1 : K - 1;
             if (I2 < 0 || I2 >= cd.nx) I2 = I;
             if (J2 < 0 || J2 >= cd.ny) J2 = J;
-            if (K2 < 0 || K2 >= cd.nz) K2 = K;
+            if ((K2 < 0 && !cd.zlo) || (K2 >= cd.nz && !cd.zhi)) K2 = K;  // a slab's ghost plane counts
             const T w[2] = {T(0.75), T(0.25)};
             const int Ii[2] = {I, I2}, Jj[2] = {J, J2}, Kk[2] = {K, K2};
             v = T(0);

@@ -128,7 +128,7 @@ __global__ void k_invdiag(Dims d, const double *__restrict__ fx, const double *_
     s += fy[c];
     if (j < d.ny - 1) s += fy[c + d.nx];
     s += fz[c];
-    if (k < d.nz - 1) s += fz[c + d.nxy];
+    if (k < d.nz - 1 || d.zhi) s += fz[c + d.nxy];  // a slab's face to its ghost plane counts
     if (invd64) invd64[c] = recip64(s);
     if (diag) diag[c] = s;
 }

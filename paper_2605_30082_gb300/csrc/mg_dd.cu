@@ -1,0 +1,530 @@
+// Domain-decomposed FP64 multigrid solve: z slabs with ghost planes (mg_dd_* in include/mg.h).
+//
+// The paper's solver runs one MPI rank per domain and names the switch between multigrid
+// levels as a cost of its scaling (§4.1, §4.3.2).  This file is that decomposition for the
+// FP64 V-cycle of this library, with the ranks held as separate slab buffers on one GPU:
+//   - level l is cut into `ranks` slabs of planes[l] planes along z; a slab stores its own
+//     planes and one ghost plane below and above for x, and its z faces up to the face to the
+//     ghost above, so that the faces between slabs act as interior faces (Dims.zlo / zhi);
+//   - every red or black half sweep, and the prolongation, is followed by a halo exchange:
+//     each slab's first and last own planes are copied into its neighbours' ghost planes;
+//   - the red-only residual + restriction of the last decomposed level writes each slab's
+//     coarse planes into one whole-grid array (the gather of the coarse levels onto one rank),
+//     where a whole-grid handle runs the rest of the V-cycle through the FP64 components; the
+//     prolongation back reads each slab's coarse planes and their neighbours from that array;
+//   - the residual norm and the mean of p are sums of per-slab partial sums, added on the
+//     host in slab order (the all-reduce).
+// Every cell sees the same arithmetic, in the same order, as in the whole-grid FP64 V-cycle,
+// so one V-cycle gives bitwise the same result for any number of slabs.  The exchange is a
+// device-to-device copy here; between GPUs it would be one send/receive per neighbour.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mg_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// one slab of one decomposed level
+struct Slab {
+    mg::Dims d;      // own planes (nz = planes), zlo / zhi when a neighbour exists below / above
+    int z0;          // first whole-grid plane of the slab
+    double *xe;      // x with a ghost plane below and above: planes + 2 planes
+    double *x;       // = xe + nxy, the first own plane
+    double *b, *r;   // own planes
+    double *fx, *fy; // low faces of the own planes
+    double *fze;     // low z faces of the own planes and of the ghost above: planes + 1 planes
+    double *invd, *dg;
+};
+
+__global__ void k_sub_scalar(mg::i64 n, const double *__restrict__ in, double c, double *out) {
+    const mg::i64 m = (mg::i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) out[m] = in[m] - c;
+}
+
+// the coarse low z faces of one plane from the 2 x 2 fine faces that tile them
+__global__ void k_coarsen_z_plane(mg::Dims f, mg::Dims c, const double *__restrict__ ffz_plane,
+                                  double *cfz_plane) {
+    const int C = blockIdx.x * blockDim.x + threadIdx.x;
+    if (C >= c.nx * c.ny) return;
+    const int I = C % c.nx, J = C / c.nx;
+    const mg::i64 base = (mg::i64)(2 * J) * f.nx + 2 * I;
+    double sz = 0.0;
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) sz += ffz_plane[base + b * f.nx + a];
+    cfz_plane[C] = sz / 4.0;
+}
+
+inline unsigned blocks_for(mg::i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+struct mg_dd {
+    mg_opts o;
+    mg_dd_plan plan;
+    cudaStream_t s;
+    int P, ndec;
+    std::vector<std::vector<Slab>> lv;  // [level < ndec][rank]
+    mg_handle *ch;                       // whole grid from the switch level down
+    int ch_nlev;
+    double *cx[MG_MAX_LEVELS], *cb[MG_MAX_LEVELS];
+    double *gfx, *gfy, *gfz, *sinv;      // set-up scratch: whole-grid level-0 low faces, 1/rho
+    double *abx, *aby, *abz;             // switch-level faces in the ABI layout
+    double *partials, *red;
+    unsigned *err;
+    std::vector<void *> allocs;
+    long long exchanges, halo_bytes;     // per V-cycle
+    int have_op;
+    char msg[256];
+};
+
+namespace {
+
+int dd_fail(mg_dd *dd, int code, const char *fmt, ...) {
+    if (dd) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(dd->msg, sizeof(dd->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define DD_CUDA(dd, call)                                                                        \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return dd_fail((dd), MG_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+mg::Coef<double> coef(const Slab &S) { return {S.fx, S.fy, S.fze, S.invd}; }
+
+// ghost planes of x on level l from the neighbouring slabs' first / last own planes
+int exchange(mg_dd *dd, int l) {
+    std::vector<Slab> &R = dd->lv[l];
+    const size_t bytes = sizeof(double) * (size_t)R[0].d.nxy;
+    for (int r = 0; r < dd->P; ++r) {
+        if (r > 0)
+            DD_CUDA(dd, cudaMemcpyAsync(R[r].xe, R[r - 1].x + (R[r - 1].d.nz - 1) * R[r - 1].d.nxy, bytes,
+                                        cudaMemcpyDeviceToDevice, dd->s));
+        if (r + 1 < dd->P)
+            DD_CUDA(dd, cudaMemcpyAsync(R[r].x + R[r].d.n, R[r + 1].x, bytes, cudaMemcpyDeviceToDevice, dd->s));
+    }
+    return MG_OK;
+}
+
+int smooth(mg_dd *dd, int l, int sweeps, int order) {
+    const double h2 = dd->o.h * dd->o.h * (double)(1ll << (2 * l));
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int half = 0; half < 2; ++half) {
+            for (Slab &S : dd->lv[l]) mg::launch_rbgs_half64(dd->s, S.d, h2, coef(S), S.b, S.x, order ? 1 - half : half);
+            int rc = exchange(dd, l);
+            if (rc) return rc;
+        }
+    return MG_OK;
+}
+
+// the whole-grid V-cycle tail (switch level down to the coarsest) from x = 0, by the FP64
+// components of the whole-grid handle
+int tail(mg_dd *dd, int k) {
+    if (k == dd->ch_nlev - 1) return mg_coarse_solve(dd->ch, MG_F64, dd->cb[k], dd->cx[k]);
+    int rc = mg_presmooth_restrict(dd->ch, k, MG_F64, dd->cx[k], dd->cb[k], dd->o.pre, 1, dd->cb[k + 1]);
+    if (rc) return rc;
+    rc = tail(dd, k + 1);
+    if (rc) return rc;
+    return mg_prolong_postsmooth(dd->ch, k, MG_F64, dd->cx[k + 1], dd->cx[k], dd->cb[k], dd->o.post);
+}
+
+// one V-cycle on decomposed level l (x from zero, or from the slabs' x with valid ghosts)
+int vcycle(mg_dd *dd, int l, bool x_zero) {
+    std::vector<Slab> &R = dd->lv[l];
+    const double h2 = dd->o.h * dd->o.h * (double)(1ll << (2 * l));
+    if (x_zero)
+        for (Slab &S : R) DD_CUDA(dd, cudaMemsetAsync(S.xe, 0, sizeof(double) * (size_t)(S.d.n + 2 * S.d.nxy), dd->s));
+    int rc = smooth(dd, l, dd->o.pre, 0);
+    if (rc) return rc;
+    const bool last = l + 1 == dd->ndec;
+    for (int r = 0; r < dd->P; ++r) {
+        Slab &S = R[r];
+        double *bc;
+        if (!last) {
+            bc = dd->lv[l + 1][r].b;
+        } else {
+            const mg::i64 cnxy = (mg::i64)(S.d.nx / 2) * (S.d.ny / 2);
+            bc = dd->cb[0] + (mg::i64)(S.z0 / 2) * cnxy;
+        }
+        // after a pre-smoothing sweep (black last) every black residual is zero
+        if (dd->o.pre > 0)
+            mg::launch_rr_red_diag64(dd->s, S.d, h2, coef(S), S.dg, S.b, S.x, bc);
+        else
+            mg::launch_resid_restrict<double>(dd->s, S.d, 1.0 / h2, coef(S), S.b, S.x, bc, false);
+    }
+    rc = last ? tail(dd, 0) : vcycle(dd, l + 1, true);
+    if (rc) return rc;
+    // prolongation: red cells only when a post sweep (black first) follows
+    for (int r = 0; r < dd->P; ++r) {
+        Slab &S = R[r];
+        mg::Dims cd;
+        const double *ec;
+        if (!last) {
+            cd = dd->lv[l + 1][r].d;
+            ec = dd->lv[l + 1][r].x;
+        } else {
+            cd = mg::make_dims(S.d.nx / 2, S.d.ny / 2, S.d.nz / 2);
+            cd.zlo = S.d.zlo;
+            cd.zhi = S.d.zhi;
+            ec = dd->cx[0] + (mg::i64)(S.z0 / 2) * cd.nxy;  // the neighbours' planes lie beside it
+        }
+        mg::launch_prolong<double>(dd->s, cd, ec, S.x, dd->o.prolong, dd->o.post > 0 ? 0 : -1);
+    }
+    rc = exchange(dd, l);
+    if (rc) return rc;
+    return smooth(dd, l, dd->o.post, 1);
+}
+
+// sums over the slabs' own planes of x (and of x^2), added in slab order
+int slab_sums(mg_dd *dd, int which, double *sum, double *sumsq) {
+    double a = 0.0, q = 0.0;
+    for (Slab &S : dd->lv[0]) {
+        const double *v = which == 0 ? S.x : (which == 1 ? S.r : S.b);
+        mg::launch_sum_sumsq<double>(dd->s, S.d.n, v, dd->partials, dd->red, sumsq != nullptr);
+        double h[2];
+        DD_CUDA(dd, cudaMemcpyAsync(h, dd->red, sizeof(h), cudaMemcpyDeviceToHost, dd->s));
+        DD_CUDA(dd, cudaStreamSynchronize(dd->s));
+        a += h[0];
+        q += h[1];
+    }
+    *sum = a;
+    if (sumsq) *sumsq = q;
+    return MG_OK;
+}
+
+void *dd_alloc(mg_dd *dd, size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    dd->allocs.push_back(p);
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_dd_make_plan(int nx, int ny, int nz, int coarsest, int ranks, int max_decomposed, mg_dd_plan *plan) {
+    if (!plan || nx < 1 || ny < 1 || nz < 1 || coarsest < 2 || ranks < 1 || ranks > MG_DD_MAX_RANKS ||
+        max_decomposed < 0)
+        return MG_ERR_ARG;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->ranks = ranks;
+    // the whole-grid hierarchy (the rule of mg_create)
+    int n = 0, x = nx, y = ny, z = nz;
+    for (;;) {
+        plan->nx[n] = x;
+        plan->ny[n] = y;
+        plan->nz[n] = z;
+        ++n;
+        const int mx = x > y ? (x > z ? x : z) : (y > z ? y : z);
+        if (x % 2 || y % 2 || z % 2 || mx <= coarsest || n == MG_MAX_LEVELS) break;
+        x /= 2;
+        y /= 2;
+        z /= 2;
+    }
+    plan->levels = n;
+    // level l is cut into slabs while it is not the coarsest, nz_l divides evenly and every
+    // slab has an even number (>= 2) of planes, so that its restriction pairs stay inside it
+    int s = 0;
+    while (s < n - 1 && (max_decomposed == 0 || s < max_decomposed) && plan->nz[s] % ranks == 0 &&
+           (plan->nz[s] / ranks) % 2 == 0 && plan->nz[s] / ranks >= 2) {
+        plan->planes[s] = plan->nz[s] / ranks;
+        ++s;
+    }
+    plan->switch_level = s;
+    return s >= 1 ? MG_OK : MG_ERR_ARG;
+}
+
+int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, mg_dd **out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (!o || o->precision != MG_FP64 || o->method != MG_METHOD_VCYCLE || o->inner_cycles != 1 ||
+        !(o->h > 0.0) || o->pre < 0 || o->post < 0 || o->max_cycles < 0 || o->warm_start)
+        return MG_ERR_ARG;
+    mg_dd *dd = new (std::nothrow) mg_dd();
+    if (!dd) return MG_ERR_OOM;
+    dd->o = *o;
+    dd->s = static_cast<cudaStream_t>(stream);
+    if (mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, max_decomposed, &dd->plan) != MG_OK) {
+        delete dd;
+        return MG_ERR_ARG;
+    }
+    dd->P = ranks;
+    dd->ndec = dd->plan.switch_level;
+    const mg_dd_plan &pl = dd->plan;
+    bool ok = true;
+    auto A = [&](size_t n_doubles) {
+        double *p = static_cast<double *>(dd_alloc(dd, 8 * n_doubles));
+        if (!p) ok = false;
+        return p;
+    };
+    dd->lv.resize(dd->ndec);
+    for (int l = 0; l < dd->ndec && ok; ++l) {
+        dd->lv[l].resize(ranks);
+        for (int r = 0; r < ranks && ok; ++r) {
+            Slab &S = dd->lv[l][r];
+            S.d = mg::make_dims(pl.nx[l], pl.ny[l], pl.planes[l]);
+            S.d.zlo = r > 0;
+            S.d.zhi = r + 1 < ranks;
+            S.z0 = r * pl.planes[l];
+            const size_t n = (size_t)S.d.n, nxy = (size_t)S.d.nxy;
+            S.xe = A(n + 2 * nxy);
+            S.x = S.xe ? S.xe + nxy : nullptr;
+            S.b = A(n);
+            S.r = A(n);
+            S.fx = A(n);
+            S.fy = A(n);
+            S.fze = A(n + nxy);
+            S.invd = A(n);
+            S.dg = A(n);
+        }
+    }
+    const mg::i64 n0 = (mg::i64)o->nx * o->ny * o->nz;
+    dd->gfx = A(n0);
+    dd->gfy = A(n0);
+    dd->gfz = A(n0);
+    dd->sinv = A(n0);
+    const int sl = dd->ndec;
+    const int snx = pl.nx[sl], sny = pl.ny[sl], snz = pl.nz[sl];
+    dd->abx = A((size_t)snz * sny * (snx + 1));
+    dd->aby = A((size_t)snz * (sny + 1) * snx);
+    dd->abz = A((size_t)(snz + 1) * sny * snx);
+    dd->partials = A(2 * (size_t)mg::reduce_blocks(n0));
+    dd->red = A(4);
+    dd->err = static_cast<unsigned *>(dd_alloc(dd, 256));
+    if (!ok || !dd->err) {
+        mg_dd_destroy(dd);
+        return MG_ERR_OOM;
+    }
+    // the whole-grid handle for the switch level and below
+    mg_opts co = *o;
+    co.nx = snx;
+    co.ny = sny;
+    co.nz = snz;
+    co.h = o->h * (double)(1ll << sl);
+    co.rtol = 0.0;
+    int rc = mg_create(&co, stream, &dd->ch);
+    if (rc != MG_OK) {
+        mg_dd_destroy(dd);
+        return rc;
+    }
+    dd->ch_nlev = mg_num_levels(dd->ch);
+    for (int k = 0; k < dd->ch_nlev && ok; ++k) {
+        int dims[3];
+        mg_level_dims(dd->ch, k, dims);
+        const size_t n = (size_t)dims[0] * dims[1] * dims[2];
+        dd->cx[k] = A(n);
+        dd->cb[k] = A(n);
+    }
+    if (!ok) {
+        mg_dd_destroy(dd);
+        return MG_ERR_OOM;
+    }
+    // halo traffic of one V-cycle: an exchange after every half sweep and after the prolongation
+    dd->exchanges = 0;
+    dd->halo_bytes = 0;
+    for (int l = 0; l < dd->ndec; ++l) {
+        const long long per = 2ll * (ranks - 1) * 8ll * pl.nx[l] * pl.ny[l];
+        const long long k = 2ll * o->pre + 2ll * o->post + 1;
+        dd->exchanges += k;
+        dd->halo_bytes += k * per;
+    }
+    *out = dd;
+    return MG_OK;
+}
+
+int mg_dd_destroy(mg_dd *dd) {
+    if (!dd) return MG_OK;
+    if (dd->s) cudaStreamSynchronize(dd->s);
+    if (dd->ch) mg_destroy(dd->ch);
+    for (void *p : dd->allocs) cudaFree(p);
+    cudaGetLastError();
+    delete dd;
+    return MG_OK;
+}
+
+const char *mg_dd_last_error(const mg_dd *dd) { return dd ? dd->msg : ""; }
+
+int mg_dd_get_plan(const mg_dd *dd, mg_dd_plan *plan) {
+    if (!dd || !plan) return MG_ERR_ARG;
+    *plan = dd->plan;
+    return MG_OK;
+}
+
+int mg_dd_traffic(const mg_dd *dd, long long *exchanges, long long *halo_bytes) {
+    if (!dd) return MG_ERR_ARG;
+    if (exchanges) *exchanges = dd->exchanges;
+    if (halo_bytes) *halo_bytes = dd->halo_bytes;
+    return MG_OK;
+}
+
+int mg_dd_set_density(mg_dd *dd, const double *rho) {
+    if (!dd) return MG_ERR_ARG;
+    if (!rho) return dd_fail(dd, MG_ERR_ARG, "rho is NULL");
+    dd->have_op = 0;
+    const mg_dd_plan &pl = dd->plan;
+    cudaStream_t s = dd->s;
+    mg::Dims g = mg::make_dims(dd->o.nx, dd->o.ny, dd->o.nz);
+    DD_CUDA(dd, cudaMemsetAsync(dd->err, 0, sizeof(unsigned), s));
+    mg::launch_faces_from_rho(s, g, rho, dd->sinv, dd->gfx, dd->gfy, dd->gfz, dd->err);
+    // level 0 slabs: their planes of the whole-grid faces; fze's last plane is the low face of
+    // the next slab's first plane (0 above the top slab: the wall)
+    for (int r = 0; r < dd->P; ++r) {
+        Slab &S = dd->lv[0][r];
+        const size_t off = (size_t)S.z0 * S.d.nxy, bytes = 8 * (size_t)S.d.n, pb = 8 * (size_t)S.d.nxy;
+        DD_CUDA(dd, cudaMemcpyAsync(S.fx, dd->gfx + off, bytes, cudaMemcpyDeviceToDevice, s));
+        DD_CUDA(dd, cudaMemcpyAsync(S.fy, dd->gfy + off, bytes, cudaMemcpyDeviceToDevice, s));
+        DD_CUDA(dd, cudaMemcpyAsync(S.fze, dd->gfz + off, bytes, cudaMemcpyDeviceToDevice, s));
+        if (S.d.zhi)
+            DD_CUDA(dd, cudaMemcpyAsync(S.fze + S.d.n, dd->gfz + off + S.d.n, pb, cudaMemcpyDeviceToDevice, s));
+        else
+            DD_CUDA(dd, cudaMemsetAsync(S.fze + S.d.n, 0, pb, s));
+    }
+    // decomposed levels: diagonal, then the next level's faces slab by slab
+    for (int l = 0; l < dd->ndec; ++l) {
+        for (int r = 0; r < dd->P; ++r) {
+            Slab &S = dd->lv[l][r];
+            mg::launch_invdiag(s, S.d, S.fx, S.fy, S.fze, S.invd, S.dg);
+            mg::Dims cd = mg::make_dims(S.d.nx / 2, S.d.ny / 2, S.d.nz / 2);
+            if (l + 1 < dd->ndec) {
+                Slab &C = dd->lv[l + 1][r];
+                mg::launch_coarsen(s, S.d, S.fx, S.fy, S.fze, C.fx, C.fy, C.fze);
+                // the face to the ghost above: from the fine faces to the fine ghost above
+                mg::count_launch();
+                k_coarsen_z_plane<<<blocks_for(cd.nxy), kThreads, 0, s>>>(S.d, cd, S.fze + S.d.n, C.fze + C.d.n);
+            } else {
+                // the switch level is whole: the slabs' coarse planes side by side
+                const mg::i64 off = (mg::i64)(S.z0 / 2) * cd.nxy;
+                mg::launch_coarsen(s, S.d, S.fx, S.fy, S.fze, dd->gfx + off, dd->gfy + off, dd->gfz + off);
+            }
+        }
+    }
+    DD_CUDA(dd, cudaGetLastError());
+    unsigned herr = 0;
+    DD_CUDA(dd, cudaMemcpyAsync(&herr, dd->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(dd, cudaStreamSynchronize(s));
+    if (herr) return dd_fail(dd, MG_ERR_DENSITY, "density must be finite and > 0 everywhere");
+    // the whole-grid handle takes the switch level's faces (ABI layout)
+    const int sl = dd->ndec;
+    mg::Dims sd = mg::make_dims(pl.nx[sl], pl.ny[sl], pl.nz[sl]);
+    mg::launch_faces_to_api(s, sd, dd->gfx, dd->gfy, dd->gfz, dd->abx, dd->aby, dd->abz);
+    int rc = mg_set_face_coeffs(dd->ch, dd->abx, dd->aby, dd->abz);
+    if (rc) return dd_fail(dd, rc, "switch level: %s", mg_last_error(dd->ch));
+    dd->have_op = 1;
+    return MG_OK;
+}
+
+int mg_dd_vcycle(mg_dd *dd, const double *b, double *x) {
+    if (!dd) return MG_ERR_ARG;
+    if (!b || !x) return dd_fail(dd, MG_ERR_ARG, "null array");
+    if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
+    cudaStream_t s = dd->s;
+    for (Slab &S : dd->lv[0]) {
+        const size_t off = (size_t)S.z0 * S.d.nxy, pb = 8 * (size_t)S.d.nxy;
+        DD_CUDA(dd, cudaMemcpyAsync(S.b, b + off, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
+        DD_CUDA(dd, cudaMemcpyAsync(S.x, x + off, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
+        if (S.d.zlo) DD_CUDA(dd, cudaMemcpyAsync(S.xe, x + off - S.d.nxy, pb, cudaMemcpyDeviceToDevice, s));
+        if (S.d.zhi) DD_CUDA(dd, cudaMemcpyAsync(S.x + S.d.n, x + off + S.d.n, pb, cudaMemcpyDeviceToDevice, s));
+    }
+    int rc = vcycle(dd, 0, false);
+    if (rc) return rc;
+    for (Slab &S : dd->lv[0])
+        DD_CUDA(dd, cudaMemcpyAsync(x + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
+    DD_CUDA(dd, cudaGetLastError());
+    DD_CUDA(dd, cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
+    if (!dd) return MG_ERR_ARG;
+    if (!b || !p) return dd_fail(dd, MG_ERR_ARG, "null array");
+    if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
+    cudaStream_t s = dd->s;
+    cudaEvent_t e0, e1;
+    DD_CUDA(dd, cudaEventCreate(&e0));
+    DD_CUDA(dd, cudaEventCreate(&e1));
+    DD_CUDA(dd, cudaEventRecord(e0, s));
+    const double n = (double)dd->o.nx * dd->o.ny * dd->o.nz;
+    // b~ = b - mean(b) slab by slab (the mean from the slabs' partial sums)
+    double sb = 0.0;
+    for (Slab &S : dd->lv[0]) {
+        mg::launch_sum_sumsq<double>(s, S.d.n, b + (size_t)S.z0 * S.d.nxy, dd->partials, dd->red, false);
+        double h[2];
+        DD_CUDA(dd, cudaMemcpyAsync(h, dd->red, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DD_CUDA(dd, cudaStreamSynchronize(s));
+        sb += h[0];
+    }
+    for (Slab &S : dd->lv[0]) {
+        mg::count_launch();
+        k_sub_scalar<<<blocks_for(S.d.n), kThreads, 0, s>>>(S.d.n, b + (size_t)S.z0 * S.d.nxy, sb / n, S.b);
+        DD_CUDA(dd, cudaMemsetAsync(S.xe, 0, 8 * (size_t)(S.d.n + 2 * S.d.nxy), s));
+    }
+    double t, nb2;
+    int rc = slab_sums(dd, 2, &t, &nb2);
+    if (rc) return rc;
+    const double nb = std::sqrt(nb2);
+    double hist[MG_HIST_LEN];
+    int hn = 0, cycles = 0, status = MG_ERR_NOT_CONVERGED;
+    double rr = nb > 0.0 ? 1.0 : 0.0;
+    hist[hn++] = rr;
+    if (nb == 0.0 || rr <= dd->o.rtol) status = MG_OK;
+    const double ih2 = 1.0 / (dd->o.h * dd->o.h);
+    while (status == MG_ERR_NOT_CONVERGED && cycles < dd->o.max_cycles) {
+        rc = vcycle(dd, 0, false);
+        if (rc) return rc;
+        for (Slab &S : dd->lv[0]) mg::launch_residual<double>(s, S.d, ih2, coef(S), S.b, S.x, S.r);
+        double sr, rn2, sp;
+        rc = slab_sums(dd, 1, &sr, &rn2);
+        if (rc) return rc;
+        rc = slab_sums(dd, 0, &sp, nullptr);
+        if (rc) return rc;
+        // zero mean, ghosts included (they hold the neighbours' planes, shifted alike)
+        for (Slab &S : dd->lv[0]) mg::launch_add_const(s, S.d.n + 2 * S.d.nxy, S.xe, -sp / n);
+        rr = std::sqrt(rn2) / nb;
+        ++cycles;
+        if (hn < MG_HIST_LEN) hist[hn++] = rr;
+        if (!std::isfinite(rr) || rr > 1e12) {
+            status = MG_ERR_DIVERGED;
+            break;
+        }
+        if (rr <= dd->o.rtol) status = MG_OK;
+    }
+    for (Slab &S : dd->lv[0])
+        DD_CUDA(dd, cudaMemcpyAsync(p + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
+    DD_CUDA(dd, cudaEventRecord(e1, s));
+    DD_CUDA(dd, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DD_CUDA(dd, cudaGetLastError());
+    if (st) {
+        st->status = status;
+        st->cycles = cycles;
+        st->outer = cycles;
+        st->relres = rr;
+        for (int q = 0; q < MG_HIST_LEN; ++q) st->relres_hist[q] = q < hn ? hist[q] : 0.0;
+        st->ms = ms;
+    }
+    if (status == MG_ERR_NOT_CONVERGED)
+        return dd_fail(dd, status, "not converged: relres %.3e after %d cycles", rr, cycles);
+    if (status == MG_ERR_DIVERGED) return dd_fail(dd, status, "diverged: relres %.3e", rr);
+    return MG_OK;
+}
+
+}  // extern "C"

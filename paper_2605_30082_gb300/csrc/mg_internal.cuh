@@ -20,6 +20,10 @@ typedef long long i64;
 struct Dims {
     int nx, ny, nz;
     i64 nxy, n;
+    // z slab of a domain-decomposed level (mg_dd.cu): a ghost plane below (zlo) or above (zhi)
+    // the nz own planes holds the neighbouring slab's values, so the faces between slabs count
+    // as interior; 0 on every whole-grid level (the walls)
+    int zlo, zhi;
 };
 
 inline Dims make_dims(int nx, int ny, int nz) {
@@ -29,6 +33,7 @@ inline Dims make_dims(int nx, int ny, int nz) {
     d.nz = nz;
     d.nxy = (i64)nx * ny;
     d.n = d.nxy * nz;
+    d.zlo = d.zhi = 0;
     return d;
 }
 

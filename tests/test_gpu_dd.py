@@ -1,0 +1,141 @@
+"""The slab-decomposed FP64 V-cycle (mg_dd_*) against the whole-grid one, on the GPU.
+
+Every cell of a slab sees the arithmetic of the whole-grid FP64 V-cycle in the same order (the
+ghost planes hold the neighbours' values, the faces between slabs count as interior), so one
+decomposed V-cycle must equal bitwise the whole-grid V-cycle assembled from the FP64 component
+entry points (mg_presmooth_restrict, mg_coarse_solve, mg_prolong_postsmooth), for 1 to 8 slabs,
+with the switch to the whole-grid levels at every allowed level, both prolongations and other
+sweep counts.  The decomposed solve differs from the whole-grid one only in the order of its
+norm and mean sums: same cycle count, p within 1e-12; and it reaches the oracle's exact
+discrete solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_30082_gb300 import Solver
+from paper_2605_30082_gb300 import _lib as L
+
+from _helpers import RHO_PHASE, dev, dropfilm_case, host, random_rho, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _opts(dims, h, coarsest=4, pre=2, post=2, prolong=L.MG_PROLONG_TRILINEAR, rtol=1e-10):
+    o = L.mg_default_opts()
+    o.nx, o.ny, o.nz = dims
+    o.h = h
+    o.precision = L.MG_FP64
+    o.coarsest, o.pre, o.post, o.prolong, o.rtol = coarsest, pre, post, prolong, rtol
+    o.max_cycles = 200
+    return o
+
+
+class DD:
+    def __init__(self, dims, ranks, max_dec=0, **kw):
+        self.dims = dims
+        st, self.h = L.mg_dd_create(_opts(dims, **kw), ranks, max_dec)
+        assert st == L.MG_OK, st
+        st, self.plan = L.mg_dd_get_plan(self.h)
+        assert st == L.MG_OK
+
+    def close(self):
+        L.mg_dd_destroy(self.h)
+
+
+def whole_vcycle(s, b, x):
+    """The whole-grid FP64 V-cycle from x, by the component entry points."""
+    nl = s.num_levels
+    B, X = [b], [x]
+    for l in range(1, nl):
+        nx, ny, nz = s.level_dims(l)
+        B.append(torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda"))
+        X.append(torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda"))
+
+    def cyc(l, zero):
+        if l == nl - 1:
+            assert L.mg_coarse_solve(s._h, B[l], X[l]) == L.MG_OK
+            return
+        assert L.mg_presmooth_restrict(s._h, l, X[l], B[l], s.opts.pre, B[l + 1], x_is_zero=zero) == L.MG_OK
+        cyc(l + 1, True)
+        assert L.mg_prolong_postsmooth(s._h, l, X[l + 1], X[l], B[l], s.opts.post) == L.MG_OK
+
+    cyc(0, False)
+
+
+CASES = [((64, 64, 64), 1, 0, {}), ((64, 64, 64), 2, 0, {}), ((64, 64, 64), 4, 0, {}),
+         ((64, 48, 128), 8, 0, {}), ((64, 48, 128), 8, 1, {}), ((64, 48, 128), 4, 2, {}),
+         ((64, 64, 32), 4, 0, {}), ((48, 40, 64), 4, 0, dict(prolong=L.MG_PROLONG_CONSTANT)),
+         ((48, 40, 64), 2, 0, dict(pre=1, post=3)), ((64, 32, 64), 2, 0, dict(pre=0, post=2, coarsest=8))]
+
+
+@pytest.mark.parametrize("dims,ranks,max_dec,kw", CASES)
+def test_dd_vcycle_is_bitwise_the_whole_grid_vcycle(dims, ranks, max_dec, kw):
+    nx, ny, nz = dims
+    h = 1.0 / max(dims)
+    rho = dev(random_rho(dims, 31))
+    o = _opts(dims, h, **kw)
+    s = Solver(dims, h=h, precision="fp64", coarsest=o.coarsest, pre=o.pre, post=o.post,
+               prolong="constant" if o.prolong == L.MG_PROLONG_CONSTANT else "trilinear")
+    s.set_density(rho)
+    dd = DD(dims, ranks, max_dec, h=h, **kw)
+    assert L.mg_dd_set_density(dd.h, rho, dims) == L.MG_OK
+    assert dd.plan.levels == s.num_levels
+    g = torch.Generator(device="cuda").manual_seed(4)
+    b = torch.randn((nz, ny, nx), generator=g, device="cuda", dtype=torch.float64)
+    x0 = torch.randn((nz, ny, nx), generator=g, device="cuda", dtype=torch.float64)
+    for _ in range(2):  # a second cycle continues from the first
+        xw = x0.clone()
+        whole_vcycle(s, b, xw)
+        xd = x0.clone()
+        assert L.mg_dd_vcycle(dd.h, b, xd, dims) == L.MG_OK, L.mg_dd_last_error(dd.h)
+        torch.cuda.synchronize()
+        assert torch.equal(xd, xw), (dims, ranks, max_dec, float((xd - xw).abs().max()))
+        x0 = xw
+    st, ex, by = L.mg_dd_traffic(dd.h)
+    k = 2 * o.pre + 2 * o.post + 1
+    assert ex == k * dd.plan.switch_level
+    assert by == sum(k * 2 * (ranks - 1) * 8 * dd.plan.nx[l] * dd.plan.ny[l] for l in range(dd.plan.switch_level))
+    dd.close()
+    s.close()
+
+
+@pytest.mark.parametrize("ranks,max_dec", [(2, 0), (4, 0), (8, 1)])
+def test_dd_solve_matches_whole_grid_and_oracle(ranks, max_dec):
+    n = 64
+    c = dropfilm_case(n)
+    dims = (n, n, n)
+    rho = dev(c["rho"])
+    b = dev(c["b"])
+    s = Solver(dims, h=c["h"], precision="fp64", coarsest=4, rtol=1e-11)
+    s.set_density(rho)
+    pw = s.solve(b)
+    dd = DD(dims, ranks, max_dec, h=c["h"], rtol=1e-11)
+    assert L.mg_dd_set_density(dd.h, rho, dims) == L.MG_OK
+    pd = torch.zeros_like(b)
+    st = L.mg_stats()
+    assert L.mg_dd_solve(dd.h, b, pd, dims, st) == L.MG_OK, L.mg_dd_last_error(dd.h)
+    assert st.relres <= 1e-11
+    assert st.cycles == s.last_stats.cycles
+    assert rel(host(pd), host(pw)) <= 1e-12
+    assert abs(float(pd.mean())) <= 1e-14 * float(pd.abs().max())
+    p_ex = O.Multigrid(c["faces"], c["h"], coarsest=4).solve_exact(c["b"])[0]
+    assert rel(host(pd), p_ex) <= 1e-9
+    dd.close()
+    s.close()
+
+
+def test_dd_errors():
+    dims = (32, 32, 32)
+    o = _opts(dims, 1 / 32)
+    o.precision = L.MG_MIXED
+    assert L.mg_dd_create(o, 2)[0] == L.MG_ERR_ARG           # FP64 only
+    assert L.mg_dd_create(_opts(dims, 1 / 32), 32)[0] == L.MG_ERR_ARG  # one plane per slab
+    dd = DD(dims, 2, h=1 / 32)
+    b = torch.zeros((32, 32, 32), dtype=torch.float64, device="cuda")
+    assert L.mg_dd_solve(dd.h, b, b.clone(), dims) == L.MG_ERR_STATE  # no operator yet
+    bad = torch.ones_like(b)
+    bad[3, 4, 5] = -1.0
+    assert L.mg_dd_set_density(dd.h, bad, dims) == L.MG_ERR_DENSITY
+    dd.close()
