@@ -59,7 +59,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # dram__bytes_read.sum,dram__bytes_write.sum` of paper_2605_30082_gb300/profile_case.py, the
 # summaries in profiles/.  A kernel changed since its capture has no entry (traffic null).
 NCU_DRAM_BYTES_PER_CELL = {"k_half_zs": 10.03, "k_half_z": 10.12, "k_fine_resid_pair": 54.3,
-                           "k_resid_dfs": 28.1}
+                           "k_resid_dfs": 28.1, "k_adjoint_grad_split2": 27.5}
 # Relative L2 distance to the exact discrete solution that the pressure must meet, and the
 # residual tolerance at which the headline (mixed) solve meets it on the 512^3 workload
 # (tests/test_gpu_parity_512.py asserts it against the oracle's exact solution)
@@ -349,14 +349,25 @@ def run_ours(args):
 
     sigma = SIGMA if args.csf else 0.0
 
-    def step(fd_, ff_, u_, w_, p_=p, lam_=lam, unew_=unew, dens_=dens):
+    def step(fd_, ff_, u_, w_, p_=p, lam_=lam, unew_=unew, dens_=dens, wait=None, forward_done=None):
+        """One step.  wait(stage) (end to end: the stream waits for that stage's input copies) is
+        called before the fractions, the face velocities and the weights are first used;
+        forward_done(p, unew) once the pressure and the corrected velocities are queued."""
+        if wait:
+            wait("fractions")
         s.density_from_fractions([fd_, ff_], RHO_PHASE, out=rho)
         s.set_density(rho)
         csf = s.csf_faces(fd_, D.curvature_band(fd_, geom)) if args.csf else None
+        if wait:
+            wait("velocities")
         s.rhs(u=u_, csf=csf, sigma=sigma, out=b)
         s.solve(b, p_)
         stats["fwd"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms, s.last_stats.outer)
         s.project(p_, u_, csf=csf, sigma=sigma, out=unew_)
+        if forward_done:
+            forward_done(p_, unew_)
+        if wait:
+            wait("weights")
         _, g, dlds = s.adjoint(w_, p_, csf=csf, sigma=sigma, lam=lam_)
         stats["adj"] = (s.last_stats.cycles, s.last_stats.relres, s.last_stats.ms, s.last_stats.outer)
         stats["dlds"] = dlds
@@ -495,12 +506,18 @@ def run_ours(args):
         gbs = class_bytes[name] * cells / (avg * 1e-3) / 1e9
         r = {"kernel": label, "launch_ms": round(avg, 4), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 3),
              "bytes_per_cell": class_bytes[name]}
+        if name == "adjoint_grad" and not args.csf:
+            r["traffic"] = _traffic("k_adjoint_grad_split2", cells)
         if name == "project":
             tf = (PROJECT_FP64_PER_CELL + (3 if args.csf else 0)) * cells / (avg * 1e-3) / 1e12
             r.update(fp64_tflops=round(tf, 3), fp64_frac_of_peak=round(tf / fp64_peak_tf, 3))
         return r
 
-    roof_side = {"project": side_roof("project", "k_project (velocity correction u + beta (G p + sigma csf), FP64)"),
+    roof_side = {"adjoint_grad": side_roof("adjoint_grad", "k_adjoint_grad (fused dL/dbeta, dL/dsigma; FP64) with "
+                                                          "a CSF term" if args.csf else
+                                           "k_adjoint_grad_split2 (fused dL/dbeta from FP32 pairs, no FP64 "
+                                           "arithmetic)"),
+                 "project": side_roof("project", "k_project (velocity correction u + beta (G p + sigma csf), FP64)"),
                  "density_grad": side_roof("density_grad", "k_density_grads (dL/drho and dL/df_q from the FP32 "
                                                            "face gradients)")}
 
@@ -553,7 +570,7 @@ def run_ours(args):
             "smoother_glups": round(cells * (n_sm / 2) / (ms_sm * 1e-3) / 1e9, 3),
             "roofline_smoother": roof_sm,
             "roofline_fp64_residual": roof_fr,
-            "projection_and_density_adjoint": roof_side,
+            "adjoint_grad_projection_and_density_adjoint": roof_side,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
             "kernel_hbm_gbs": {**{k: (round(class_bytes[k] * cells * v[0] / (v[1] * 1e-3) / 1e9, 1)
                                       if v[1] > 0 and k in class_bytes else None) for k, v in prof.items()},
@@ -642,18 +659,24 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
     import torch
 
     srcs = (fd, ff, *u, w)
+    # input copies in the order the step first uses them: fractions (set-up), face velocities
+    # (RHS), weights (adjoint); the step waits for each group only where it needs it
+    groups = {"fractions": (0, 2), "velocities": (2, 5), "weights": (5, 6)}
     hin = [t.cpu().pin_memory() for t in srcs]
     din = [[torch.empty_like(t) for t in srcs] for _ in range(2)]
     p2 = [torch.empty_like(fd) for _ in range(2)]
     lam2 = [torch.empty_like(fd) for _ in range(2)]
     un2 = [tuple(torch.empty_like(a) for a in u) for _ in range(2)]
     dens2 = [(torch.empty_like(fd), [torch.empty_like(fd), torch.empty_like(fd)]) for _ in range(2)]
-    hout = [torch.empty(fd.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-    hout += [torch.empty(sh, dtype=torch.float32, pin_memory=True) for sh in s.face_shapes]
-    hout += [torch.empty(a.shape, dtype=torch.float64, pin_memory=True) for a in u]
-    hout += [torch.empty(fd.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    # results: p and the corrected velocities (copied out while the adjoint runs), then lambda,
+    # the face gradients and the fraction gradients
+    hout_fwd = [torch.empty(fd.shape, dtype=torch.float64, pin_memory=True)]
+    hout_fwd += [torch.empty(a.shape, dtype=torch.float64, pin_memory=True) for a in u]
+    hout_adj = [torch.empty(fd.shape, dtype=torch.float64, pin_memory=True)]
+    hout_adj += [torch.empty(sh, dtype=torch.float32, pin_memory=True) for sh in s.face_shapes]
+    hout_adj += [torch.empty(fd.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
     bytes_in = sum(t.numel() * t.element_size() for t in hin)
-    bytes_out = sum(t.numel() * t.element_size() for t in hout)
+    bytes_out = sum(t.numel() * t.element_size() for t in hout_fwd + hout_adj)
     comp = torch.cuda.current_stream()
     cs = torch.cuda.Stream()     # host -> device
     cs_out = torch.cuda.Stream()  # device -> host, concurrently (the link carries both directions)
@@ -665,16 +688,24 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
         ev.record(st)
         return ev
 
+    def copy_in(q):
+        """The inputs of a step into buffers q, one event per group."""
+        evs = {}
+        with torch.cuda.stream(cs):
+            for name, (lo, hi) in groups.items():
+                for d_, h_ in zip(din[q][lo:hi], hin[lo:hi]):
+                    d_.copy_(h_, non_blocking=True)
+                evs[name] = torch.cuda.Event()
+                evs[name].record(cs)
+        return evs
+
     def pipeline(K):
-        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_in = [None, None]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         spans = []
         torch.cuda.synchronize()
         e0.record(cs)
-        with torch.cuda.stream(cs):
-            for d_, h_ in zip(din[0], hin):
-                d_.copy_(h_, non_blocking=True)
-        ev_in[0].record(cs)
+        ev_in[0] = copy_in(0)
         ev_prev = None
         ev_read = [None, None]  # result buffers q read back to the host
         for k in range(K):
@@ -683,23 +714,30 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
                 if ev_prev is not None:
                     cs.wait_event(ev_prev)
                 a = timed(cs)
-                with torch.cuda.stream(cs):
-                    for d_, h_ in zip(din[1 - q], hin):
-                        d_.copy_(h_, non_blocking=True)
+                ev_in[1 - q] = copy_in(1 - q)
                 spans.append(("h2d", a, timed(cs)))
-                ev_in[1 - q].record(cs)
-            comp.wait_event(ev_in[q])
             if ev_read[q] is not None:  # step k - 2's results left buffers q
                 comp.wait_event(ev_read[q])
+            evq = ev_in[q]
+
+            def forward_done(p_, un_, q=q):
+                ev_f = torch.cuda.Event()
+                ev_f.record(comp)
+                cs_out.wait_event(ev_f)
+                with torch.cuda.stream(cs_out):
+                    for h_, d_ in zip(hout_fwd, (p_, *un_)):
+                        h_.copy_(d_, non_blocking=True)
+
             a_c = timed(comp)
-            g = step(din[q][0], din[q][1], tuple(din[q][2:5]), din[q][5], p2[q], lam2[q], un2[q], dens2[q])
+            g = step(din[q][0], din[q][1], tuple(din[q][2:5]), din[q][5], p2[q], lam2[q], un2[q], dens2[q],
+                     wait=lambda name, evq=evq: comp.wait_event(evq[name]), forward_done=forward_done)
             spans.append(("compute", a_c, timed(comp)))
             ev_out = torch.cuda.Event()
             ev_out.record(comp)
             cs_out.wait_event(ev_out)
             a = timed(cs_out)
             with torch.cuda.stream(cs_out):
-                for h_, d_ in zip(hout, (p2[q], lam2[q], *g, *un2[q], *dens2[q][1])):
+                for h_, d_ in zip(hout_adj, (lam2[q], *g, *dens2[q][1])):
                     h_.copy_(d_, non_blocking=True)
                 for t in g:
                     t.record_stream(cs_out)
@@ -722,8 +760,9 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
             for d_, h_ in zip(din[0], hin):
                 d_.copy_(h_, non_blocking=True)
             ev[1].record(cs)
-            for h_, d_ in zip(hout, (p2[0], lam2[0], *[torch.empty(sh, dtype=torch.float32, device=fd.device)
-                                                         for sh in s.face_shapes], *un2[0], *dens2[0][1])):
+            for h_, d_ in zip(hout_fwd + hout_adj,
+                              (p2[0], *un2[0], lam2[0], *[torch.empty(sh, dtype=torch.float32, device=fd.device)
+                                                          for sh in s.face_shapes], *dens2[0][1])):
                 h_.copy_(d_, non_blocking=True)
             ev[2].record(cs)
         torch.cuda.synchronize()
@@ -744,7 +783,9 @@ def _e2e_pinned(args, s, step, fd, ff, u, w):
     under = {k: round(sorted(v)[len(v) // 2], 2) if v else None for k, v in copy_ms.items()}
     return {"value": round(n3 / (ms * 1e-3) / 1e9, 4), "unit": "Gcell/s", "ms_per_step": round(ms, 3),
             "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": ksteps,
-            "copies": "host-to-device and device-to-host on two streams of their own, double-buffered; every "
+            "copies": "host-to-device and device-to-host on two streams of their own, double-buffered; each "
+                      "step waits for its fractions, face velocities and weights only where it first uses "
+                      "them, and p and the corrected velocities are copied out while the adjoint runs; every "
                       "step's copies inside the timed region",
             "copy_gbs_alone": {"h2d": rate_in, "d2h": rate_out},
             "copy_ms_per_step_under_load": {k: v for k, v in under.items() if k != "compute"},
