@@ -10,6 +10,8 @@
 #include <atomic>
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mg_internal.cuh"
 
 namespace mg {
@@ -17,6 +19,9 @@ namespace mg {
 static unsigned long long g_launches = 0;
 
 void count_launch(int k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 unsigned long long launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 

@@ -696,6 +696,7 @@ void mg_default_opts(mg_opts *o) {
 }
 
 int mg_create(const mg_opts *o, void *stream, mg_handle **out) {
+    mg::NvtxRange nvtx_("mg_create");
     if (!out) return MG_ERR_ARG;
     *out = nullptr;
     if (!o) return MG_ERR_ARG;
@@ -857,6 +858,7 @@ int mg_level_dims(const mg_handle *h, int level, int *dims3) {
 
 int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac_dev,
                               const double *rho_phase, double *rho_dev) {
+    mg::NvtxRange nvtx_("mg_density_from_fractions");
     if (!h) return MG_ERR_ARG;
     if (nfrac < 1 || nfrac > 4 || !frac_dev || !rho_phase || !rho_dev)
         return fail(h, MG_ERR_ARG, "mg_density_from_fractions: 1..4 fractions and non-null arrays");
@@ -867,6 +869,7 @@ int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac
 }
 
 int mg_set_density(mg_handle *h, const double *rho) {
+    mg::NvtxRange nvtx_("mg_set_density");
     if (!h) return MG_ERR_ARG;
     if (!rho) return fail(h, MG_ERR_ARG, "rho is NULL");
     h->have_op = 0;
@@ -880,6 +883,7 @@ int mg_set_density(mg_handle *h, const double *rho) {
 }
 
 int mg_set_face_coeffs(mg_handle *h, const double *bx, const double *by, const double *bz) {
+    mg::NvtxRange nvtx_("mg_set_face_coeffs");
     if (!h) return MG_ERR_ARG;
     if (!bx || !by || !bz) return fail(h, MG_ERR_ARG, "face arrays must be non-null");
     h->have_op = 0;
@@ -901,6 +905,7 @@ int mg_get_level_faces(mg_handle *h, int level, double *bx, double *by, double *
 
 int mg_csf_faces(mg_handle *h, const double *f, const double *kappa, double *cx, double *cy,
                  double *cz) {
+    mg::NvtxRange nvtx_("mg_csf_faces");
     if (!h) return MG_ERR_ARG;
     if (!f || !kappa || !cx || !cy || !cz) return fail(h, MG_ERR_ARG, "mg_csf_faces: null array");
     mg::launch_csf_faces(h->s, h->lv[0].d, h->o.h, f, kappa, cx, cy, cz);
@@ -909,6 +914,7 @@ int mg_csf_faces(mg_handle *h, const double *f, const double *kappa, double *cx,
 
 int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, const double *uz,
            const double *csfx, const double *csfy, const double *csfz, double sigma, double *b) {
+    mg::NvtxRange nvtx_("mg_rhs");
     if (!h) return MG_ERR_ARG;
     if (!b) return fail(h, MG_ERR_ARG, "mg_rhs: b is NULL");
     bool u = ux || uy || uz;
@@ -926,6 +932,7 @@ int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, c
 static bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
 
 int mg_solve(mg_handle *h, const double *b, double *p, mg_stats *st) {
+    mg::NvtxRange nvtx_("mg_solve");
     if (!h) return MG_ERR_ARG;
     if (!b || !p) return fail(h, MG_ERR_ARG, "mg_solve: null array");
     if (!aligned16(p)) return fail(h, MG_ERR_ARG, "mg_solve: p must be 16-byte aligned");
@@ -937,6 +944,7 @@ int mg_solve(mg_handle *h, const double *b, double *p, mg_stats *st) {
 int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, float *gbx, float *gby,
                float *gbz, const double *csfx, const double *csfy, const double *csfz, double sigma,
                double *dLdsigma, mg_stats *st) {
+    mg::NvtxRange nvtx_("mg_adjoint");
     if (!h) return MG_ERR_ARG;
     if (!w || !p || !lam) return fail(h, MG_ERR_ARG, "mg_adjoint: w, p, lam must be non-null");
     if (!aligned16(lam)) return fail(h, MG_ERR_ARG, "mg_adjoint: lam must be 16-byte aligned");
@@ -968,6 +976,7 @@ int mg_adjoint(mg_handle *h, const double *w, const double *p, double *lam, floa
 int mg_project(mg_handle *h, const double *p, const double *csfx, const double *csfy, const double *csfz,
                double sigma, const double *ux, const double *uy, const double *uz, double *ox, double *oy,
                double *oz) {
+    mg::NvtxRange nvtx_("mg_project");
     if (!h) return MG_ERR_ARG;
     if (!p || !ux || !uy || !uz || !ox || !oy || !oz)
         return fail(h, MG_ERR_ARG, "mg_project: p, u and out arrays must be non-null");
@@ -988,6 +997,7 @@ int mg_project(mg_handle *h, const double *p, const double *csfx, const double *
 
 int mg_density_grads(mg_handle *h, const double *rho, const float *gbx, const float *gby, const float *gbz,
                      double *drho, int nfrac, const double *rho_phase, double *const *dfrac_dev) {
+    mg::NvtxRange nvtx_("mg_density_grads");
     if (!h) return MG_ERR_ARG;
     if (!rho || !gbx || !gby || !gbz || !drho)
         return fail(h, MG_ERR_ARG, "mg_density_grads: rho, gradients and drho must be non-null");

@@ -251,6 +251,7 @@ int mg_dd_make_plan(int nx, int ny, int nz, int coarsest, int ranks, int max_dec
 }
 
 int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, mg_dd **out) {
+    mg::NvtxRange nvtx_("mg_dd_create");
     if (!out) return MG_ERR_ARG;
     *out = nullptr;
     if (!o || o->precision != MG_FP64 || o->method != MG_METHOD_VCYCLE || o->inner_cycles != 1 ||
@@ -374,6 +375,7 @@ int mg_dd_traffic(const mg_dd *dd, long long *exchanges, long long *halo_bytes) 
 }
 
 int mg_dd_set_density(mg_dd *dd, const double *rho) {
+    mg::NvtxRange nvtx_("mg_dd_set_density");
     if (!dd) return MG_ERR_ARG;
     if (!rho) return dd_fail(dd, MG_ERR_ARG, "rho is NULL");
     dd->have_op = 0;
@@ -430,6 +432,7 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
 }
 
 int mg_dd_vcycle(mg_dd *dd, const double *b, double *x) {
+    mg::NvtxRange nvtx_("mg_dd_vcycle");
     if (!dd) return MG_ERR_ARG;
     if (!b || !x) return dd_fail(dd, MG_ERR_ARG, "null array");
     if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
@@ -451,6 +454,7 @@ int mg_dd_vcycle(mg_dd *dd, const double *b, double *x) {
 }
 
 int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
+    mg::NvtxRange nvtx_("mg_dd_solve");
     if (!dd) return MG_ERR_ARG;
     if (!b || !p) return dd_fail(dd, MG_ERR_ARG, "null array");
     if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");

@@ -130,6 +130,16 @@ __device__ __forceinline__ double recip64(double x) {
 // process-wide count of kernel launches (read through mg_kernel_launches)
 void count_launch(int k = 1);
 
+// NVTX range for the lifetime of the object: a profiler attached to the process (Nsight
+// Systems, ncu --nvtx) sees each entry point as one named range; without one the calls do
+// nothing (header-only NVTX3, which looks up a tool only when one is injected)
+struct NvtxRange {
+    explicit NvtxRange(const char *name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // the most blocks a deterministic reduction over n elements uses (its partials buffer holds
 // that many pairs); launchers take min(this, one wave of the kernel)
 int reduce_blocks(i64 n);
