@@ -62,6 +62,15 @@ __global__ void k_coarsen_z_plane(mg::Dims f, mg::Dims c, const double *__restri
 
 inline unsigned blocks_for(mg::i64 n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// a CUDA event pair destroyed on every way out of a call
+struct EventPair {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~EventPair() {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
 }  // namespace
 
 struct mg_dd {
@@ -459,10 +468,10 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     if (!b || !p) return dd_fail(dd, MG_ERR_ARG, "null array");
     if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
     cudaStream_t s = dd->s;
-    cudaEvent_t e0, e1;
-    DD_CUDA(dd, cudaEventCreate(&e0));
-    DD_CUDA(dd, cudaEventCreate(&e1));
-    DD_CUDA(dd, cudaEventRecord(e0, s));
+    EventPair ev;
+    DD_CUDA(dd, cudaEventCreate(&ev.e[0]));
+    DD_CUDA(dd, cudaEventCreate(&ev.e[1]));
+    DD_CUDA(dd, cudaEventRecord(ev.e[0], s));
     const double n = (double)dd->o.nx * dd->o.ny * dd->o.nz;
     // b~ = b - mean(b) slab by slab (the mean from the slabs' partial sums)
     double sb = 0.0;
@@ -510,12 +519,10 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     }
     for (Slab &S : dd->lv[0])
         DD_CUDA(dd, cudaMemcpyAsync(p + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
-    DD_CUDA(dd, cudaEventRecord(e1, s));
-    DD_CUDA(dd, cudaEventSynchronize(e1));
+    DD_CUDA(dd, cudaEventRecord(ev.e[1], s));
+    DD_CUDA(dd, cudaEventSynchronize(ev.e[1]));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]);
     DD_CUDA(dd, cudaGetLastError());
     if (st) {
         st->status = status;
