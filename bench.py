@@ -317,6 +317,48 @@ def parity_gate(args, b, w, rho, s, p_mixed, lam, p_fp64, t_mixed, t_fp64, time_
     return out
 
 
+# ---------------------------------------------------------------- domain decomposition
+
+def decomposed_solve(args, b, rho, p_fp64, t_fp64, cyc_fp64, ranks=4):
+    """The FP64 solve of the same workload cut into `ranks` z slabs held on this GPU (mg_dd_*),
+    timed like the whole-grid FP64 solve (median of 3): its cost over the whole-grid solve is the
+    halo copies and the per-slab launches; the pressure must agree with the whole-grid one."""
+    import torch
+
+    from paper_2605_30082_gb300 import _lib as L
+
+    n = args.n
+    o = L.mg_default_opts()
+    o.nx = o.ny = o.nz = n
+    o.h = 1.0 / n
+    o.precision, o.coarsest, o.rtol, o.max_cycles = L.MG_FP64, 8, 1e-10, 200
+    st, h = L.mg_dd_create(o, ranks)
+    if st != L.MG_OK:
+        return {"unavailable": f"mg_dd_create: status {st}"}
+    try:
+        if L.mg_dd_set_density(h, rho, (n, n, n)) != L.MG_OK:
+            return {"unavailable": L.mg_dd_last_error(h)}
+        p = torch.zeros_like(b)
+        times, stats = [], None
+        for _ in range(3):
+            stats = L.mg_stats()
+            if L.mg_dd_solve(h, b, p, (n, n, n), stats) != L.MG_OK:
+                return {"unavailable": L.mg_dd_last_error(h)}
+            times.append(stats.ms)
+        _, pl = L.mg_dd_get_plan(h)
+        _, ex, by = L.mg_dd_traffic(h)
+        t = statistics.median(times)
+        rel = float(torch.linalg.vector_norm(p - p_fp64) / torch.linalg.vector_norm(p_fp64))
+        return {"ranks": ranks, "slabs_held_on": "one GPU (halo exchange = device copies)",
+                "switch_level": pl.switch_level, "time_to_tol_ms": round(t, 3), "cycles": stats.cycles,
+                "whole_grid_fp64_ms": None if t_fp64 is None else round(t_fp64, 3), "whole_grid_cycles": cyc_fp64,
+                "overhead": None if not t_fp64 else round(t / t_fp64 - 1.0, 4),
+                "exchanges_per_cycle": ex, "halo_bytes_per_cycle": by,
+                "rel_diff_vs_whole_grid_p": float(f"{rel:.3e}")}
+    finally:
+        L.mg_dd_destroy(h)
+
+
 # ---------------------------------------------------------------- our path
 
 def run_ours(args):
@@ -464,8 +506,10 @@ def run_ours(args):
 
     # ---- parity gate: distance to the exact discrete solution, and the time to reach GATE_ERR
     gate = None
+    dd = None
     if not args.no_fp64:
         gate = parity_gate(args, b, w, rho, s, p_mixed, lam, p_fp64, t_mixed, t_fp64, time_solve)
+        dd = decomposed_solve(args, b, rho, p_fp64, t_fp64, cyc_fp64)
     s.solve(b, p)  # restore the headline solution
 
     # with the CSF term the gradient pass also reads the CSF faces and the face coefficients
@@ -586,6 +630,7 @@ def run_ours(args):
         "cycles": {"mixed": cyc_mixed, "fp64": cyc_fp64, "adjoint": stats["adj"][0],
                    "outer_forward": stats["fwd"][3], "outer_adjoint": stats["adj"][3]},
         "parity_gate": gate,
+        "domain_decomposition": dd,
         "fp64_peak": fp64_peak,
         "roofline": roofline,
         "cpu_baseline": None if cpu is None else {k: v for k, v in cpu.items() if k != "step_s_est"},
