@@ -35,7 +35,7 @@ RHO_PHASE = (998.0, 880.0, 1.2)
 SIGMA = 0.03  # interfacial tension of the CSF term (--csf)
 # FP32 V-cycles per outer FP64 residual and update in the timed configuration: 0 = adaptive (5
 # in the first outer iteration, then as many as the observed contraction predicts the tolerance
-# still needs, at most 5).  The 512^3 drop/film solve needs 24 V-cycles whether 1, 2, 3 or 4 run
+# still needs, at most 6).  The 512^3 drop/film solve needs 24 V-cycles whether 1, 2, 3 or 4 run
 # per FP64 residual; fewer outer iterations evaluate the FP64 residual, bound by the FP64 pipe,
 # less often, and the adaptive count does so without rounding the V-cycles up to a multiple.
 INNER = 0
@@ -100,7 +100,7 @@ def workload_config(n, csf, world):
     return {"workload": f"{n}^3 drop-on-film, density ratio 998/880/1.2, V(2,2), coarsest 8^3, rtol 1e-10, "
                         f"forward + velocity correction + adjoint + density adjoint"
                         + (f", CSF term sigma {SIGMA} with dL/dsigma" if csf else ""),
-            "method": "mixed: FP32 V-cycles (adaptive count, 5 then up to 5) per FP64 outer residual and update "
+            "method": "mixed: FP32 V-cycles (adaptive count, 6 then up to 6) per FP64 outer residual and update "
                       "(reference arm: the FP64 CPU oracle's V-cycle)",
             "cells": n**3, "l2_flush": "none needed: every array >= 1 GB > 129 MB L2",
             "parallelism": f"replicas x{world}"}

@@ -101,8 +101,8 @@ typedef struct {
     int inner_cycles; /* mixed modes: FP32 V-cycles per outer iteration (1..8), the first from
                          zero, the next ones continuing from the previous correction; the
                          FP64 (or double-float) residual and update run once per outer
-                         iteration.  0 (V-cycle iteration only): adaptive, 5 V-cycles in the
-                         first outer iteration, then as many (1..5) as the contraction per
+                         iteration.  0 (V-cycle iteration only): adaptive, 6 V-cycles in the
+                         first outer iteration, then as many (1..6) as the contraction per
                          V-cycle observed in the last outer iteration predicts the tolerance
                          still needs, so that few FP64 residuals are evaluated without adding
                          V-cycles.  With

@@ -177,6 +177,18 @@ void prof_collect(mg_handle *h) {
 // gaps between them.  The graph is recorded once in mg_create (build_tail_graph) from the
 // same functions the cycle calls, so a replay launches the same kernels with the same
 // arguments in the same order.
+}  // namespace
+
+namespace mg {
+cudaStream_t swap_handle_stream(mg_handle *h, cudaStream_t s) {
+    cudaStream_t o = h->s;
+    h->s = s;
+    return o;
+}
+}  // namespace mg
+
+namespace {
+
 void replay_tail(mg_handle *h) {
     if (cudaGraphLaunch(h->tail_exec, h->s) == cudaSuccess) mg::count_launch((int)h->tail_launches);
     // a failed launch leaves its error for the solve's check_launch
@@ -447,11 +459,11 @@ void inner_fcg32(mg_handle *h, int k) {
 // taken from the last outer iteration, and the next iteration runs
 //     k = ceil(log(rtol / rr) / log(rho) + margin),   1 <= k <= kMaxAdaptive,
 // V-cycles (margin 0.25 of a cycle: a slightly optimistic rho would otherwise cost a whole
-// extra outer iteration).  At most 5: the inner cycles work on one FP32-scaled residual, whose
-// FP32 rounding floor (about 2^-24 times |A| |e| / |A e|) they approach after more cycles (at
-// 512^3 eight cycles contracted the outer residual by 8.8e-3 where single cycles give 4.9e-3,
-// five by as much as single cycles).
-constexpr int kFirstAdaptive = 5, kMaxAdaptive = 5;
+// extra outer iteration).  At most 6: the inner cycles work on one FP32-scaled residual; at
+// 512^3 five, six, seven and eight cycles per outer residual all contract by 0.50-0.53 per
+// cycle, but seven and eight round the cycle count up (28 and 32 forward V-cycles against 24),
+// while six needs 24 + 30 V-cycles with 4 + 5 FP64 residuals where five needs 5 + 6.
+constexpr int kFirstAdaptive = 6, kMaxAdaptive = 6;
 
 int next_inner(double rr_prev, double rr, int k, double rtol) {
     if (!(rr > 0.0) || !(rr_prev > 0.0) || !(rtol > 0.0) || rr <= rtol) return k;

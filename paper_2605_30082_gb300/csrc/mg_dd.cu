@@ -88,6 +88,11 @@ struct mg_dd {
     unsigned *err;
     std::vector<void *> allocs;
     long long exchanges, halo_bytes;     // per V-cycle
+    // the whole V-cycle recorded once as a CUDA graph (fixed buffers and arguments) and replayed
+    // by every cycle; null: launched call by call
+    cudaGraphExec_t cyc_exec;
+    long long cyc_launches;
+    bool cyc_tried;
     int have_op;
     char msg[256];
 };
@@ -196,20 +201,95 @@ int vcycle(mg_dd *dd, int l, bool x_zero) {
     return smooth(dd, l, dd->o.post, 1);
 }
 
-// sums over the slabs' own planes of x (and of x^2), added in slab order
-int slab_sums(mg_dd *dd, int which, double *sum, double *sumsq) {
+// Record one V-cycle of level 0 (x_zero false) on a private stream, the whole-grid handle's
+// launches included; nothing runs.  Where recording is refused the cycles launch call by call.
+void build_cycle_graph(mg_dd *dd) {
+    dd->cyc_tried = true;
+    dd->cyc_exec = nullptr;
+    dd->cyc_launches = 0;
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    // the recording must not see work still queued on the caller's stream
+    if (cudaStreamSynchronize(dd->s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(cap);
+        return;
+    }
+    cudaStream_t saved = dd->s;
+    dd->s = cap;
+    cudaStream_t saved_ch = mg::swap_handle_stream(dd->ch, cap);
+    const unsigned long long l0 = mg::launches_total();
+    cudaGraph_t g = nullptr;
+    int rc = MG_ERR_CUDA;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        rc = vcycle(dd, 0, false);
+        if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = MG_ERR_CUDA;
+    }
+    const long long n = (long long)(mg::launches_total() - l0);
+    mg::count_launch((int)-n);  // recorded, not run
+    mg::swap_handle_stream(dd->ch, saved_ch);
+    dd->s = saved;
+    if (rc == MG_OK && g && cudaGraphInstantiate(&dd->cyc_exec, g, 0) != cudaSuccess) dd->cyc_exec = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    cudaGetLastError();
+    dd->cyc_launches = dd->cyc_exec ? n : 0;
+}
+
+// one V-cycle of level 0 from the slabs' x: the recorded graph, or call by call
+int cycle(mg_dd *dd) {
+    if (dd->cyc_exec) {
+        DD_CUDA(dd, cudaGraphLaunch(dd->cyc_exec, dd->s));
+        mg::count_launch((int)dd->cyc_launches);
+        return MG_OK;
+    }
+    return vcycle(dd, 0, false);
+}
+
+// per slab: sum of r, sum of r^2 and sum of x over its own planes; one read-back for all
+// slabs, added in slab order (the all-reduce of the two scalars a rank would exchange)
+int slab_sums(mg_dd *dd, double *sr, double *rn2, double *sp) {
+    const int P = dd->P;
+    for (int r = 0; r < P; ++r) {
+        Slab &S = dd->lv[0][r];
+        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.r, dd->partials, dd->red + 4 * r, true);
+        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.x, dd->partials, dd->red + 4 * r + 2, false);
+    }
+    std::vector<double> h(4 * (size_t)P);
+    DD_CUDA(dd, cudaMemcpyAsync(h.data(), dd->red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, dd->s));
+    DD_CUDA(dd, cudaStreamSynchronize(dd->s));
+    double a = 0.0, q = 0.0, x = 0.0;
+    for (int r = 0; r < P; ++r) {
+        a += h[4 * r];
+        q += h[4 * r + 1];
+        x += h[4 * r + 2];
+    }
+    *sr = a;
+    *rn2 = q;
+    *sp = x;
+    return MG_OK;
+}
+
+// the same for one array per slab: sum and sum of squares of the slabs' b
+int slab_sums_b(mg_dd *dd, double *sum, double *sumsq) {
+    const int P = dd->P;
+    for (int r = 0; r < P; ++r) {
+        Slab &S = dd->lv[0][r];
+        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.b, dd->partials, dd->red + 2 * r, true);
+    }
+    std::vector<double> h(2 * (size_t)P);
+    DD_CUDA(dd, cudaMemcpyAsync(h.data(), dd->red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, dd->s));
+    DD_CUDA(dd, cudaStreamSynchronize(dd->s));
     double a = 0.0, q = 0.0;
-    for (Slab &S : dd->lv[0]) {
-        const double *v = which == 0 ? S.x : (which == 1 ? S.r : S.b);
-        mg::launch_sum_sumsq<double>(dd->s, S.d.n, v, dd->partials, dd->red, sumsq != nullptr);
-        double h[2];
-        DD_CUDA(dd, cudaMemcpyAsync(h, dd->red, sizeof(h), cudaMemcpyDeviceToHost, dd->s));
-        DD_CUDA(dd, cudaStreamSynchronize(dd->s));
-        a += h[0];
-        q += h[1];
+    for (int r = 0; r < P; ++r) {
+        a += h[2 * r];
+        q += h[2 * r + 1];
     }
     *sum = a;
-    if (sumsq) *sumsq = q;
+    *sumsq = q;
     return MG_OK;
 }
 
@@ -315,7 +395,7 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
     dd->aby = A((size_t)snz * (sny + 1) * snx);
     dd->abz = A((size_t)(snz + 1) * sny * snx);
     dd->partials = A(2 * (size_t)mg::reduce_blocks(n0));
-    dd->red = A(4);
+    dd->red = A(4 * (size_t)MG_DD_MAX_RANKS);
     dd->err = static_cast<unsigned *>(dd_alloc(dd, 256));
     if (!ok || !dd->err) {
         mg_dd_destroy(dd);
@@ -361,6 +441,7 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
 int mg_dd_destroy(mg_dd *dd) {
     if (!dd) return MG_OK;
     if (dd->s) cudaStreamSynchronize(dd->s);
+    if (dd->cyc_exec) cudaGraphExecDestroy(dd->cyc_exec);
     if (dd->ch) mg_destroy(dd->ch);
     for (void *p : dd->allocs) cudaFree(p);
     cudaGetLastError();
@@ -437,6 +518,8 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
     int rc = mg_set_face_coeffs(dd->ch, dd->abx, dd->aby, dd->abz);
     if (rc) return dd_fail(dd, rc, "switch level: %s", mg_last_error(dd->ch));
     dd->have_op = 1;
+    // the cycle's buffers and arguments do not depend on the operator: recorded once
+    if (!dd->cyc_tried) build_cycle_graph(dd);
     return MG_OK;
 }
 
@@ -453,7 +536,7 @@ int mg_dd_vcycle(mg_dd *dd, const double *b, double *x) {
         if (S.d.zlo) DD_CUDA(dd, cudaMemcpyAsync(S.xe, x + off - S.d.nxy, pb, cudaMemcpyDeviceToDevice, s));
         if (S.d.zhi) DD_CUDA(dd, cudaMemcpyAsync(S.x + S.d.n, x + off + S.d.n, pb, cudaMemcpyDeviceToDevice, s));
     }
-    int rc = vcycle(dd, 0, false);
+    int rc = cycle(dd);
     if (rc) return rc;
     for (Slab &S : dd->lv[0])
         DD_CUDA(dd, cudaMemcpyAsync(x + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
@@ -488,7 +571,7 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
         DD_CUDA(dd, cudaMemsetAsync(S.xe, 0, 8 * (size_t)(S.d.n + 2 * S.d.nxy), s));
     }
     double t, nb2;
-    int rc = slab_sums(dd, 2, &t, &nb2);
+    int rc = slab_sums_b(dd, &t, &nb2);
     if (rc) return rc;
     const double nb = std::sqrt(nb2);
     double hist[MG_HIST_LEN];
@@ -498,13 +581,11 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     if (nb == 0.0 || rr <= dd->o.rtol) status = MG_OK;
     const double ih2 = 1.0 / (dd->o.h * dd->o.h);
     while (status == MG_ERR_NOT_CONVERGED && cycles < dd->o.max_cycles) {
-        rc = vcycle(dd, 0, false);
+        rc = cycle(dd);
         if (rc) return rc;
         for (Slab &S : dd->lv[0]) mg::launch_residual<double>(s, S.d, ih2, coef(S), S.b, S.x, S.r);
         double sr, rn2, sp;
-        rc = slab_sums(dd, 1, &sr, &rn2);
-        if (rc) return rc;
-        rc = slab_sums(dd, 0, &sp, nullptr);
+        rc = slab_sums(dd, &sr, &rn2, &sp);
         if (rc) return rc;
         // zero mean, ghosts included (they hold the neighbours' planes, shifted alike)
         for (Slab &S : dd->lv[0]) mg::launch_add_const(s, S.d.n + 2 * S.d.nxy, S.xe, -sp / n);

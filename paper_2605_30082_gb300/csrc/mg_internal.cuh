@@ -129,6 +129,12 @@ __device__ __forceinline__ double recip64(double x) {
 
 // process-wide count of kernel launches (read through mg_kernel_launches)
 void count_launch(int k = 1);
+unsigned long long launches_total();
+
+// the stream a handle queues its work on, replaced by `s`; returns the previous one (the
+// decomposed solver records its cycle, the whole-grid handle's launches included, on a
+// private stream)
+cudaStream_t swap_handle_stream(mg_handle *h, cudaStream_t s);
 
 // NVTX range for the lifetime of the object: a profiler attached to the process (Nsight
 // Systems, ncu --nvtx) sees each entry point as one named range; without one the calls do
