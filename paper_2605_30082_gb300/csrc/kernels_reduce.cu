@@ -300,6 +300,17 @@ __global__ void k_fine_resid_pair(Dims d, Lay L, double h2, const double *__rest
     block_sum2((double)q, (double)sp, partials + 2 * blockIdx.x);
 }
 
+// r32 = s32 * (the residual of p = 0) in the level layout, rounded as the residual kernels round
+// theirs: the residual of p = 0 is h^2 b~ itself, truncated to FP32, times s32.  A cold-started
+// solve takes its first inner right-hand side from here instead of an FP64 residual pass.
+__global__ void k_zero_resid32(Dims d, Lay L, const double *__restrict__ b, float s32, float *r32) {
+    const i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.n) return;
+    const unsigned cu = (unsigned)c, r = cu / (unsigned)d.nx;  // c < 2^32: 32-bit divisions
+    const int i = (int)(cu - r * (unsigned)d.nx), j = (int)(r % (unsigned)d.ny), k = (int)(r / (unsigned)d.ny);
+    r32[sto(L, i, j, k)] = d2f_trunc(b[c]) * s32;
+}
+
 // the same residual, one thread per cell (any nx; used when nx is odd)
 template <bool SCALED>
 __global__ void k_fine_resid_cell(Dims d, Lay L, double h2, const double *__restrict__ fx,
@@ -726,6 +737,11 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
     else k_fine_resid_pair<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
+}
+
+void launch_zero_resid32(cudaStream_t s, Dims d, Lay L, const double *b, double scale32, float *r32) {
+    count_launch();
+    k_zero_resid32<<<blocks_for(d.n), kThreads, 0, s>>>(d, L, b, (float)scale32, r32);
 }
 
 void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift) {

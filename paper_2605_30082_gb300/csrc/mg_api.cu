@@ -541,10 +541,19 @@ int solve_impl(mg_handle *h, const double *b, double *p, int warm, mg_stats *st)
             prof_collect(h);
             return check_launch(h, "fine residual");
         };
-        rc = residual(mixed);
-        if (rc) return rc;
-        double rn = std::sqrt(h->hred[6]) * F.ih2;  // the kernel sums (h^2 r)^2
-        double mu = h->hred[7] / (double)n;
+        double rn, mu;
+        if (!warm && !df) {
+            // p = 0: its residual is b~ itself, of norm nb, and mean(p) = 0; the mixed modes take
+            // the scaled FP32 copy the residual kernel would have written (no FP64 pass)
+            if (mixed) mg::launch_zero_resid32(s, F.d, F.lay, h->bt, F.ih2 * scale, F.b32);
+            rn = nb;
+            mu = 0.0;
+        } else {
+            rc = residual(mixed);
+            if (rc) return rc;
+            rn = std::sqrt(h->hred[6]) * F.ih2;  // the kernel sums (h^2 r)^2
+            mu = h->hred[7] / (double)n;
+        }
         rr = rn / nb;
         hist[hist_n++] = rr;
         status = MG_ERR_NOT_CONVERGED;

@@ -308,6 +308,9 @@ void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const doubl
 void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
                         const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
                         float *r32, float s32, double *partials, double *out);
+// r32 = (float)(ih2 scale) * trunc_fp32(b): the scaled FP32 residual of p = 0, as the outer
+// residual kernels would write it (b = h^2 b~ in the mixed modes)
+void launch_zero_resid32(cudaStream_t s, Dims d, Lay L, const double *b, double scale32, float *r32);
 // p = p - shift + alpha * e32 (e32 in the level-0 FP32 layout L; shift a host scalar)
 void launch_update(cudaStream_t s, Dims d, Lay L, double *p, const float *e32, double alpha, double shift);
 void launch_add_const(cudaStream_t s, i64 n, double *p, double c);
