@@ -159,7 +159,8 @@ const char *mg_last_error(const mg_handle *h);
 int mg_num_levels(const mg_handle *h);
 int mg_level_dims(const mg_handle *h, int level, int *dims3);
 
-/* Eq. (5): rho = sum_{q<nfrac} rho_q f_q + rho_{nfrac} (1 - sum_{q<nfrac} f_q).
+/* Eq. (5): rho = sum_{q<nfrac} rho_q f_q + rho_{nfrac} (1 - sum_{q<nfrac} f_q), evaluated as
+ * rho_{nfrac} + sum_{q<nfrac} (rho_q - rho_{nfrac}) f_q (equal up to FP64 rounding).
  * frac_dev: host array of nfrac (1..4) device pointers to cell arrays;
  * rho_phase: host array of nfrac+1 phase densities; rho_dev: output cell array. */
 int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac_dev,

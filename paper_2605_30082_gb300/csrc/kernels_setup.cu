@@ -14,20 +14,21 @@ inline unsigned blocks_for(i64 n) { return (unsigned)((n + kThreads - 1) / kThre
 
 struct FracArgs {
     const double *f[4];
-    double rho[5];
+    double drho[4];  // rho_q - rho_last
+    double rho_last;
     int nfrac;
 };
 
+// Eq. (5) in the form rho_last + sum_q (rho_q - rho_last) f_q: one FMA per fraction (the
+// literal sum_q rho_q f_q + rho_last (1 - sum_q f_q) takes 2 nfrac + 1 FP64 operations, which
+// bound this kernel by the FP64 pipe); equal in exact arithmetic, within a few units in the
+// last place in FP64
 __global__ void k_density(i64 n, FracArgs a, double *rho) {
     i64 m = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    double r = 0.0, rest = 1.0;
-    for (int q = 0; q < a.nfrac; ++q) {
-        double f = a.f[q][m];
-        r += a.rho[q] * f;
-        rest -= f;
-    }
-    rho[m] = r + a.rho[a.nfrac] * rest;
+    double r = a.rho_last;
+    for (int q = 0; q < a.nfrac; ++q) r = fma(a.drho[q], a.f[q][m], r);
+    rho[m] = r;
 }
 
 // 0 < v <= 1.79e308, tested on the bit pattern (positive doubles order like their bits, NaN and
@@ -72,6 +73,36 @@ __global__ void k_faces_from_s(Dims d, const double *__restrict__ sv, double *fx
         fx[c] = i > 0 ? half_of(sv[c - 1] + sc) : 0.0;
         fy[c] = j > 0 ? half_of(sv[c - d.nx] + sc) : 0.0;
         fz[c] = k > 0 ? half_of(sv[c - d.nxy] + sc) : 0.0;
+    }
+}
+
+// the same for even nx, two cells per thread: 16-byte loads and stores (the x - 1 value of the
+// pair's first cell is one scalar load, from the line the neighbouring lane reads); the same
+// additions in the same order as k_faces_from_s, so bitwise the same faces
+__global__ void k_faces_from_s2(Dims d, const double *__restrict__ sv, double *fx, double *fy, double *fz) {
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= d.nx) return;
+    const i64 rows = (i64)d.ny * d.nz;
+    auto ld2 = [](const double *q) { return *reinterpret_cast<const double2 *>(q); };
+    auto st2 = [](double *q, double a, double b) { *reinterpret_cast<double2 *>(q) = make_double2(a, b); };
+    for (i64 row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = (int)((unsigned)row % (unsigned)d.ny), k = (int)((unsigned)row / (unsigned)d.ny);  // rows < 2^31
+        const i64 c = row * d.nx + i;
+        const double2 sc = ld2(sv + c);
+        const double sl = i > 0 ? sv[c - 1] : 0.0;
+        st2(fx + c, i > 0 ? half_of(sl + sc.x) : 0.0, half_of(sc.x + sc.y));
+        if (j > 0) {
+            const double2 sy = ld2(sv + c - d.nx);
+            st2(fy + c, half_of(sy.x + sc.x), half_of(sy.y + sc.y));
+        } else {
+            st2(fy + c, 0.0, 0.0);
+        }
+        if (k > 0) {
+            const double2 sz = ld2(sv + c - d.nxy);
+            st2(fz + c, half_of(sz.x + sc.x), half_of(sz.y + sc.y));
+        } else {
+            st2(fz + c, 0.0, 0.0);
+        }
     }
 }
 
@@ -361,8 +392,11 @@ void launch_density(cudaStream_t s, i64 n, int nfrac, const double *const *frac,
                     const double *rho_phase, double *rho) {
     FracArgs a;
     a.nfrac = nfrac;
-    for (int q = 0; q < 4; ++q) a.f[q] = q < nfrac ? frac[q] : nullptr;
-    for (int q = 0; q < 5; ++q) a.rho[q] = q <= nfrac ? rho_phase[q] : 0.0;
+    a.rho_last = rho_phase[nfrac];
+    for (int q = 0; q < 4; ++q) {
+        a.f[q] = q < nfrac ? frac[q] : nullptr;
+        a.drho[q] = q < nfrac ? rho_phase[q] - rho_phase[nfrac] : 0.0;
+    }
     count_launch();
     k_density<<<blocks_for(n), kThreads, 0, s>>>(n, a, rho);
 }
@@ -372,6 +406,12 @@ void launch_faces_from_rho(cudaStream_t s, Dims d, const double *rho, double *si
     count_launch(2);
     k_inv_rho<<<blocks_for(d.n), kThreads, 0, s>>>(d.n, rho, sinv, err);
     const i64 rows = (i64)d.ny * d.nz;
+    auto a16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    if (d.nx % 2 == 0 && a16(sinv) && a16(fx) && a16(fy) && a16(fz)) {
+        const dim3 grd((unsigned)((d.nx / 2 + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
+        k_faces_from_s2<<<grd, 128, 0, s>>>(d, sinv, fx, fy, fz);
+        return;
+    }
     const dim3 grd((unsigned)((d.nx + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
     k_faces_from_s<<<grd, 128, 0, s>>>(d, sinv, fx, fy, fz);
 }
