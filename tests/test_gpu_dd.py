@@ -139,3 +139,32 @@ def test_dd_errors():
     bad[3, 4, 5] = -1.0
     assert L.mg_dd_set_density(dd.h, bad, dims) == L.MG_ERR_DENSITY
     dd.close()
+
+
+def test_dd_solve_at_512_in_four_slabs():
+    """The benchmark's 512^3 drop-on-film field, FP64 to rtol 1e-10, cut into 4 slabs: the same
+    V-cycles as the whole-grid FP64 solve and the same pressure up to the order of the sums."""
+    import dropfilm as D
+
+    n = 512
+    dims = (n, n, n)
+    cuda = torch.device("cuda")
+    g = D.scaled_geometry(n)
+    fd, ff = D.fractions_ramp(g, device=cuda, z_chunk=32)
+    u = D.face_velocities(n, 0, device=cuda, z_chunk=32)
+    s = Solver(dims, h=1.0 / n, precision="fp64", coarsest=8, rtol=1e-10)
+    rho = s.density_from_fractions([fd, ff], list(RHO_PHASE))
+    s.set_density(rho)
+    b = s.rhs(u=u)
+    pw = s.solve(b)
+    cycles = s.last_stats.cycles
+    s.close()
+    dd = DD(dims, 4, h=1.0 / n, coarsest=8, rtol=1e-10)
+    assert L.mg_dd_set_density(dd.h, rho, dims) == L.MG_OK
+    pd = torch.zeros_like(b)
+    st = L.mg_stats()
+    assert L.mg_dd_solve(dd.h, b, pd, dims, st) == L.MG_OK, L.mg_dd_last_error(dd.h)
+    assert st.cycles == cycles
+    rel_t = float(torch.linalg.vector_norm(pd - pw) / torch.linalg.vector_norm(pw))
+    assert rel_t <= 1e-12, rel_t
+    dd.close()
