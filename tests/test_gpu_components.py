@@ -67,6 +67,26 @@ def test_levels_and_faces_match_oracle(dims, precision):
             assert np.max(np.abs(g[nz] - o[nz]) / o[nz]) <= 1e-15
 
 
+@pytest.mark.parametrize("dims", [(72, 40, 24), (40, 24, 56), (36, 20, 12)])
+def test_density_and_face_loading_give_bitwise_the_same_fp64_solve(dims):
+    """mg_set_density forms the finest faces from s = 1/rho; mg_set_face_coeffs takes them as
+    given.  Loaded with the same faces, the two FP64 hierarchies (coarsened faces, diagonals and
+    their reciprocals, the dense coarse inverse) must be the same bit for bit, and so must the
+    FP64 solves."""
+    nx, ny, nz = dims
+    h = 1.0 / 64
+    a = Solver(dims, h=h, precision="fp64", coarsest=4, rtol=1e-10)
+    a.set_density(dev(random_rho(dims, 17)))
+    b_ = Solver(dims, h=h, precision="fp64", coarsest=4, rtol=1e-10)
+    b_.set_face_coeffs(*a.level_faces(0))
+    rhs = dev(rnd((nz, ny, nx), 5))
+    pa, pb = a.solve(rhs), b_.solve(rhs)
+    assert a.last_stats.cycles == b_.last_stats.cycles
+    assert torch.equal(pa, pb)
+    a.close()
+    b_.close()
+
+
 def test_density_from_fractions_and_face_round_trip():
     n = 24
     fd, ff = D.fractions_ramp(D.scaled_geometry(n))
