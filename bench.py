@@ -74,6 +74,22 @@ FP64_FLOPS_PER_CELL = {"smooth": 7.5, "resid_restrict": 8.0, "prolong": 8.0, "fi
 
 # algorithmic bytes per fine grid cell of one launch of each profiled class (the smoother's
 # mix of regular and from-zero sweeps is computed from the launch counts instead)
+# profile classes timed as one interval per V-cycle (the levels below the finest) or per call
+GROUPED = ("coarse_levels", "setup", "rhs", "density")
+
+
+def step_accounting(prof, ms_step, steps):
+    """The step's device time split into the timed classes and the rest (gauge sums and
+    shifts, the cold start's first FP32 residual, scalar read-backs, host waits between launches)."""
+    per = {k: v[1] / steps for k, v in prof.items()}
+    timed = sum(per.values())
+    return {"ms_per_step": round(ms_step, 3), "timed_classes_ms": round(timed, 3),
+            "other_ms": round(ms_step - timed, 3),
+            "coarse_levels_ms_per_vcycle": (round(prof["coarse_levels"][1] / prof["coarse_levels"][0], 4)
+                                            if prof["coarse_levels"][0] else None),
+            "vcycles_per_step": prof["coarse_levels"][0] / steps}
+
+
 CLASS_BYTES = {"resid_restrict": 10.5, "prolong": 4.5, "update": 26.0, "fine_residual": 52.0,
                "adjoint_grad": 28.0, "project": 80.0, "density_grad": 44.0}
 # velocity correction: per interior face one FP64 subtraction, one multiply and one FMA (3 faces
@@ -446,7 +462,8 @@ def run_ours(args):
         ("smooth", L.MG_PROF_SMOOTH), ("resid_restrict", L.MG_PROF_RESID_RESTRICT),
         ("prolong", L.MG_PROF_PROLONG), ("fine_residual", L.MG_PROF_FINE_RESIDUAL),
         ("update", L.MG_PROF_UPDATE), ("adjoint_grad", L.MG_PROF_ADJOINT_GRAD), ("project", L.MG_PROF_PROJECT),
-        ("density_grad", L.MG_PROF_DENSITY_GRAD)]}
+        ("density_grad", L.MG_PROF_DENSITY_GRAD), ("coarse_levels", L.MG_PROF_COARSE_LEVELS),
+        ("setup", L.MG_PROF_SETUP), ("rhs", L.MG_PROF_RHS), ("density", L.MG_PROF_DENSITY)]}
     s.profile(False)
     barrier()
     ms_total = max_over_ranks(ms_total, dev)
@@ -621,7 +638,8 @@ def run_ours(args):
                                       if v[1] > 0 and k in class_bytes else None) for k, v in prof.items()},
                                "smooth": round(gbs_sm, 1)},
             "dL_dsigma": stats.get("dlds") if args.csf else None,
-            "kernel_launches_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "kernel_launches_per_step": {k: v[0] / args.steps for k, v in prof.items() if k not in GROUPED},
+            "step_accounting": step_accounting(prof, ms_step, args.steps),
         },
         "time_to_tol_ms": {"mixed": round(t_mixed, 3), "fp64": None if t_fp64 is None else round(t_fp64, 3),
                            "rtol": 1e-10},

@@ -290,9 +290,10 @@ int mg_coarse_solve(mg_handle *h, int dtype, const void *r, void *e);
 
 /* ---- instrumentation ------------------------------------------------------------
  * With profiling on, the library records a CUDA event pair around every launch
- * of a level-0 kernel class below (on the handle's stream) and accumulates the
- * elapsed device time per class.  It measures the kernels inside real solves;
- * it adds two event records per timed launch and nothing else. */
+ * of a level-0 kernel class below, and around each of the coarser groups below
+ * (on the handle's stream), and accumulates the elapsed device time per class.
+ * It measures the kernels inside real solves; it adds two event records per
+ * timed interval and nothing else. */
 enum {
     MG_PROF_SMOOTH = 0,         /* finest-level fused sweep passes (with the restriction or
                                    prolongation some of them carry) */
@@ -304,13 +305,20 @@ enum {
     MG_PROF_ADJOINT_GRAD = 6,   /* fused adjoint gradient kernel */
     MG_PROF_PROJECT = 7,        /* velocity correction (mg_project) */
     MG_PROF_DENSITY_GRAD = 8,   /* density adjoint (mg_density_grads) */
-    MG_PROF_NCLASS = 9
+    MG_PROF_COARSE_LEVELS = 9,  /* the V-cycle below the finest level: one interval per V-cycle
+                                   (the replayed graph of its launches, or the launches) */
+    MG_PROF_SETUP = 10,         /* operator set-up: one interval per mg_set_density /
+                                   mg_set_face_coeffs (faces, coarsening, packs, coarse inverse) */
+    MG_PROF_RHS = 11,           /* right-hand side (mg_rhs) */
+    MG_PROF_DENSITY = 12,       /* density from the fractions (mg_density_from_fractions) */
+    MG_PROF_NCLASS = 13
 };
 
 /* Turn timing on (1) or off (0); either way the accumulated totals are reset. */
 int mg_profile(mg_handle *h, int enable);
 
-/* Launches timed and their total device milliseconds for one class. */
+/* Intervals timed (launches, or V-cycles / calls for the grouped classes) and their
+ * total device milliseconds for one class. */
 int mg_profile_read(mg_handle *h, int cls, long long *launches, double *ms);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */

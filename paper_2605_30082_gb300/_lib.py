@@ -27,7 +27,8 @@ MG_NOALLOC_MAX_CELLS = 512
 MG_INJECT_FUSED_WAIT, MG_INJECT_DIVERGE = 1, 2
 (MG_PROF_SMOOTH, MG_PROF_RESID_RESTRICT, MG_PROF_PROLONG, MG_PROF_COARSE,
  MG_PROF_FINE_RESIDUAL, MG_PROF_UPDATE, MG_PROF_ADJOINT_GRAD, MG_PROF_PROJECT,
- MG_PROF_DENSITY_GRAD, MG_PROF_NCLASS) = range(10)
+ MG_PROF_DENSITY_GRAD, MG_PROF_COARSE_LEVELS, MG_PROF_SETUP, MG_PROF_RHS, MG_PROF_DENSITY,
+ MG_PROF_NCLASS) = range(14)
 
 ERROR_NAMES = {
     MG_OK: "MG_OK", MG_ERR_ARG: "MG_ERR_ARG", MG_ERR_DENSITY: "MG_ERR_DENSITY",

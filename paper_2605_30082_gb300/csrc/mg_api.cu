@@ -238,8 +238,10 @@ void vcycle64(mg_handle *h, int l, const double *b, double *x, bool x_zero) {
     Level &L = h->lv[l], &C = h->lv[l + 1];
     if (x_zero) cudaMemsetAsync(x, 0, sizeof(double) * (size_t)L.d.n, h->s);
     presmooth_restrict64(h, l, b, x, C.b64, h->o.pre);
+    if (l == 0) prof_begin(h, MG_PROF_COARSE_LEVELS);
     if (l == 0 && h->tail_exec) replay_tail(h);
     else vcycle64(h, l + 1, C.b64, C.x64, true);
+    if (l == 0) prof_end(h);
     prolong_postsmooth64(h, l, b, C.x64, x, h->o.post);
 }
 
@@ -352,8 +354,10 @@ void vcycle32(mg_handle *h, int l, const float *b, float *x, const OuterUpdate *
     }
     Level &C = h->lv[l + 1];
     presmooth_restrict32(h, l, b, x, C.b32, h->o.pre, from_zero);
+    if (l == 0) prof_begin(h, MG_PROF_COARSE_LEVELS);
     if (l == 0 && h->tail_exec) replay_tail(h);
     else vcycle32(h, l + 1, C.b32, C.x32);
+    if (l == 0) prof_end(h);
     prolong_postsmooth32(h, l, b, C.x32, x, h->o.post, up);
 }
 
@@ -418,6 +422,7 @@ int finish_operator(mg_handle *h) {
     mg::launch_coarse_assemble(s, C.d, C.ih2, C.fx64, C.fy64, C.fz64, h->pinv, h->scal);
     mg::launch_gj_blocked(s, h->nc, h->pinv, h->gj_tmp);  // in place, 32 pivots per step
     mg::launch_pinv_finish(s, h->nc, h->pinv, h->scal);
+    prof_end(h);  // MG_PROF_SETUP, begun by the caller
     int st = check_launch(h, "operator set-up");
     if (st) return st;
     MG_READBACK_ERR(h, s);
@@ -885,7 +890,9 @@ int mg_density_from_fractions(mg_handle *h, int nfrac, const double *const *frac
         return fail(h, MG_ERR_ARG, "mg_density_from_fractions: 1..4 fractions and non-null arrays");
     for (int q = 0; q < nfrac; ++q)
         if (!frac_dev[q]) return fail(h, MG_ERR_ARG, "fraction %d is NULL", q);
+    prof_begin(h, MG_PROF_DENSITY);
     mg::launch_density(h->s, h->lv[0].d.n, nfrac, frac_dev, rho_phase, rho_dev);
+    prof_end(h);
     return check_launch(h, "mg_density_from_fractions");
 }
 
@@ -894,6 +901,7 @@ int mg_set_density(mg_handle *h, const double *rho) {
     if (!h) return MG_ERR_ARG;
     if (!rho) return fail(h, MG_ERR_ARG, "rho is NULL");
     h->have_op = 0;
+    prof_begin(h, MG_PROF_SETUP);  // ended by finish_operator
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
     // s = 1/rho goes through the RHS buffer, which holds nothing between calls
@@ -908,6 +916,7 @@ int mg_set_face_coeffs(mg_handle *h, const double *bx, const double *by, const d
     if (!h) return MG_ERR_ARG;
     if (!bx || !by || !bz) return fail(h, MG_ERR_ARG, "face arrays must be non-null");
     h->have_op = 0;
+    prof_begin(h, MG_PROF_SETUP);  // ended by finish_operator
     MG_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->s));
     Level &F = h->lv[0];
     mg::launch_faces_from_api(h->s, F.d, bx, by, bz, F.fx64, F.fy64, F.fz64, h->err);
@@ -945,8 +954,10 @@ int mg_rhs(mg_handle *h, const double *b0, const double *ux, const double *uy, c
     if (csf && !h->have_op) return fail(h, MG_ERR_STATE, "mg_rhs: the surface term needs coefficients set");
     if (!std::isfinite(sigma)) return fail(h, MG_ERR_ARG, "mg_rhs: sigma not finite");
     Level &F = h->lv[0];
+    prof_begin(h, MG_PROF_RHS);
     mg::launch_rhs(h->s, F.d, h->o.h, b0, u ? ux : nullptr, uy, uz, F.fx64, F.fy64, F.fz64,
                    csf ? csfx : nullptr, csf ? csfy : nullptr, csf ? csfz : nullptr, sigma, b);
+    prof_end(h);
     return check_launch(h, "mg_rhs");
 }
 

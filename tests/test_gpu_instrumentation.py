@@ -1,5 +1,6 @@
-"""Instrumentation entry points: the FP64 FMA rate (the FP64 rooflines' denominator) and the
-per-class kernel timing and launch counter."""
+"""Instrumentation entry points: the FP64 FMA rate (the FP64 rooflines' denominator), the
+per-class kernel timing (finest-level kernels, the levels below as one interval per V-cycle,
+the set-up calls) and the launch counter."""
 import pytest
 import torch
 
@@ -43,6 +44,19 @@ def test_profile_classes_count_the_finest_level_launches():
     assert n_res == outer  # one per outer iteration (a cold start's opening residual is b~ itself)
     assert n_sm == cycles * 8 - outer  # V(2,2): 8 half sweeps, the last one carries the update
     assert ms_upd > 0 and ms_res > 0 and ms_sm > 0
+    n_cl, ms_cl = s.profile_read(L.MG_PROF_COARSE_LEVELS)
+    assert n_cl == cycles and ms_cl > 0  # one interval per V-cycle below the finest level
     s.profile(False)
     assert s.profile_read(L.MG_PROF_SMOOTH) == (0, 0.0)
+    # the grouped classes around the set-up calls: one interval per call
+    s.profile(True)
+    fr = [torch.full((64, 64, 64), 0.3, dtype=torch.float64, device="cuda") for _ in range(2)]
+    rho = s.density_from_fractions(fr, [998.0, 880.0, 1.2])
+    s.set_density(rho)
+    s.set_density(rho)
+    s.rhs(b0=b)
+    for cls, k in ((L.MG_PROF_DENSITY, 1), (L.MG_PROF_SETUP, 2), (L.MG_PROF_RHS, 1)):
+        n_k, ms_k = s.profile_read(cls)
+        assert n_k == k and ms_k > 0, (cls, n_k, ms_k)
+    s.profile(False)
     s.close()
