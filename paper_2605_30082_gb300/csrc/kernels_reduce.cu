@@ -236,7 +236,9 @@ __device__ __forceinline__ i64 sto(const Lay &L, int x, int y, int z) {
 // The FP32 sum of p only steers the per-iteration gauge shift; the exit gauge is exact.
 // One thread handles the cell pair x = 2k, 2k+1 of a row (even nx): aligned double2 loads,
 // and the pair's red and black r32 values land at index k of the two colour halves.
-template <bool SCALED>
+// GHOST: a slab of a decomposed grid (d.zlo / d.zhi): its ghost planes count as interior
+// neighbours; whole-grid levels compile without the two extra tests
+template <bool SCALED, bool GHOST>
 __global__ void k_fine_resid_pair(Dims d, Lay L, double h2, const double *__restrict__ fx,
                                   const double *__restrict__ fy, const double *__restrict__ fz,
                                   const double *__restrict__ dg, const double *__restrict__ b,
@@ -273,12 +275,12 @@ __global__ void k_fine_resid_pair(Dims d, Lay L, double h2, const double *__rest
             a0 = fma(f.x, pp.x, a0);
             a1 = fma(f.y, pp.y, a1);
         }
-        if (z > 0) {
+        if (z > 0 || (GHOST && d.zlo)) {
             const double2 pm = *reinterpret_cast<const double2 *>(p + c - nxy);
             a0 = fma(fza.x, pm.x, a0);
             a1 = fma(fza.y, pm.y, a1);
         }
-        if (z < nz - 1) {
+        if (z < nz - 1 || (GHOST && d.zhi)) {
             const double2 f = *reinterpret_cast<const double2 *>(fz + c + nxy);
             const double2 pp = *reinterpret_cast<const double2 *>(p + c + nxy);
             a0 = fma(f.x, pp.x, a0);
@@ -330,8 +332,8 @@ __global__ void k_fine_resid_cell(Dims d, Lay L, double h2, const double *__rest
         if (i < nx - 1) acc = fma(fx[c + 1], p[c + 1], acc);
         if (j > 0) acc = fma(fy[c], p[c - nx], acc);
         if (j < ny - 1) acc = fma(fy[c + nx], p[c + nx], acc);
-        if (k > 0) acc = fma(fz[c], p[c - nxy], acc);
-        if (k < nz - 1) acc = fma(fz[c + nxy], p[c + nxy], acc);
+        if (k > 0 || d.zlo) acc = fma(fz[c], p[c - nxy], acc);  // a slab's ghost planes count as interior
+        if (k < nz - 1 || d.zhi) acc = fma(fz[c + nxy], p[c + nxy], acc);
         acc = fma(-dg[c], pc, acc);
         const float rf = d2f_trunc(acc);
         if (r32) r32[sto(L, i, j, k)] = rf * s32;
@@ -729,12 +731,26 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
         k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
         return;
     }
-    static const int wave_pt = wave_blocks((const void *)k_fine_resid_pair<true>, kReduceThreads);
-    static const int wave_pf = wave_blocks((const void *)k_fine_resid_pair<false>, kReduceThreads);
+    static const int wave_pt = wave_blocks((const void *)k_fine_resid_pair<true, false>, kReduceThreads);
+    static const int wave_pf = wave_blocks((const void *)k_fine_resid_pair<false, false>, kReduceThreads);
     const int nb = fill_blocks(reduce_blocks(d.n / 2), b_scaled ? wave_pt : wave_pf);
     count_launch();
-    if (b_scaled) k_fine_resid_pair<true><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
-    else k_fine_resid_pair<false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    if (d.zlo || d.zhi) {
+        // a slab (FP64 arithmetic only: b unscaled, no FP32 copy); its own wave: the ghost tests
+        // take 6 more registers, one resident block fewer per SM
+        static const int wave_g = wave_blocks((const void *)k_fine_resid_pair<false, true>, kReduceThreads);
+        const int ng = fill_blocks(reduce_blocks(d.n / 2), wave_g);
+        k_fine_resid_pair<false, true><<<ng, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, nullptr, 0.f,
+                                                                     partials);
+        count_launch();
+        k_final<<<1, kReduceThreads, 0, s>>>(partials, ng, out);
+        return;
+    }
+    if (b_scaled) {
+        k_fine_resid_pair<true, false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    } else {
+        k_fine_resid_pair<false, false><<<nb, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+    }
     count_launch();
     k_final<<<1, kReduceThreads, 0, s>>>(partials, nb, out);
 }

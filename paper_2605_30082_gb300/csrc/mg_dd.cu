@@ -36,7 +36,7 @@ struct Slab {
     int z0;          // first whole-grid plane of the slab
     double *xe;      // x with a ghost plane below and above: planes + 2 planes
     double *x;       // = xe + nxy, the first own plane
-    double *b, *r;   // own planes
+    double *b;       // own planes
     double *fx, *fy; // low faces of the own planes
     double *fze;     // low z faces of the own planes and of the ghost above: planes + 1 planes
     double *invd, *dg;
@@ -88,6 +88,12 @@ struct mg_dd {
     unsigned *err;
     std::vector<void *> allocs;
     long long exchanges, halo_bytes;     // per V-cycle
+    // one stream per rank: each phase of the cycle (a half sweep, an exchange, the restriction,
+    // the prolongation) forks from s onto the ranks' streams and joins back, so the ranks' slabs
+    // are worked on concurrently, as on separate GPUs (empty: every rank on s, one after another)
+    std::vector<cudaStream_t> rs;
+    std::vector<cudaEvent_t> rdone;
+    cudaEvent_t fork;
     // the whole V-cycle recorded once as a CUDA graph (fixed buffers and arguments) and replayed
     // by every cycle; null: launched call by call
     cudaGraphExec_t cyc_exec;
@@ -118,26 +124,55 @@ int dd_fail(mg_dd *dd, int code, const char *fmt, ...) {
 
 mg::Coef<double> coef(const Slab &S) { return {S.fx, S.fy, S.fze, S.invd}; }
 
-// ghost planes of x on level l from the neighbouring slabs' first / last own planes
+// f(r, stream) for every rank, on the rank's stream after everything queued so far on dd->s;
+// dd->s then waits for all of them
+template <typename F>
+int per_rank(mg_dd *dd, F &&f) {
+    if (dd->rs.empty()) {
+        for (int r = 0; r < dd->P; ++r) {
+            const int rc = f(r, dd->s);
+            if (rc) return rc;
+        }
+        return MG_OK;
+    }
+    DD_CUDA(dd, cudaEventRecord(dd->fork, dd->s));
+    for (int r = 0; r < dd->P; ++r) {
+        DD_CUDA(dd, cudaStreamWaitEvent(dd->rs[r], dd->fork, 0));
+        const int rc = f(r, dd->rs[r]);
+        DD_CUDA(dd, cudaEventRecord(dd->rdone[r], dd->rs[r]));  // joined even after a failed launch
+        if (rc) return rc;
+    }
+    for (int r = 0; r < dd->P; ++r) DD_CUDA(dd, cudaStreamWaitEvent(dd->s, dd->rdone[r], 0));
+    return MG_OK;
+}
+
+// ghost planes of x on level l from the neighbouring slabs' first / last own planes: each rank
+// receives its two planes (the neighbours' planes were finished by the phase before)
 int exchange(mg_dd *dd, int l) {
     std::vector<Slab> &R = dd->lv[l];
     const size_t bytes = sizeof(double) * (size_t)R[0].d.nxy;
-    for (int r = 0; r < dd->P; ++r) {
+    return per_rank(dd, [&](int r, cudaStream_t st) -> int {
         if (r > 0)
             DD_CUDA(dd, cudaMemcpyAsync(R[r].xe, R[r - 1].x + (R[r - 1].d.nz - 1) * R[r - 1].d.nxy, bytes,
-                                        cudaMemcpyDeviceToDevice, dd->s));
+                                        cudaMemcpyDeviceToDevice, st));
         if (r + 1 < dd->P)
-            DD_CUDA(dd, cudaMemcpyAsync(R[r].x + R[r].d.n, R[r + 1].x, bytes, cudaMemcpyDeviceToDevice, dd->s));
-    }
-    return MG_OK;
+            DD_CUDA(dd, cudaMemcpyAsync(R[r].x + R[r].d.n, R[r + 1].x, bytes, cudaMemcpyDeviceToDevice, st));
+        return MG_OK;
+    });
 }
 
 int smooth(mg_dd *dd, int l, int sweeps, int order) {
     const double h2 = dd->o.h * dd->o.h * (double)(1ll << (2 * l));
+    std::vector<Slab> &R = dd->lv[l];
     for (int sw = 0; sw < sweeps; ++sw)
         for (int half = 0; half < 2; ++half) {
-            for (Slab &S : dd->lv[l]) mg::launch_rbgs_half64(dd->s, S.d, h2, coef(S), S.b, S.x, order ? 1 - half : half);
-            int rc = exchange(dd, l);
+            const int col = order ? 1 - half : half;
+            int rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+                mg::launch_rbgs_half64(st, R[r].d, h2, coef(R[r]), R[r].b, R[r].x, col);
+                return MG_OK;
+            });
+            if (rc) return rc;
+            rc = exchange(dd, l);
             if (rc) return rc;
         }
     return MG_OK;
@@ -158,12 +193,18 @@ int tail(mg_dd *dd, int k) {
 int vcycle(mg_dd *dd, int l, bool x_zero) {
     std::vector<Slab> &R = dd->lv[l];
     const double h2 = dd->o.h * dd->o.h * (double)(1ll << (2 * l));
-    if (x_zero)
-        for (Slab &S : R) DD_CUDA(dd, cudaMemsetAsync(S.xe, 0, sizeof(double) * (size_t)(S.d.n + 2 * S.d.nxy), dd->s));
-    int rc = smooth(dd, l, dd->o.pre, 0);
+    int rc;
+    if (x_zero) {
+        rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+            DD_CUDA(dd, cudaMemsetAsync(R[r].xe, 0, sizeof(double) * (size_t)(R[r].d.n + 2 * R[r].d.nxy), st));
+            return MG_OK;
+        });
+        if (rc) return rc;
+    }
+    rc = smooth(dd, l, dd->o.pre, 0);
     if (rc) return rc;
     const bool last = l + 1 == dd->ndec;
-    for (int r = 0; r < dd->P; ++r) {
+    rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
         Slab &S = R[r];
         double *bc;
         if (!last) {
@@ -174,14 +215,16 @@ int vcycle(mg_dd *dd, int l, bool x_zero) {
         }
         // after a pre-smoothing sweep (black last) every black residual is zero
         if (dd->o.pre > 0)
-            mg::launch_rr_red_diag64(dd->s, S.d, h2, coef(S), S.dg, S.b, S.x, bc);
+            mg::launch_rr_red_diag64(st, S.d, h2, coef(S), S.dg, S.b, S.x, bc);
         else
-            mg::launch_resid_restrict<double>(dd->s, S.d, 1.0 / h2, coef(S), S.b, S.x, bc, false);
-    }
+            mg::launch_resid_restrict<double>(st, S.d, 1.0 / h2, coef(S), S.b, S.x, bc, false);
+        return MG_OK;
+    });
+    if (rc) return rc;
     rc = last ? tail(dd, 0) : vcycle(dd, l + 1, true);
     if (rc) return rc;
     // prolongation: red cells only when a post sweep (black first) follows
-    for (int r = 0; r < dd->P; ++r) {
+    rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
         Slab &S = R[r];
         mg::Dims cd;
         const double *ec;
@@ -194,8 +237,10 @@ int vcycle(mg_dd *dd, int l, bool x_zero) {
             cd.zhi = S.d.zhi;
             ec = dd->cx[0] + (mg::i64)(S.z0 / 2) * cd.nxy;  // the neighbours' planes lie beside it
         }
-        mg::launch_prolong<double>(dd->s, cd, ec, S.x, dd->o.prolong, dd->o.post > 0 ? 0 : -1);
-    }
+        mg::launch_prolong<double>(st, cd, ec, S.x, dd->o.prolong, dd->o.post > 0 ? 0 : -1);
+        return MG_OK;
+    });
+    if (rc) return rc;
     rc = exchange(dd, l);
     if (rc) return rc;
     return smooth(dd, l, dd->o.post, 1);
@@ -249,27 +294,43 @@ int cycle(mg_dd *dd) {
     return vcycle(dd, 0, false);
 }
 
-// per slab: sum of r, sum of r^2 and sum of x over its own planes; one read-back for all
-// slabs, added in slab order (the all-reduce of the two scalars a rank would exchange)
-int slab_sums(mg_dd *dd, double *sr, double *rn2, double *sp) {
+// per slab, by the whole grid's fused residual kernel over the slab's own planes (its ghost
+// planes as neighbours): sum of (h^2 r)^2 and sum of x; one read-back for all slabs, added in
+// slab order (the all-reduce of the two scalars a rank would exchange)
+int slab_residual_norms(mg_dd *dd, double *rn2_h4, double *sp) {
+    const int P = dd->P;
+    const double h2 = dd->o.h * dd->o.h;
+    for (int r = 0; r < P; ++r) {
+        Slab &S = dd->lv[0][r];
+        mg::launch_fine_resid2(dd->s, S.d, mg::make_lay(S.d), h2, S.fx, S.fy, S.fze, S.dg, S.b, false, S.x,
+                               nullptr, 0.f, dd->partials, dd->red + 2 * r);
+    }
+    std::vector<double> h(2 * (size_t)P);
+    DD_CUDA(dd, cudaMemcpyAsync(h.data(), dd->red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, dd->s));
+    DD_CUDA(dd, cudaStreamSynchronize(dd->s));
+    double q = 0.0, x = 0.0;
+    for (int r = 0; r < P; ++r) {
+        q += h[2 * r];
+        x += h[2 * r + 1];
+    }
+    *rn2_h4 = q;
+    *sp = x;
+    return MG_OK;
+}
+
+// the sum of the slabs' own planes of x in FP64, added in slab order
+int slab_sum_x(mg_dd *dd, double *sum) {
     const int P = dd->P;
     for (int r = 0; r < P; ++r) {
         Slab &S = dd->lv[0][r];
-        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.r, dd->partials, dd->red + 4 * r, true);
-        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.x, dd->partials, dd->red + 4 * r + 2, false);
+        mg::launch_sum_sumsq<double>(dd->s, S.d.n, S.x, dd->partials, dd->red + 2 * r, false);
     }
-    std::vector<double> h(4 * (size_t)P);
+    std::vector<double> h(2 * (size_t)P);
     DD_CUDA(dd, cudaMemcpyAsync(h.data(), dd->red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, dd->s));
     DD_CUDA(dd, cudaStreamSynchronize(dd->s));
-    double a = 0.0, q = 0.0, x = 0.0;
-    for (int r = 0; r < P; ++r) {
-        a += h[4 * r];
-        q += h[4 * r + 1];
-        x += h[4 * r + 2];
-    }
-    *sr = a;
-    *rn2 = q;
-    *sp = x;
+    double a = 0.0;
+    for (int r = 0; r < P; ++r) a += h[2 * r];
+    *sum = a;
     return MG_OK;
 }
 
@@ -376,7 +437,6 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
             S.xe = A(n + 2 * nxy);
             S.x = S.xe ? S.xe + nxy : nullptr;
             S.b = A(n);
-            S.r = A(n);
             S.fx = A(n);
             S.fy = A(n);
             S.fze = A(n + nxy);
@@ -434,6 +494,29 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
         dd->exchanges += k;
         dd->halo_bytes += k * per;
     }
+    // the ranks' streams (without them the ranks run one after another on the caller's stream)
+    bool streams = cudaEventCreateWithFlags(&dd->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int r = 0; r < ranks && streams; ++r) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            streams = false;
+            break;
+        }
+        dd->rs.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            streams = false;
+            break;
+        }
+        dd->rdone.push_back(ev);
+    }
+    if (!streams) {
+        cudaGetLastError();
+        for (cudaStream_t st : dd->rs) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : dd->rdone) cudaEventDestroy(ev);
+        dd->rs.clear();
+        dd->rdone.clear();
+    }
     *out = dd;
     return MG_OK;
 }
@@ -441,6 +524,12 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
 int mg_dd_destroy(mg_dd *dd) {
     if (!dd) return MG_OK;
     if (dd->s) cudaStreamSynchronize(dd->s);
+    for (cudaStream_t st : dd->rs) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : dd->rdone) cudaEventDestroy(ev);
+    if (dd->fork) cudaEventDestroy(dd->fork);
     if (dd->cyc_exec) cudaGraphExecDestroy(dd->cyc_exec);
     if (dd->ch) mg_destroy(dd->ch);
     for (void *p : dd->allocs) cudaFree(p);
@@ -583,13 +672,12 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     while (status == MG_ERR_NOT_CONVERGED && cycles < dd->o.max_cycles) {
         rc = cycle(dd);
         if (rc) return rc;
-        for (Slab &S : dd->lv[0]) mg::launch_residual<double>(s, S.d, ih2, coef(S), S.b, S.x, S.r);
-        double sr, rn2, sp;
-        rc = slab_sums(dd, &sr, &rn2, &sp);
+        double rn2, sp;
+        rc = slab_residual_norms(dd, &rn2, &sp);
         if (rc) return rc;
         // zero mean, ghosts included (they hold the neighbours' planes, shifted alike)
         for (Slab &S : dd->lv[0]) mg::launch_add_const(s, S.d.n + 2 * S.d.nxy, S.xe, -sp / n);
-        rr = std::sqrt(rn2) / nb;
+        rr = std::sqrt(rn2) * ih2 / nb;
         ++cycles;
         if (hn < MG_HIST_LEN) hist[hn++] = rr;
         if (!std::isfinite(rr) || rr > 1e12) {
@@ -597,6 +685,13 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
             break;
         }
         if (rr <= dd->o.rtol) status = MG_OK;
+    }
+    // exact zero-mean gauge at exit (the per-cycle shifts use the residual kernel's FP32 sum of x)
+    if (nb > 0.0) {
+        double sx;
+        rc = slab_sum_x(dd, &sx);
+        if (rc) return rc;
+        for (Slab &S : dd->lv[0]) mg::launch_add_const(s, S.d.n, S.x, -sx / n);
     }
     for (Slab &S : dd->lv[0])
         DD_CUDA(dd, cudaMemcpyAsync(p + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));

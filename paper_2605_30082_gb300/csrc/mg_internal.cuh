@@ -304,7 +304,10 @@ void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const doubl
                           const double *fz, const double *b, const double *p, float *r32,
                           double scale, double *partials, double *out);
 // fine FP64 residual in diagonal form, h^2 r = h^2 b - (diag p_c - sum_f beta_f p_nb):
-// out[0] = sum (h^2 r)^2, out[1] = sum p; optional r32 = s32 * h^2 r in the level-0 layout L
+// out[0] = sum (h^2 r)^2, out[1] = sum p; optional r32 = s32 * h^2 r in the level-0 layout L.
+// On a slab of a decomposed grid (d.zlo or d.zhi, even nx; p with its ghost planes beside the
+// own ones, fz with the face to the ghost above) the ghost planes count as interior neighbours;
+// there b is unscaled and no FP32 copy is written (b_scaled and r32 are ignored)
 void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
                         const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
                         float *r32, float s32, double *partials, double *out);
