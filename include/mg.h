@@ -363,6 +363,13 @@ int mg_fp64_fma_rate(void *stream, double *sink, int blocks, int iters, double *
  * gather), a whole-grid handle runs the rest of the V-cycle, and each slab's prolongation
  * reads its coarse planes and their neighbours from there.  The norm and the mean of p are
  * sums of per-slab partial sums.  One V-cycle gives bitwise the whole-grid FP64 V-cycle.
+ * The mixed-precision solve (precision MG_MIXED) is decomposed at its finest level only
+ * (switch_level 1): FP32 slabs of the colour-split layout with a ghost plane per colour below
+ * and above, an exchange of the colour just updated after every half sweep and after the
+ * prolongation, the restriction written into the whole-grid handle's FP32 level, the rest of
+ * each inner V-cycle on that handle, and the FP64 outer loop (residual, norms, update) slab by
+ * slab with p's ghost planes exchanged before each residual; it follows the whole-grid mixed
+ * solve cell for cell (the same residual history up to the order of the sums).
  * Arrays passed in and out are whole-grid device arrays (cell layout above). */
 #define MG_DD_MAX_RANKS 64
 typedef struct mg_dd mg_dd;
@@ -379,21 +386,27 @@ typedef struct {
  * of level l; its neighbours are r - 1 and r + 1. */
 int mg_dd_make_plan(int nx, int ny, int nz, int coarsest, int ranks, int max_decomposed, mg_dd_plan *plan);
 
-/* Create a decomposed FP64 solver (opts: precision MG_FP64, method MG_METHOD_VCYCLE,
- * inner_cycles 1, warm_start 0; other fields as for mg_create).  Allocates every slab's
- * buffers and the whole-grid handle of the switch level on the current device. */
+/* Create a decomposed solver.  opts: method MG_METHOD_VCYCLE, warm_start 0, and either
+ * precision MG_FP64 with inner_cycles 1, or precision MG_MIXED (inner_cycles as for mg_create)
+ * with pre >= 1, post >= 1, trilinear prolongation, nx a multiple of 16 and nz a multiple of
+ * 4 * ranks (max_decomposed is then 1); other fields as for mg_create.  MG_ERR_ARG otherwise.
+ * Allocates every slab's buffers and the whole-grid handle of the switch level on the current
+ * device. */
 int mg_dd_create(const mg_opts *opts, int ranks, int max_decomposed, void *stream, mg_dd **out);
 int mg_dd_destroy(mg_dd *dd);
 const char *mg_dd_last_error(const mg_dd *dd);
 int mg_dd_get_plan(const mg_dd *dd, mg_dd_plan *plan);
-/* Halo exchanges of one V-cycle and the bytes they copy between slabs. */
+/* Halo exchanges of one V-cycle and the bytes they copy between slabs (mixed: FP32 planes of
+ * one colour; the outer loop's exchange of p's FP64 planes, once per outer iteration, apart). */
 int mg_dd_traffic(const mg_dd *dd, long long *exchanges, long long *halo_bytes);
 /* Operator from a whole-grid density (as mg_set_density); each slab takes its faces, the
  * coarse slabs are coarsened slab by slab.  Synchronises. */
 int mg_dd_set_density(mg_dd *dd, const double *rho);
-/* One V-cycle for A x = b (b as given, no mean removed), x in place.  Synchronises. */
+/* One FP64 V-cycle for A x = b (b as given, no mean removed), x in place; FP64 solvers only
+ * (MG_ERR_ARG for a mixed one).  Synchronises. */
 int mg_dd_vcycle(mg_dd *dd, const double *b, double *x);
-/* As mg_solve in MG_FP64: zero-mean p with A p = b - mean(b) to opts.rtol, from p = 0. */
+/* As mg_solve in the solver's precision (MG_FP64 or MG_MIXED): zero-mean p with
+ * A p = b - mean(b) to opts.rtol, from p = 0. */
 int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *stats);
 
 /* ---- allocation-free entry point ----------------------------------------------------

@@ -736,12 +736,15 @@ void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *
     const int nb = fill_blocks(reduce_blocks(d.n / 2), b_scaled ? wave_pt : wave_pf);
     count_launch();
     if (d.zlo || d.zhi) {
-        // a slab (FP64 arithmetic only: b unscaled, no FP32 copy); its own wave: the ghost tests
-        // take 6 more registers, one resident block fewer per SM
-        static const int wave_g = wave_blocks((const void *)k_fine_resid_pair<false, true>, kReduceThreads);
-        const int ng = fill_blocks(reduce_blocks(d.n / 2), wave_g);
-        k_fine_resid_pair<false, true><<<ng, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, nullptr, 0.f,
-                                                                     partials);
+        // a slab; its own wave: the ghost tests take more registers, one resident block fewer
+        // per SM
+        static const int wave_gt = wave_blocks((const void *)k_fine_resid_pair<true, true>, kReduceThreads);
+        static const int wave_gf = wave_blocks((const void *)k_fine_resid_pair<false, true>, kReduceThreads);
+        const int ng = fill_blocks(reduce_blocks(d.n / 2), b_scaled ? wave_gt : wave_gf);
+        if (b_scaled)
+            k_fine_resid_pair<true, true><<<ng, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
+        else
+            k_fine_resid_pair<false, true><<<ng, kReduceThreads, 0, s>>>(d, L, h2, fx, fy, fz, diag, b, p, r32, s32, partials);
         count_launch();
         k_final<<<1, kReduceThreads, 0, s>>>(partials, ng, out);
         return;

@@ -126,7 +126,8 @@ __device__ __forceinline__ void df_add(float &h, float &l, float t) {
 // add alpha * x - shift for them and for the 4 black values of the same row positions --
 // together the 8 consecutive cells x = 2 k0 .. 2 k0 + 7 -- to the solution: the FP64 one
 // (UPDATE 1) or the double-float one (UPDATE 2).
-template <bool SFORM, bool FROM_ZERO, int UPDATE = 0>
+// GHOST: a slab of a decomposed level (L.zlo / L.zhi), its ghost planes as z neighbours
+template <bool SFORM, bool FROM_ZERO, int UPDATE = 0, bool GHOST = false>
 __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__ b, float *xv, int col,
                            Upd up = Upd{}) {
     const int hx = L.hx, kv = hx >> 2;
@@ -142,7 +143,8 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
     const int p = (col + y + z) & 1;  // x = 2k + p
     const i64 own = col * L.half + row * hx + k0;
     const i64 opp = (1 - col) * L.half + row * hx + k0;
-    const bool hy0 = y > 0, hy1 = y < L.ny - 1, hz0 = z > 0, hz1 = z < L.nz - 1;
+    const bool hy0 = y > 0, hy1 = y < L.ny - 1;
+    const bool hz0 = z > 0 || (GHOST && L.zlo), hz1 = z < L.nz - 1 || (GHOST && L.zhi);
     const i64 dy = hx, dz = (i64)L.ny * hx;
     // same-row other-colour window: xm[v] = O[k0+v+p-1], xp[v] = O[k0+v+p]
     auto window = [&](const float *O, float (&m)[4], float (&q)[4]) {
@@ -268,7 +270,7 @@ __global__ void k_half_vec(Lay L, float h2, Coef32 cf, const float *__restrict__
 // lanes at a warp's edge load them.  Lanes past the end of a row, or rows past ny, compute on
 // clamped (in-bounds) indices and store nothing; all lanes of a warp share one row and one
 // z-range, so the shuffles are always converged.  Arithmetic per cell is that of k_half_vec.
-template <bool SFORM, bool FROM_ZERO, int UPDATE, int ZC>
+template <bool SFORM, bool FROM_ZERO, int UPDATE, int ZC, bool GHOST = false>
 __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, const float *__restrict__ b,
                                                     float *xv, int col, Upd up) {
     const int hx = L.hx, kv = hx >> 2;
@@ -288,17 +290,18 @@ __global__ void __launch_bounds__(64, 12) k_half_z(Lay L, float h2, Coef32 cf, c
     auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
     // planes z-1 and z of the other colour (x, and s in SFORM)
     float4 xzm = f0, xzc = f0, szm = f0, szc = f0;
+    const bool glo = GHOST && L.zlo, ghi = GHOST && L.zhi;  // a slab's ghost planes are neighbours
     if (!FROM_ZERO) {
-        if (z0 > 0) xzm = ld(xv, opp - dz);
+        if (z0 > 0 || glo) xzm = ld(xv, opp - dz);
         xzc = ld(xv, opp);
     }
     if (SFORM) {
-        if (z0 > 0) szm = ld(cf.s, opp - dz);
+        if (z0 > 0 || glo) szm = ld(cf.s, opp - dz);
         szc = ld(cf.s, opp);
     }
     const float hh = SFORM ? 2.f * h2 : h2;
     for (int z = z0; z < z1; ++z) {
-        const bool hz0 = z > 0, hz1 = z < L.nz - 1;
+        const bool hz0 = z > 0 || glo, hz1 = z < L.nz - 1 || ghi;
         const int p = (col + y + z) & 1;  // x = 2k + p
         const bool xw0 = (p == 0 && !kl), xw1 = (p == 1 && !kr);
         float4 xzp = f0, ym = f0, yp = f0;
@@ -597,7 +600,7 @@ bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32
 
 // 16 planes per thread where that still gives about 4 waves of 64-thread blocks (12 resident
 // per SM, on the device's SM count), else 4
-template <bool SFORM, bool FROM_ZERO, int UPDATE>
+template <bool SFORM, bool FROM_ZERO, int UPDATE, bool GHOST = false>
 void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
                 const Upd &up) {
     const int kv = L.hx / 4;
@@ -606,7 +609,7 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
     const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
     const dim3 blk(vb, ry);
     const i64 sms = device_sms();
-    if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 8) {
+    if (SFORM && !FROM_ZERO && UPDATE == 0 && !GHOST && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 8) {
         // 11 blocks x 18 KB of staging per SM: ask for the largest shared-memory carveout
         static const bool carveout = [] {
             // a preference only: the launch is valid either way
@@ -620,9 +623,9 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
         return;
     }
     if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 12)
-        k_half_z<SFORM, FROM_ZERO, UPDATE, 16><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf, b, x, col, up);
+        k_half_z<SFORM, FROM_ZERO, UPDATE, 16, GHOST><<<dim3(gx, gy, (L.nz + 15) / 16), blk, 0, s>>>(L, h2, cf, b, x, col, up);
     else
-        k_half_z<SFORM, FROM_ZERO, UPDATE, 4><<<dim3(gx, gy, (L.nz + 3) / 4), blk, 0, s>>>(L, h2, cf, b, x, col, up);
+        k_half_z<SFORM, FROM_ZERO, UPDATE, 4, GHOST><<<dim3(gx, gy, (L.nz + 3) / 4), blk, 0, s>>>(L, h2, cf, b, x, col, up);
 }
 
 // ---- vectorised red-only residual + restriction (split fine level, hx % 4 == 0) ----------
@@ -630,7 +633,9 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
 // (2J + b, 2K + c); one thread handles coarse cells I0..I0+3 of one coarse row.
 constexpr int kRrThreads = 64;
 
-template <bool SFORM>
+// GHOST: the fine level is a slab (L.zlo / L.zhi) and Lc a view of the whole coarse level
+// (its arrays at the slab's first coarse plane, an even one)
+template <bool SFORM, bool GHOST = false>
 __global__ void __launch_bounds__(kRrThreads, 12) k_rr_red_vec(Lay L, Lay Lc, float ih2, Coef32 cf, const float *__restrict__ b,
                              const float *__restrict__ xv, float *bc) {
     const int hx = L.hx, kv = hx >> 2;
@@ -651,7 +656,8 @@ __global__ void __launch_bounds__(kRrThreads, 12) k_rr_red_vec(Lay L, Lay Lc, fl
         const i64 row = (i64)z * L.ny + y;
         const i64 own = row * hx + k0;               // red half
         const i64 opp = L.half + row * hx + k0;      // black half
-        const bool hy0 = y > 0, hy1 = y < L.ny - 1, hz0 = z > 0, hz1 = z < L.nz - 1;
+        const bool hy0 = y > 0, hy1 = y < L.ny - 1;
+        const bool hz0 = z > 0 || (GHOST && L.zlo), hz1 = z < L.nz - 1 || (GHOST && L.zhi);
         const bool xw0 = (p == 0 && k0 == 0), xw1 = (p == 1 && k0 + 4 == hx);
         auto window = [&](const float *O, float (&m)[4], float (&q)[4]) {
             const float4 c4 = *reinterpret_cast<const float4 *>(O + opp);
@@ -795,6 +801,10 @@ __global__ void k_prolong_red_vec(Lay L, Lay Lc, const float *__restrict__ ec, f
 // half) and two scalars.
 constexpr int kProlThreads = 64;
 
+// GHOST: the fine level is a slab and Lc a view of the whole coarse level from the slab's first
+// coarse plane (Lc.zlo / Lc.zhi: the coarse planes next to the view are the neighbours', read
+// where the whole grid would read them instead of the wall's mirror)
+template <bool GHOST = false>
 __global__ void __launch_bounds__(kProlThreads, 10) k_prolong_red8(Lay L, Lay Lc, const float *__restrict__ ec, float *xv) {
     const int hx = L.hx, kv = hx >> 3;  // 8-cell groups per fine row
     const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -807,7 +817,7 @@ __global__ void __launch_bounds__(kProlThreads, 10) k_prolong_red8(Lay L, Lay Lc
     const int J = (int)(crowu % (unsigned)Lc.ny), K = (int)(crowu / (unsigned)Lc.ny);
     const int hxc = Lc.hx, ncx = Lc.nx;
     const int Js[3] = {max(J - 1, 0), J, min(J + 1, Lc.ny - 1)};
-    const int Ks[3] = {max(K - 1, 0), K, min(K + 1, Lc.nz - 1)};
+    const int Ks[3] = {(GHOST && Lc.zlo) ? K - 1 : max(K - 1, 0), K, (GHOST && Lc.zhi) ? K + 1 : min(K + 1, Lc.nz - 1)};
     float R[4][10];  // [2e + d][I - k0 + 1]
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -1020,13 +1030,31 @@ Lay make_lay(Dims d) {
     L.split = (d.nx % 2 == 0);
     L.hx = d.nx / 2;
     L.half = d.n / 2;
+    L.zlo = L.zhi = 0;
     return L;
+}
+
+// a slab (L.zlo / L.zhi): s-form only, split layout with hx % 4 == 0 (the decomposed mixed cycle)
+void launch_half32_slab(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
+                        bool from_zero) {
+    if (half_z_ok(L)) {
+        if (from_zero) run_half_z<true, true, 0, true>(s, L, h2, cf, b, x, col, Upd{});
+        else run_half_z<true, false, 0, true>(s, L, h2, cf, b, x, col, Upd{});
+        return;
+    }
+    const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
+    if (from_zero) k_half_vec<true, true, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
+    else k_half_vec<true, false, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
 }
 
 void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
                    const float *fz, const float *b, float *x, int col, bool from_zero) {
     Coef32 cf{sinv, fx, fy, fz};
     count_launch();
+    if (L.zlo || L.zhi) {
+        launch_half32_slab(s, L, (float)h2, cf, b, x, col, from_zero);
+        return;
+    }
     if (half_z_ok(L)) {
         if (sinv) {
             if (from_zero) run_half_z<true, true, 0>(s, L, (float)h2, cf, b, x, col, Upd{});
@@ -1060,6 +1088,11 @@ void launch_half32_update(cudaStream_t s, Lay L, double h2, const float *sinv, c
     count_launch();
     const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
     float *xv = const_cast<float *>(x);  // read only in the UPDATE variants
+    if (L.zlo || L.zhi) {  // a slab: s-form, FP64 solution (the decomposed mixed cycle)
+        if (half_z_ok(L)) run_half_z<true, false, 1, true>(s, L, (float)h2, cf, b, xv, 0, up);
+        else k_half_vec<true, false, 1, true><<<blocks_for(work), kThreads, 0, s>>>(L, (float)h2, cf, b, xv, 0, up);
+        return;
+    }
     if (half_z_ok(L)) {
         if (p2) {
             if (sinv) run_half_z<true, false, 2>(s, L, (float)h2, cf, b, xv, 0, up);
@@ -1094,7 +1127,8 @@ void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const fl
     if (red_only && L.split && L.hx % 4 == 0) {
         const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 4);
         const unsigned nb = (unsigned)((work + kRrThreads - 1) / kRrThreads);
-        if (sinv) k_rr_red_vec<true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        if (L.zlo || L.zhi) k_rr_red_vec<true, true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        else if (sinv) k_rr_red_vec<true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         else k_rr_red_vec<false><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         return;
     }
@@ -1106,7 +1140,9 @@ void launch_prolong32(cudaStream_t s, Lay L, Lay Lc, const float *ec, float *x, 
     if (only_col == 0 && kind == MG_PROLONG_TRILINEAR && L.split && Lc.split && Lc.nx % 8 == 0 &&
         2 * Lc.nx == L.nx && 2 * Lc.ny == L.ny && 2 * Lc.nz == L.nz) {
         const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 8);
-        k_prolong_red8<<<(unsigned)((work + kProlThreads - 1) / kProlThreads), kProlThreads, 0, s>>>(L, Lc, ec, x);
+        const unsigned nb = (unsigned)((work + kProlThreads - 1) / kProlThreads);
+        if (Lc.zlo || Lc.zhi) k_prolong_red8<true><<<nb, kProlThreads, 0, s>>>(L, Lc, ec, x);
+        else k_prolong_red8<<<nb, kProlThreads, 0, s>>>(L, Lc, ec, x);
         return;
     }
     if (only_col == 0 && L.split && L.hx % 4 == 0) {

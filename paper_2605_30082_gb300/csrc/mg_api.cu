@@ -702,6 +702,15 @@ int check_level(mg_handle *h, int level, int dtype, bool need_coarser) {
 
 }  // namespace
 
+namespace mg {
+Lay handle_lay32(mg_handle *h, int l) { return h->lv[l].lay; }
+float *handle_b32(mg_handle *h, int l) { return h->lv[l].b32; }
+float *handle_x32(mg_handle *h, int l) { return h->lv[l].x32; }
+void handle_vcycle32(mg_handle *h, int l) { vcycle32(h, l, h->lv[l].b32, h->lv[l].x32); }
+int handle_first_inner() { return kFirstAdaptive; }
+int handle_next_inner(double rr_prev, double rr, int k, double rtol) { return next_inner(rr_prev, rr, k, rtol); }
+}  // namespace mg
+
 extern "C" {
 
 void mg_default_opts(mg_opts *o) {

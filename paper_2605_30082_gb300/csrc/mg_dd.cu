@@ -17,6 +17,15 @@
 // Every cell sees the same arithmetic, in the same order, as in the whole-grid FP64 V-cycle,
 // so one V-cycle gives bitwise the same result for any number of slabs.  The exchange is a
 // device-to-device copy here; between GPUs it would be one send/receive per neighbour.
+//
+// The mixed-precision solve (precision MG_MIXED) decomposes the finest level only: FP32 slabs
+// in the colour-split layout with a ghost plane below and above in each colour half (mg::Lay
+// zlo / zhi), the finest level's FP32 kernels in their ghost variants, an exchange of the
+// colour just updated after every half sweep and after the prolongation, the red residuals'
+// restriction written straight into the whole-grid handle's FP32 level (the gather), the rest
+// of the inner V-cycle on that handle, and the FP64 outer loop slab by slab (the fused residual
+// kernel over each slab with its p ghost planes exchanged first; the norms and sums of p added
+// over the slabs).
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -40,7 +49,33 @@ struct Slab {
     double *fx, *fy; // low faces of the own planes
     double *fze;     // low z faces of the own planes and of the ghost above: planes + 1 planes
     double *invd, *dg;
+    // mixed precision, finest level: FP32 arrays in the slab layout `lay` (each colour half
+    // with a ghost plane below and above; the pointers at the red half's first own plane)
+    mg::Lay lay;
+    float *x32, *b32, *s32;
 };
+
+// p ghost planes, b~ and the FP32 slab arrays of the mixed solve: s = 1/rho of the whole grid
+// (natural FP64) into a slab's FP32 layout, its ghost planes included, rounded to nearest as
+// the whole-grid pack rounds it; z0 is the slab's first whole-grid plane (even, so colours agree)
+__global__ void k_pack_slab_s32(mg::Lay L, int z0, int nz_total, const double *__restrict__ s_whole, float *s32) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.nx) return;
+    const int rows = L.ny * (L.nz + 2);
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % L.ny, z = row / L.ny - 1;  // z = -1 .. nz (the ghost planes)
+        const int zg = z0 + z;
+        if (zg < 0 || zg >= nz_total) continue;  // beyond a wall: never read
+        const double v = s_whole[((mg::i64)zg * L.ny + y) * L.nx + x];
+        s32[((x + y + z) & 1) * L.half + ((mg::i64)z * L.ny + y) * L.hx + (x >> 1)] = mg::d2f_rn(v);
+    }
+}
+
+// out = (in - c) * scale, the mixed modes' scaled zero-mean right-hand side
+__global__ void k_sub_scalar_scale(mg::i64 n, const double *__restrict__ in, double c, double scale, double *out) {
+    const mg::i64 m = (mg::i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) out[m] = (in[m] - c) * scale;
+}
 
 __global__ void k_sub_scalar(mg::i64 n, const double *__restrict__ in, double c, double *out) {
     const mg::i64 m = (mg::i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,6 +135,11 @@ struct mg_dd {
     long long cyc_launches;
     bool cyc_tried;
     int have_op;
+    // mixed precision: the whole-grid handle's FP32 level 0 (the switch level), its layout and
+    // arrays, gathered into by the slabs' restriction and read by their prolongation
+    bool mixed;
+    mg::Lay clay;
+    float *cb32, *cx32;
     char msg[256];
 };
 
@@ -246,6 +286,96 @@ int vcycle(mg_dd *dd, int l, bool x_zero) {
     return smooth(dd, l, dd->o.post, 1);
 }
 
+// ---- the mixed-precision cycle: FP32 slabs of the finest level ------------------------------
+
+// the whole-grid handle's FP32 level 0 seen from slab S: its arrays from the slab's first coarse
+// plane (even, so colours agree), its neighbours' planes beside it (zlo / zhi of the slab)
+mg::Lay coarse_view(const mg_dd *dd, const Slab &S, mg::i64 *off) {
+    mg::Lay v = dd->clay;
+    v.nz = S.d.nz / 2;
+    v.n = (mg::i64)v.nx * v.ny * v.nz;
+    v.zlo = S.d.zlo;
+    v.zhi = S.d.zhi;
+    *off = (mg::i64)(S.z0 / 2) * v.ny * v.hx;
+    return v;
+}
+
+// colour c's first and last own planes of every slab's FP32 x into its neighbours' ghost planes
+int exchange32(mg_dd *dd, int c) {
+    std::vector<Slab> &R = dd->lv[0];
+    const size_t plane = (size_t)R[0].lay.ny * R[0].lay.hx;
+    return per_rank(dd, [&](int r, cudaStream_t st) -> int {
+        float *col = R[r].x32 + (size_t)c * R[r].lay.half;
+        if (r > 0) {
+            const Slab &B = R[r - 1];
+            DD_CUDA(dd, cudaMemcpyAsync(col - plane, B.x32 + (size_t)c * B.lay.half + (size_t)(B.lay.nz - 1) * plane,
+                                        4 * plane, cudaMemcpyDeviceToDevice, st));
+        }
+        if (r + 1 < dd->P)
+            DD_CUDA(dd, cudaMemcpyAsync(col + (size_t)R[r].lay.nz * plane, R[r + 1].x32 + (size_t)c * R[r + 1].lay.half,
+                                        4 * plane, cudaMemcpyDeviceToDevice, st));
+        return MG_OK;
+    });
+}
+
+// a half sweep of colour c on every slab, then the exchange of that colour
+int half_mixed(mg_dd *dd, int c, bool from_zero) {
+    std::vector<Slab> &R = dd->lv[0];
+    const double h2 = dd->o.h * dd->o.h;
+    const int rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+        mg::launch_half32(st, R[r].lay, h2, R[r].s32, nullptr, nullptr, nullptr, R[r].b32, R[r].x32, c, from_zero);
+        return MG_OK;
+    });
+    return rc ? rc : exchange32(dd, c);
+}
+
+// One FP32 V-cycle of the finest level, in the order of the whole-grid cycle: from x32 = 0
+// (from_zero) or from the slabs' x32; with alpha_shift, the last red half sweep adds
+// alpha x - shift to the slabs' FP64 p instead of storing x32.
+int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift) {
+    std::vector<Slab> &R = dd->lv[0];
+    const double h2 = dd->o.h * dd->o.h;
+    int rc;
+    for (int sw = 0; sw < dd->o.pre; ++sw) {
+        if ((rc = half_mixed(dd, 0, from_zero && sw == 0))) return rc;
+        if ((rc = half_mixed(dd, 1, false))) return rc;
+    }
+    // the red residuals (every black one is zero after the black sweep), restricted into the
+    // whole grid's coarse right-hand side (the gather)
+    rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+        mg::i64 off;
+        const mg::Lay cv = coarse_view(dd, R[r], &off);
+        mg::launch_resid_restrict32(st, R[r].lay, cv, 1.0 / h2, R[r].s32, nullptr, nullptr, nullptr, R[r].b32, R[r].x32,
+                                    dd->cb32 + off, true);
+        return MG_OK;
+    });
+    if (rc) return rc;
+    mg::handle_vcycle32(dd->ch, 0);  // the switch level down, on the caller's stream
+    // the prolongation back: the red cells of each slab from the coarse planes beside it
+    rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+        mg::i64 off;
+        const mg::Lay cv = coarse_view(dd, R[r], &off);
+        mg::launch_prolong32(st, R[r].lay, cv, dd->cx32 + off, R[r].x32, MG_PROLONG_TRILINEAR, 0);
+        return MG_OK;
+    });
+    if (rc) return rc;
+    if ((rc = exchange32(dd, 0))) return rc;
+    for (int sw = 0; sw < dd->o.post; ++sw) {
+        if ((rc = half_mixed(dd, 1, false))) return rc;
+        if (sw + 1 < dd->o.post || !alpha_shift) {
+            if ((rc = half_mixed(dd, 0, false))) return rc;
+            continue;
+        }
+        rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
+            mg::launch_half32_update(st, R[r].lay, h2, R[r].s32, nullptr, nullptr, nullptr, R[r].b32, R[r].x32, R[r].x,
+                                     nullptr, alpha_shift[0], alpha_shift[1]);
+            return MG_OK;
+        });
+        if (rc) return rc;
+    }
+    return MG_OK;
+}
+
 // Record one V-cycle of level 0 (x_zero false) on a private stream, the whole-grid handle's
 // launches included; nothing runs.  Where recording is refused the cycles launch call by call.
 void build_cycle_graph(mg_dd *dd) {
@@ -364,6 +494,111 @@ void *dd_alloc(mg_dd *dd, size_t bytes) {
     return p;
 }
 
+// The mixed-precision solve on the slabs, step for step the whole grid's cold-started mixed
+// loop: b~ = (b - mean b) h^2; the first inner right-hand side is b~ in FP32 scaled by 1 / |b~|;
+// each outer iteration runs `inner` FP32 V-cycles (the last one adding its correction to p), then
+// the FP64 residual of every slab, with p's ghost planes exchanged first, which also writes the
+// next scaled FP32 right-hand side and the partial sums of r^2 and p; the exact FP64 mean of p is
+// removed at exit.
+int solve_mixed(mg_dd *dd, const double *b, double *p, mg_stats *st) {
+    cudaStream_t s = dd->s;
+    EventPair ev;
+    DD_CUDA(dd, cudaEventCreate(&ev.e[0]));
+    DD_CUDA(dd, cudaEventCreate(&ev.e[1]));
+    DD_CUDA(dd, cudaEventRecord(ev.e[0], s));
+    const double n = (double)dd->o.nx * dd->o.ny * dd->o.nz;
+    const double h2 = dd->o.h * dd->o.h, ih2 = 1.0 / h2;
+    std::vector<Slab> &R = dd->lv[0];
+    double sb = 0.0;
+    for (Slab &S : R) {
+        mg::launch_sum_sumsq<double>(s, S.d.n, b + (size_t)S.z0 * S.d.nxy, dd->partials, dd->red, false);
+        double hb[2];
+        DD_CUDA(dd, cudaMemcpyAsync(hb, dd->red, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        DD_CUDA(dd, cudaStreamSynchronize(s));
+        sb += hb[0];
+    }
+    for (Slab &S : R) {
+        mg::count_launch();
+        k_sub_scalar_scale<<<blocks_for(S.d.n), kThreads, 0, s>>>(S.d.n, b + (size_t)S.z0 * S.d.nxy, sb / n, h2, S.b);
+        DD_CUDA(dd, cudaMemsetAsync(S.xe, 0, 8 * (size_t)(S.d.n + 2 * S.d.nxy), s));
+    }
+    double t, q0;
+    int rc = slab_sums_b(dd, &t, &q0);
+    if (rc) return rc;
+    const double nb = std::sqrt(q0) / h2;
+    double hist[MG_HIST_LEN];
+    int hn = 0, cycles = 0, outer = 0, status = MG_ERR_NOT_CONVERGED;
+    double rr = nb > 0.0 ? 1.0 : 0.0;
+    hist[hn++] = rr;
+    if (nb == 0.0 || rr <= dd->o.rtol) status = MG_OK;
+    const bool adaptive = dd->o.inner_cycles == 0;
+    int inner = adaptive ? mg::handle_first_inner() : dd->o.inner_cycles;
+    double scale = 1.0 / nb, rn = nb, mu = 0.0;
+    if (status == MG_ERR_NOT_CONVERGED)
+        for (Slab &S : R) mg::launch_zero_resid32(s, S.d, S.lay, S.b, ih2 * scale, S.b32);
+    while (status == MG_ERR_NOT_CONVERGED) {
+        if (adaptive && cycles + inner > dd->o.max_cycles) inner = dd->o.max_cycles - cycles;
+        if (inner < 1 || cycles + inner > dd->o.max_cycles) break;
+        for (int k = 0; k + 1 < inner; ++k)
+            if ((rc = vcycle_mixed(dd, k == 0, nullptr))) return rc;
+        const double as[2] = {1.0 / scale, mu};
+        if ((rc = vcycle_mixed(dd, inner == 1, as))) return rc;
+        scale = 1.0 / rn;
+        if ((rc = exchange(dd, 0))) return rc;  // p's ghost planes
+        for (int r = 0; r < dd->P; ++r) {
+            Slab &S = R[r];
+            mg::launch_fine_resid2(s, S.d, S.lay, h2, S.fx, S.fy, S.fze, S.dg, S.b, true, S.x, S.b32, (float)(ih2 * scale),
+                                   dd->partials, dd->red + 2 * r);
+        }
+        std::vector<double> hs(2 * (size_t)dd->P);
+        DD_CUDA(dd, cudaMemcpyAsync(hs.data(), dd->red, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s));
+        DD_CUDA(dd, cudaStreamSynchronize(s));
+        double q = 0.0, sp = 0.0;
+        for (int r = 0; r < dd->P; ++r) {
+            q += hs[2 * r];
+            sp += hs[2 * r + 1];
+        }
+        rn = std::sqrt(q) * ih2;
+        mu = sp / n;
+        const double rr_prev = rr;
+        rr = rn / nb;
+        cycles += inner;
+        ++outer;
+        if (adaptive) inner = mg::handle_next_inner(rr_prev, rr, inner, dd->o.rtol);
+        if (hn < MG_HIST_LEN) hist[hn++] = rr;
+        if (!std::isfinite(rr) || rr > 1e12) {
+            status = MG_ERR_DIVERGED;
+            break;
+        }
+        if (rr <= dd->o.rtol) status = MG_OK;
+    }
+    // exact zero-mean gauge at exit (the outer loop shifts by an FP32-accumulated mean)
+    if (nb > 0.0) {
+        double sx;
+        if ((rc = slab_sum_x(dd, &sx))) return rc;
+        for (Slab &S : R) mg::launch_add_const(s, S.d.n, S.x, -sx / n);
+    }
+    for (Slab &S : R)
+        DD_CUDA(dd, cudaMemcpyAsync(p + (size_t)S.z0 * S.d.nxy, S.x, 8 * (size_t)S.d.n, cudaMemcpyDeviceToDevice, s));
+    DD_CUDA(dd, cudaEventRecord(ev.e[1], s));
+    DD_CUDA(dd, cudaEventSynchronize(ev.e[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]);
+    DD_CUDA(dd, cudaGetLastError());
+    if (st) {
+        st->status = status;
+        st->cycles = cycles;
+        st->outer = outer;
+        st->relres = rr;
+        for (int k = 0; k < MG_HIST_LEN; ++k) st->relres_hist[k] = k < hn ? hist[k] : 0.0;
+        st->ms = ms;
+    }
+    if (status == MG_ERR_NOT_CONVERGED)
+        return dd_fail(dd, status, "not converged: relres %.3e after %d cycles", rr, cycles);
+    if (status == MG_ERR_DIVERGED) return dd_fail(dd, status, "diverged: relres %.3e", rr);
+    return MG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -404,14 +639,23 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
     mg::NvtxRange nvtx_("mg_dd_create");
     if (!out) return MG_ERR_ARG;
     *out = nullptr;
-    if (!o || o->precision != MG_FP64 || o->method != MG_METHOD_VCYCLE || o->inner_cycles != 1 ||
-        !(o->h > 0.0) || o->pre < 0 || o->post < 0 || o->max_cycles < 0 || o->warm_start)
+    if (!o || o->method != MG_METHOD_VCYCLE || !(o->h > 0.0) || o->pre < 0 || o->post < 0 || o->max_cycles < 0 ||
+        o->warm_start)
+        return MG_ERR_ARG;
+    const bool mixed = o->precision == MG_MIXED;
+    if (!mixed && (o->precision != MG_FP64 || o->inner_cycles != 1)) return MG_ERR_ARG;
+    // the mixed cycle cuts the finest level only, with the finest level's fast kernels: red-only
+    // restriction (pre >= 1), red-only trilinear prolongation (post >= 1) from a coarse level
+    // whose rows hold a multiple of 8 cells, and even first coarse planes (slabs of 4k planes)
+    if (mixed && (o->inner_cycles < 0 || o->pre < 1 || o->post < 1 || o->prolong != MG_PROLONG_TRILINEAR ||
+                  o->nx % 16 != 0 || ranks < 1 || o->nz % (4 * ranks) != 0))
         return MG_ERR_ARG;
     mg_dd *dd = new (std::nothrow) mg_dd();
     if (!dd) return MG_ERR_OOM;
     dd->o = *o;
+    dd->mixed = mixed;
     dd->s = static_cast<cudaStream_t>(stream);
-    if (mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, max_decomposed, &dd->plan) != MG_OK) {
+    if (mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, mixed ? 1 : max_decomposed, &dd->plan) != MG_OK) {
         delete dd;
         return MG_ERR_ARG;
     }
@@ -440,8 +684,23 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
             S.fx = A(n);
             S.fy = A(n);
             S.fze = A(n + nxy);
-            S.invd = A(n);
+            S.invd = mixed ? nullptr : A(n);
             S.dg = A(n);
+            if (mixed) {  // the FP32 slab layout: each colour half with its two ghost planes
+                S.lay = mg::make_lay(S.d);
+                S.lay.zlo = S.d.zlo;
+                S.lay.zhi = S.d.zhi;
+                const size_t plane = (size_t)S.lay.ny * S.lay.hx;
+                S.lay.half = (mg::i64)((S.d.nz + 2) * plane);
+                float *f[3];
+                for (float *&q : f) {
+                    q = static_cast<float *>(dd_alloc(dd, 4 * 2 * (size_t)S.lay.half));
+                    if (!q) ok = false;
+                }
+                S.x32 = f[0] ? f[0] + plane : nullptr;
+                S.b32 = f[1] ? f[1] + plane : nullptr;
+                S.s32 = f[2] ? f[2] + plane : nullptr;
+            }
         }
     }
     const mg::i64 n0 = (mg::i64)o->nx * o->ny * o->nz;
@@ -474,7 +733,12 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
         return rc;
     }
     dd->ch_nlev = mg_num_levels(dd->ch);
-    for (int k = 0; k < dd->ch_nlev && ok; ++k) {
+    if (mixed) {  // the slabs gather into, and prolong from, the handle's own FP32 level 0
+        dd->clay = mg::handle_lay32(dd->ch, 0);
+        dd->cb32 = mg::handle_b32(dd->ch, 0);
+        dd->cx32 = mg::handle_x32(dd->ch, 0);
+    }
+    for (int k = 0; k < dd->ch_nlev && ok && !mixed; ++k) {
         int dims[3];
         mg_level_dims(dd->ch, k, dims);
         const size_t n = (size_t)dims[0] * dims[1] * dims[2];
@@ -489,7 +753,10 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
     dd->exchanges = 0;
     dd->halo_bytes = 0;
     for (int l = 0; l < dd->ndec; ++l) {
-        const long long per = 2ll * (ranks - 1) * 8ll * pl.nx[l] * pl.ny[l];
+        // FP64: both colours of a plane; mixed (finest level only): the one colour just updated,
+        // FP32 (the outer loop's exchange of p's FP64 planes comes once per outer iteration)
+        const long long per = mixed ? 2ll * (ranks - 1) * 4ll * (pl.nx[l] / 2) * pl.ny[l]
+                                    : 2ll * (ranks - 1) * 8ll * pl.nx[l] * pl.ny[l];
         const long long k = 2ll * o->pre + 2ll * o->post + 1;
         dd->exchanges += k;
         dd->halo_bytes += k * per;
@@ -575,6 +842,12 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
             DD_CUDA(dd, cudaMemcpyAsync(S.fze + S.d.n, dd->gfz + off + S.d.n, pb, cudaMemcpyDeviceToDevice, s));
         else
             DD_CUDA(dd, cudaMemsetAsync(S.fze + S.d.n, 0, pb, s));
+        if (dd->mixed) {  // s = 1/rho in FP32 over the slab's planes and its ghost planes
+            const int rows = S.lay.ny * (S.lay.nz + 2);
+            const dim3 grd((unsigned)((S.lay.nx + 127) / 128), (unsigned)(rows < 65535 ? rows : 65535));
+            mg::count_launch();
+            k_pack_slab_s32<<<grd, 128, 0, s>>>(S.lay, S.z0, dd->o.nz, dd->sinv, S.s32);
+        }
     }
     // decomposed levels: diagonal, then the next level's faces slab by slab
     for (int l = 0; l < dd->ndec; ++l) {
@@ -607,8 +880,9 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
     int rc = mg_set_face_coeffs(dd->ch, dd->abx, dd->aby, dd->abz);
     if (rc) return dd_fail(dd, rc, "switch level: %s", mg_last_error(dd->ch));
     dd->have_op = 1;
-    // the cycle's buffers and arguments do not depend on the operator: recorded once
-    if (!dd->cyc_tried) build_cycle_graph(dd);
+    // the cycle's buffers and arguments do not depend on the operator: recorded once (the FP64
+    // cycle; the mixed cycle's last sweep takes each outer iteration's update scalars)
+    if (!dd->cyc_tried && !dd->mixed) build_cycle_graph(dd);
     return MG_OK;
 }
 
@@ -616,6 +890,7 @@ int mg_dd_vcycle(mg_dd *dd, const double *b, double *x) {
     mg::NvtxRange nvtx_("mg_dd_vcycle");
     if (!dd) return MG_ERR_ARG;
     if (!b || !x) return dd_fail(dd, MG_ERR_ARG, "null array");
+    if (dd->mixed) return dd_fail(dd, MG_ERR_ARG, "mg_dd_vcycle: FP64 decompositions only");
     if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
     cudaStream_t s = dd->s;
     for (Slab &S : dd->lv[0]) {
@@ -639,6 +914,7 @@ int mg_dd_solve(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     if (!dd) return MG_ERR_ARG;
     if (!b || !p) return dd_fail(dd, MG_ERR_ARG, "null array");
     if (!dd->have_op) return dd_fail(dd, MG_ERR_STATE, "coefficients not set");
+    if (dd->mixed) return solve_mixed(dd, b, p, st);
     cudaStream_t s = dd->s;
     EventPair ev;
     DD_CUDA(dd, cudaEventCreate(&ev.e[0]));

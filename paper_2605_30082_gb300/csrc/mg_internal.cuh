@@ -39,12 +39,19 @@ inline Dims make_dims(int nx, int ny, int nz) {
 
 // Storage layout of an FP32 level: colour-split (all red cells, then all black, each
 // colour row by row, cell x of a row at k = x >> 1) when nx is even, else natural.
+// A z slab of a decomposed level (mg_dd.cu, split layout only) keeps a ghost plane below and
+// above its nz own planes in each colour half: `half` is then the stride between the two
+// halves (nz + 2 planes each), the arrays point at the red half's first own plane, and zlo /
+// zhi say whether the ghost below / above holds a neighbour's values (the planes between
+// slabs count as interior) or is a wall; the slab starts at an even whole-grid plane, so the
+// colour of a cell is the same as on the whole grid.
 struct Lay {
     int nx, ny, nz;
     i64 n;
     bool split;
     int hx;     // nx / 2
-    i64 half;   // n / 2
+    i64 half;   // n / 2 (a slab: the colour stride)
+    int zlo, zhi;
 };
 Lay make_lay(Dims d);
 
@@ -136,6 +143,19 @@ unsigned long long launches_total();
 // private stream)
 cudaStream_t swap_handle_stream(mg_handle *h, cudaStream_t s);
 
+// A mixed-precision handle's FP32 level l, for the decomposed mixed cycle (mg_dd.cu), which
+// runs the levels from its switch level down on a whole-grid handle: the level's storage layout,
+// its right-hand side and iterate arrays, and one FP32 V-cycle of the handle from level l down
+// (from x = 0, on that level's b32, into its x32; the handle's options and recorded tail)
+Lay handle_lay32(mg_handle *h, int l);
+float *handle_b32(mg_handle *h, int l);
+float *handle_x32(mg_handle *h, int l);
+void handle_vcycle32(mg_handle *h, int l);
+// the adaptive inner-cycle count of the mixed outer loop: the first, and the next from the
+// contraction of the last outer iteration (k cycles from relres rr_prev to rr)
+int handle_first_inner();
+int handle_next_inner(double rr_prev, double rr, int k, double rtol);
+
 // NVTX range for the lifetime of the object: a profiler attached to the process (Nsight
 // Systems, ncu --nvtx) sees each entry point as one named range; without one the calls do
 // nothing (header-only NVTX3, which looks up a tool only when one is injected)
@@ -194,7 +214,11 @@ void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 // ---- V-cycle kernels --------------------------------------------------------------
 // ---- FP32 colour-split level kernels (kernels_split.cu) ----
 // half sweep of colour col in place; sinv = 1/rho per cell (beta = (s_L + s_R)/2) when
-// non-null, else the low-face arrays; from_zero: the other colour is taken as zero
+// non-null, else the low-face arrays; from_zero: the other colour is taken as zero.
+// On a slab (L.zlo / L.zhi; see Lay) the V-cycle kernels of the finest level take its ghost
+// planes as z neighbours: s-form, split layout with hx % 4 == 0, restriction of red residuals
+// only, trilinear prolongation of the red cells from a coarse view (Lc.zlo / Lc.zhi) whose
+// nx is a multiple of 8; other cases are not supported on slabs
 void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
                    const float *fz, const float *b, float *x, int col, bool from_zero);
 // the last red half sweep of the finest level with the outer update fused in: the new red
@@ -306,8 +330,8 @@ void launch_fine_residual(cudaStream_t s, Dims d, Lay L, double ih2, const doubl
 // fine FP64 residual in diagonal form, h^2 r = h^2 b - (diag p_c - sum_f beta_f p_nb):
 // out[0] = sum (h^2 r)^2, out[1] = sum p; optional r32 = s32 * h^2 r in the level-0 layout L.
 // On a slab of a decomposed grid (d.zlo or d.zhi, even nx; p with its ghost planes beside the
-// own ones, fz with the face to the ghost above) the ghost planes count as interior neighbours;
-// there b is unscaled and no FP32 copy is written (b_scaled and r32 are ignored)
+// own ones, fz with the face to the ghost above) the ghost planes count as interior neighbours,
+// and r32 is stored in the slab's layout L (L.half the colour stride)
 void launch_fine_resid2(cudaStream_t s, Dims d, Lay L, double h2, const double *fx, const double *fy,
                         const double *fz, const double *diag, const double *b, bool b_scaled, const double *p,
                         float *r32, float s32, double *partials, double *out);

@@ -129,8 +129,8 @@ def test_dd_solve_matches_whole_grid_and_oracle(ranks, max_dec):
 def test_dd_errors():
     dims = (32, 32, 32)
     o = _opts(dims, 1 / 32)
-    o.precision = L.MG_MIXED
-    assert L.mg_dd_create(o, 2)[0] == L.MG_ERR_ARG           # FP64 only
+    o.precision = L.MG_MIXED_DF
+    assert L.mg_dd_create(o, 2)[0] == L.MG_ERR_ARG           # FP64 or MG_MIXED only
     assert L.mg_dd_create(_opts(dims, 1 / 32), 32)[0] == L.MG_ERR_ARG  # one plane per slab
     dd = DD(dims, 2, h=1 / 32)
     b = torch.zeros((32, 32, 32), dtype=torch.float64, device="cuda")
@@ -168,3 +168,66 @@ def test_dd_solve_at_512_in_four_slabs():
     rel_t = float(torch.linalg.vector_norm(pd - pw) / torch.linalg.vector_norm(pw))
     assert rel_t <= 1e-12, rel_t
     dd.close()
+
+
+def _mixed_opts(dims, h, inner, rtol=1e-11, **kw):
+    o = _opts(dims, h, rtol=rtol, **kw)
+    o.precision = L.MG_MIXED
+    o.inner_cycles = inner
+    return o
+
+
+@pytest.mark.parametrize("ranks,inner", [(2, 1), (4, 1), (2, 3), (4, 0)])
+def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
+    """The mixed solve with its finest level cut into slabs (FP32 slab kernels with ghost planes,
+    the coarse levels on one whole-grid handle, the FP64 outer loop slab by slab) follows the
+    whole-grid mixed solve: every cell sees the same arithmetic, so the residual histories agree
+    (the norms are sums in another order) and so does p, up to the order of the exit gauge's sum;
+    and it reaches the oracle's exact discrete solution."""
+    n = 64
+    c = dropfilm_case(n)
+    dims = (n, n, n)
+    rho = dev(c["rho"])
+    b = dev(c["b"])
+    s = Solver(dims, h=c["h"], precision="mixed", coarsest=4, rtol=1e-11, inner_cycles=inner)
+    s.set_density(rho)
+    pw = s.solve(b)
+    st, h = L.mg_dd_create(_mixed_opts(dims, c["h"], inner), ranks, 0)
+    assert st == L.MG_OK, st
+    st, plan = L.mg_dd_get_plan(h)
+    assert plan.switch_level == 1  # the mixed cycle cuts the finest level only
+    assert L.mg_dd_set_density(h, rho, dims) == L.MG_OK
+    pd = torch.zeros_like(b)
+    sts = L.mg_stats()
+    assert L.mg_dd_solve(h, b, pd, dims, sts) == L.MG_OK, L.mg_dd_last_error(h)
+    assert sts.relres <= 1e-11
+    assert (sts.cycles, sts.outer) == (s.last_stats.cycles, s.last_stats.outer)
+    hd, hw = np.array(sts.history()), np.array(s.last_stats.history())
+    assert np.allclose(hd, hw, rtol=1e-12, atol=0.0)
+    # every cell sees the whole-grid arithmetic: p differs by the order of the gauge sums only
+    assert rel(host(pd), host(pw)) <= 1e-15
+    assert abs(float(pd.mean())) <= 1e-14 * float(pd.abs().max())
+    p_ex = O.Multigrid(c["faces"], c["h"], coarsest=4).solve_exact(c["b"])[0]
+    assert rel(host(pd), p_ex) <= 1e-9
+    _, ex, by = L.mg_dd_traffic(h)
+    k = 2 * 2 + 2 * 2 + 1
+    assert ex == k and by == k * 2 * (ranks - 1) * 4 * (n // 2) * n
+    L.mg_dd_destroy(h)
+    s.close()
+
+
+def test_dd_mixed_rejects_what_it_does_not_cut():
+    dims = (64, 64, 64)
+    h = 1 / 64
+    for kw, ranks in ((dict(pre=0), 2), (dict(post=0), 2), (dict(prolong=L.MG_PROLONG_CONSTANT), 2), ({}, 32)):
+        assert L.mg_dd_create(_mixed_opts(dims, h, 1, **kw), ranks)[0] == L.MG_ERR_ARG, (kw, ranks)
+    assert L.mg_dd_create(_mixed_opts((72, 64, 64), h, 1), 2)[0] == L.MG_ERR_ARG  # nx not a multiple of 16
+    assert L.mg_dd_create(_mixed_opts((64, 64, 40), h, 1), 4)[0] == L.MG_ERR_ARG  # 10 planes per slab
+    o = _mixed_opts(dims, h, 1)
+    o.precision = L.MG_MIXED_DF
+    assert L.mg_dd_create(o, 2)[0] == L.MG_ERR_ARG
+    st, hd = L.mg_dd_create(_mixed_opts(dims, h, 1), 2)
+    assert st == L.MG_OK
+    b = torch.zeros(dims, dtype=torch.float64, device="cuda")
+    assert L.mg_dd_vcycle(hd, b, b.clone(), dims) == L.MG_ERR_ARG  # FP64 decompositions only
+    L.mg_dd_destroy(hd)
