@@ -9,7 +9,11 @@ The plan is host-only library code.  Checked here without a GPU:
     with its neighbours, and must find bitwise the whole grid's planes in its ghost planes; the
     restriction of its own planes must be bitwise its planes of the next level (pairs never
     straddle two slabs); and the slabs' restrictions gathered on rank 0 at the switch level
-    must be bitwise the whole-grid coarse array.
+    must be bitwise the whole-grid coarse array;
+  - for the mixed decomposition's FP32 storage, with 2 and 4 gloo ranks: slabs of 4k planes
+    keep the whole grid's colours in their own colour-split storage, a per-colour exchange
+    fills each colour half's ghost planes with bitwise the whole grid's split planes, and a
+    slab's view of the whole coarse level starts at an even plane (the same colours).
 """
 import os
 import socket
@@ -137,6 +141,87 @@ def test_halo_exchange_and_gather_follow_the_plan_gloo(world, dims, coarsest):
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_worker, args=(r, world, port, dims, coarsest, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, checks, err in res:
+        assert err is None, (rank, err)
+        assert checks > 0
+
+
+def _split(a):
+    """Colour-split storage of a whole-grid (or slab) array whose first plane is even: all cells
+    with (x + y + z) even, then the odd ones, each colour row by row with cell x at k = x // 2."""
+    nz, ny, nx = a.shape
+    out = np.zeros((2, nz, ny, nx // 2))
+    z, y, x = np.meshgrid(range(nz), range(ny), range(nx), indexing="ij")
+    c = (x + y + z) % 2
+    out[c, z, y, x // 2] = a
+    return out
+
+
+def _worker_split(rank, world, port, dims, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nx, ny, nz = dims
+        m = nz // world
+        assert m % 4 == 0  # slabs of 4k planes: even first planes on this level and the next
+        g = np.random.default_rng(11).standard_normal((nz, ny, nx))
+        whole = _split(g)
+        z0 = rank * m
+        # the slab's own planes in its own split storage: the whole grid's colours (z0 even)
+        own = _split(g[z0:z0 + m])
+        assert np.array_equal(own, whole[:, z0:z0 + m]), "slab colours"
+        slab = np.zeros((2, m + 2, ny, nx // 2))  # each colour half: ghost below, own planes, ghost above
+        slab[:, 1:-1] = own
+        checks = 0
+        for c in (0, 1):  # one colour per exchange, as after a half sweep of that colour
+            t = torch.from_numpy(slab[c])
+            reqs = []
+            if rank > 0:
+                reqs.append(dist.isend(t[1].clone(), rank - 1, tag=10 + 2 * c))
+                reqs.append(dist.irecv(t[0], rank - 1, tag=11 + 2 * c))
+            if rank + 1 < world:
+                reqs.append(dist.isend(t[m].clone(), rank + 1, tag=11 + 2 * c))
+                reqs.append(dist.irecv(t[m + 1], rank + 1, tag=10 + 2 * c))
+            for r in reqs:
+                r.wait()
+            if rank > 0:
+                assert np.array_equal(slab[c, 0], whole[c, z0 - 1]), (rank, c, "ghost below")
+                checks += 1
+            if rank + 1 < world:
+                assert np.array_equal(slab[c, m + 1], whole[c, z0 + m]), (rank, c, "ghost above")
+                checks += 1
+        # the coarse view: the slab's coarse planes start at an even whole-grid plane, so their
+        # colours in the whole coarse level's storage are the slab's own
+        zc0 = z0 // 2
+        gc = np.random.default_rng(12).standard_normal((nz // 2, ny // 2, nx // 2))
+        assert zc0 % 2 == 0
+        assert np.array_equal(_split(gc[zc0:zc0 + m // 2]), _split(gc)[:, zc0:zc0 + m // 2]), "coarse view"
+        q.put((rank, checks + 1, None))
+    except Exception as e:
+        q.put((rank, -1, repr(e)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,dims", [(2, (16, 12, 16)), (4, (16, 8, 32))])
+def test_split_layout_exchange_per_colour_gloo(world, dims):
+    """The mixed decomposition's layout: each rank's colour-split slab (ghost plane below and
+    above in each colour half) receives its neighbours' boundary planes one colour at a time
+    and must find bitwise the whole grid's split planes in its ghosts."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_split, args=(r, world, port, dims, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = sorted(q.get(timeout=180) for _ in procs)
