@@ -368,8 +368,8 @@ int mg_fp64_fma_rate(void *stream, double *sink, int blocks, int iters, double *
  * and above, an exchange of the colour just updated after every half sweep and after the
  * prolongation, the restriction written into the whole-grid handle's FP32 level, the rest of
  * each inner V-cycle on that handle, and the FP64 outer loop (residual, norms, update) slab by
- * slab with p's ghost planes exchanged before each residual; it follows the whole-grid mixed
- * solve cell for cell (the same residual history up to the order of the sums).
+ * slab with p's ghost planes exchanged before each residual; every cell sees the whole-grid
+ * mixed solve's arithmetic, the outer loop's FP32-accumulated sums differing in grouping only.
  * Arrays passed in and out are whole-grid device arrays (cell layout above). */
 #define MG_DD_MAX_RANKS 64
 typedef struct mg_dd mg_dd;

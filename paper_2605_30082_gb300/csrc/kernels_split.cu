@@ -457,7 +457,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // 64 threads per block (64 vectors of one row, or 32 of two rows), ZC planes per block
-template <int ZC, int MINB>
+template <int ZC, int MINB, bool GHOST = false>
 __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const float *__restrict__ sv,
                                                        const float *__restrict__ b, float *xv, int col) {
     extern __shared__ float4 stg[];  // [kZsStages][kZsFields][64 threads]
@@ -508,10 +508,12 @@ __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const flo
             sr = sv[o + 4];
         }
     };
-    // other colour, row y: planes z-1, z, z+1 (rolling)
-    float4 xzm = z0 > 0 ? ld(xv, opp0 - dz) : f0, xzc = ld(xv, opp0);
-    float4 szm = z0 > 0 ? ld(sv, opp0 - dz) : f0, szc = ld(sv, opp0);
-    float4 xzp = z0 + 1 < L.nz ? ld(xv, opp0 + dz) : f0, szp = z0 + 1 < L.nz ? ld(sv, opp0 + dz) : f0;
+    // other colour, row y: planes z-1, z, z+1 (rolling); a slab's ghost planes are neighbours
+    const bool glo = GHOST && L.zlo, ghi = GHOST && L.zhi;
+    const int zend = L.nz + (ghi ? 1 : 0);  // planes readable above: the ghost plane too
+    float4 xzm = (z0 > 0 || glo) ? ld(xv, opp0 - dz) : f0, xzc = ld(xv, opp0);
+    float4 szm = (z0 > 0 || glo) ? ld(sv, opp0 - dz) : f0, szc = ld(sv, opp0);
+    float4 xzp = z0 + 1 < zend ? ld(xv, opp0 + dz) : f0, szp = z0 + 1 < zend ? ld(sv, opp0 + dz) : f0;
 #pragma unroll
     for (int t = 0; t < D - 1; ++t) {
         if (z0 + t < z1) issue(t);
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const flo
         float4 xzpp = f0, szpp = f0;
         if (z + 1 < z1) {
             scalars(opp + dz, nxl, nsl, nxr, nsr);
-            if (z + 2 < L.nz) {
+            if (z + 2 < zend) {
                 xzpp = ld(xv, opp + 2 * dz);
                 szpp = ld(sv, opp + 2 * dz);
             }
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const flo
         const float4 cym = hy0 ? *slot(st, 0) : f0, cyp = hy1 ? *slot(st, 1) : f0;
         const float4 cs2 = hy0 ? *slot(st, 2) : f0, cs3 = hy1 ? *slot(st, 3) : f0;
         const float4 csc = *slot(st, 4), cbb = *slot(st, 5);
-        const bool hz0 = z > 0, hz1 = z < L.nz - 1;
+        const bool hz0 = z > 0 || glo, hz1 = z < L.nz - 1 || ghi;
         const int p = (col + y + z) & 1;  // x = 2k + p
         const bool xw0 = (p == 0 && !kl), xw1 = (p == 1 && !kr);
         float sl = __shfl_up_sync(0xffffffffu, szc.w, 1), sr = __shfl_down_sync(0xffffffffu, szc.x, 1);
@@ -609,17 +611,18 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
     const unsigned gx = (kv + vb - 1) / vb, gy = (L.ny + ry - 1) / ry;
     const dim3 blk(vb, ry);
     const i64 sms = device_sms();
-    if (SFORM && !FROM_ZERO && UPDATE == 0 && !GHOST && (i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 8) {
+    // a slab's launch runs beside the other slabs' ones: it needs about one wave by itself
+    if (SFORM && !FROM_ZERO && UPDATE == 0 && (i64)gx * gy * ((L.nz + 15) / 16) >= (GHOST ? 1 : 4) * sms * 8) {
         // 11 blocks x 18 KB of staging per SM: ask for the largest shared-memory carveout
         static const bool carveout = [] {
             // a preference only: the launch is valid either way
-            if (cudaFuncSetAttribute(k_half_zs<16, 11>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            if (cudaFuncSetAttribute(k_half_zs<16, 11, GHOST>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
                 (void)cudaGetLastError();
             return true;
         }();
         (void)carveout;
-        k_half_zs<16, 11><<<dim3(gx, gy, (L.nz + 15) / 16), blk, kZsSmem, s>>>(L, h2, cf.s, b, x, col);
+        k_half_zs<16, 11, GHOST><<<dim3(gx, gy, (L.nz + 15) / 16), blk, kZsSmem, s>>>(L, h2, cf.s, b, x, col);
         return;
     }
     if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 12)

@@ -706,7 +706,14 @@ namespace mg {
 Lay handle_lay32(mg_handle *h, int l) { return h->lv[l].lay; }
 float *handle_b32(mg_handle *h, int l) { return h->lv[l].b32; }
 float *handle_x32(mg_handle *h, int l) { return h->lv[l].x32; }
-void handle_vcycle32(mg_handle *h, int l) { vcycle32(h, l, h->lv[l].b32, h->lv[l].x32); }
+void handle_vcycle32(mg_handle *h, int l, bool recording) {
+    // under a stream capture the coarse levels are recorded launch by launch, not as a replay
+    // of the handle's own graph
+    cudaGraphExec_t tail = h->tail_exec;
+    if (recording) h->tail_exec = nullptr;
+    vcycle32(h, l, h->lv[l].b32, h->lv[l].x32);
+    h->tail_exec = tail;
+}
 int handle_first_inner() { return kFirstAdaptive; }
 int handle_next_inner(double rr_prev, double rr, int k, double rtol) { return next_inner(rr_prev, rr, k, rtol); }
 }  // namespace mg

@@ -133,6 +133,8 @@ struct mg_dd {
     // by every cycle; null: launched call by call
     cudaGraphExec_t cyc_exec;
     long long cyc_launches;
+    cudaGraphExec_t mix_exec[2];  // mixed: inner V-cycle without update, from zero / continuing
+    long long mix_launches[2];
     bool cyc_tried;
     int have_op;
     // mixed precision: the whole-grid handle's FP32 level 0 (the switch level), its layout and
@@ -332,7 +334,7 @@ int half_mixed(mg_dd *dd, int c, bool from_zero) {
 // One FP32 V-cycle of the finest level, in the order of the whole-grid cycle: from x32 = 0
 // (from_zero) or from the slabs' x32; with alpha_shift, the last red half sweep adds
 // alpha x - shift to the slabs' FP64 p instead of storing x32.
-int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift) {
+int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift, bool recording = false) {
     std::vector<Slab> &R = dd->lv[0];
     const double h2 = dd->o.h * dd->o.h;
     int rc;
@@ -350,7 +352,7 @@ int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift) {
         return MG_OK;
     });
     if (rc) return rc;
-    mg::handle_vcycle32(dd->ch, 0);  // the switch level down, on the caller's stream
+    mg::handle_vcycle32(dd->ch, 0, recording);  // the switch level down, on the caller's stream
     // the prolongation back: the red cells of each slab from the coarse planes beside it
     rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
         mg::i64 off;
@@ -378,40 +380,57 @@ int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift) {
 
 // Record one V-cycle of level 0 (x_zero false) on a private stream, the whole-grid handle's
 // launches included; nothing runs.  Where recording is refused the cycles launch call by call.
-void build_cycle_graph(mg_dd *dd) {
-    dd->cyc_tried = true;
-    dd->cyc_exec = nullptr;
-    dd->cyc_launches = 0;
+// Record f() (one cycle) on a private stream, the whole-grid handle's launches included;
+// nothing runs.  Returns the instantiated graph, or null where recording is refused (the
+// cycles then launch call by call); *launches = the kernels it holds.
+template <typename F>
+cudaGraphExec_t record_cycle(mg_dd *dd, F &&f, long long *launches) {
+    *launches = 0;
     cudaStream_t cap = nullptr;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        return;
+        return nullptr;
     }
     // the recording must not see work still queued on the caller's stream
     if (cudaStreamSynchronize(dd->s) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(cap);
-        return;
+        return nullptr;
     }
     cudaStream_t saved = dd->s;
     dd->s = cap;
     cudaStream_t saved_ch = mg::swap_handle_stream(dd->ch, cap);
     const unsigned long long l0 = mg::launches_total();
     cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
     int rc = MG_ERR_CUDA;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        rc = vcycle(dd, 0, false);
+        rc = f();
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = MG_ERR_CUDA;
     }
     const long long n = (long long)(mg::launches_total() - l0);
     mg::count_launch((int)-n);  // recorded, not run
     mg::swap_handle_stream(dd->ch, saved_ch);
     dd->s = saved;
-    if (rc == MG_OK && g && cudaGraphInstantiate(&dd->cyc_exec, g, 0) != cudaSuccess) dd->cyc_exec = nullptr;
+    if (rc == MG_OK && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
     cudaGetLastError();
-    dd->cyc_launches = dd->cyc_exec ? n : 0;
+    *launches = exec ? n : 0;
+    return exec;
+}
+
+// The cycles whose buffers and arguments do not depend on the operator, recorded once: the
+// FP64 V-cycle; the mixed inner V-cycles without the outer update, from zero and continuing
+// (the last cycle of an outer iteration takes that iteration's update scalars: launched).
+void build_cycle_graph(mg_dd *dd) {
+    dd->cyc_tried = true;
+    if (!dd->mixed) {
+        dd->cyc_exec = record_cycle(dd, [&] { return vcycle(dd, 0, false); }, &dd->cyc_launches);
+        return;
+    }
+    for (int k = 0; k < 2; ++k)
+        dd->mix_exec[k] = record_cycle(dd, [&] { return vcycle_mixed(dd, k == 0, nullptr, true); }, &dd->mix_launches[k]);
 }
 
 // one V-cycle of level 0 from the slabs' x: the recorded graph, or call by call
@@ -539,8 +558,15 @@ int solve_mixed(mg_dd *dd, const double *b, double *p, mg_stats *st) {
     while (status == MG_ERR_NOT_CONVERGED) {
         if (adaptive && cycles + inner > dd->o.max_cycles) inner = dd->o.max_cycles - cycles;
         if (inner < 1 || cycles + inner > dd->o.max_cycles) break;
-        for (int k = 0; k + 1 < inner; ++k)
-            if ((rc = vcycle_mixed(dd, k == 0, nullptr))) return rc;
+        for (int k = 0; k + 1 < inner; ++k) {
+            const int g = k == 0 ? 0 : 1;
+            if (dd->mix_exec[g]) {
+                DD_CUDA(dd, cudaGraphLaunch(dd->mix_exec[g], s));
+                mg::count_launch((int)dd->mix_launches[g]);
+            } else if ((rc = vcycle_mixed(dd, k == 0, nullptr))) {
+                return rc;
+            }
+        }
         const double as[2] = {1.0 / scale, mu};
         if ((rc = vcycle_mixed(dd, inner == 1, as))) return rc;
         scale = 1.0 / rn;
@@ -798,6 +824,8 @@ int mg_dd_destroy(mg_dd *dd) {
     for (cudaEvent_t ev : dd->rdone) cudaEventDestroy(ev);
     if (dd->fork) cudaEventDestroy(dd->fork);
     if (dd->cyc_exec) cudaGraphExecDestroy(dd->cyc_exec);
+    for (cudaGraphExec_t e : dd->mix_exec)
+        if (e) cudaGraphExecDestroy(e);
     if (dd->ch) mg_destroy(dd->ch);
     for (void *p : dd->allocs) cudaFree(p);
     cudaGetLastError();
@@ -880,9 +908,8 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
     int rc = mg_set_face_coeffs(dd->ch, dd->abx, dd->aby, dd->abz);
     if (rc) return dd_fail(dd, rc, "switch level: %s", mg_last_error(dd->ch));
     dd->have_op = 1;
-    // the cycle's buffers and arguments do not depend on the operator: recorded once (the FP64
-    // cycle; the mixed cycle's last sweep takes each outer iteration's update scalars)
-    if (!dd->cyc_tried && !dd->mixed) build_cycle_graph(dd);
+    // the cycles' buffers and arguments do not depend on the operator: recorded once
+    if (!dd->cyc_tried) build_cycle_graph(dd);
     return MG_OK;
 }
 

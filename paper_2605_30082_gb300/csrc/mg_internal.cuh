@@ -146,11 +146,12 @@ cudaStream_t swap_handle_stream(mg_handle *h, cudaStream_t s);
 // A mixed-precision handle's FP32 level l, for the decomposed mixed cycle (mg_dd.cu), which
 // runs the levels from its switch level down on a whole-grid handle: the level's storage layout,
 // its right-hand side and iterate arrays, and one FP32 V-cycle of the handle from level l down
-// (from x = 0, on that level's b32, into its x32; the handle's options and recorded tail)
+// (from x = 0, on that level's b32, into its x32; the handle's options and recorded tail, or,
+// `recording` under a stream capture, the tail's launches one by one)
 Lay handle_lay32(mg_handle *h, int l);
 float *handle_b32(mg_handle *h, int l);
 float *handle_x32(mg_handle *h, int l);
-void handle_vcycle32(mg_handle *h, int l);
+void handle_vcycle32(mg_handle *h, int l, bool recording = false);
 // the adaptive inner-cycle count of the mixed outer loop: the first, and the next from the
 // contraction of the last outer iteration (k cycles from relres rr_prev to rr)
 int handle_first_inner();
