@@ -55,8 +55,8 @@ struct Slab {
     float *x32, *b32, *s32;
 };
 
-// p ghost planes, b~ and the FP32 slab arrays of the mixed solve: s = 1/rho of the whole grid
-// (natural FP64) into a slab's FP32 layout, its ghost planes included, rounded to nearest as
+// The mixed solve's FP32 s = 1/rho of one slab: the whole grid's s (natural FP64) over the
+// slab's planes and its ghost planes into the slab's colour-split layout, rounded to nearest as
 // the whole-grid pack rounds it; z0 is the slab's first whole-grid plane (even, so colours agree)
 __global__ void k_pack_slab_s32(mg::Lay L, int z0, int nz_total, const double *__restrict__ s_whole, float *s32) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
