@@ -335,12 +335,13 @@ def parity_gate(args, b, w, rho, s, p_mixed, lam, p_fp64, t_mixed, t_fp64, time_
 
 # ---------------------------------------------------------------- domain decomposition
 
-def decomposed_solve(args, b, rho, p_whole, t_whole, cyc_whole, precision="fp64", ranks=4):
+def decomposed_solve(args, b, rho, p_whole, t_whole, cyc_whole, precision="fp64", ranks=4, max_decomposed=0):
     """The solve of the same workload cut into `ranks` z slabs held on this GPU (mg_dd_*), timed
     like the whole-grid solve of the same precision (median of 3): FP64 (every level above the
     switch level cut) or mixed (the finest level cut, FP32 slabs inside the FP64 outer loop, the
-    adaptive inner cycles).  Its cost over the whole-grid solve is the halo copies and the
-    per-slab launches; the pressure must agree with the whole-grid one."""
+    adaptive inner cycles), every level above the switch level cut (at most max_decomposed, 0:
+    as deep as allowed).  Its cost over the whole-grid solve is the halo copies and the per-slab
+    launches; the pressure must agree with the whole-grid one."""
     import torch
 
     from paper_2605_30082_gb300 import _lib as L
@@ -354,7 +355,7 @@ def decomposed_solve(args, b, rho, p_whole, t_whole, cyc_whole, precision="fp64"
         o.precision = L.MG_FP64
     else:
         o.precision, o.inner_cycles = L.MG_MIXED, INNER
-    st, h = L.mg_dd_create(o, ranks)
+    st, h = L.mg_dd_create(o, ranks, max_decomposed)
     if st != L.MG_OK:
         return {"unavailable": f"mg_dd_create: status {st}"}
     try:
@@ -533,8 +534,12 @@ def run_ours(args):
     dd = None
     if not args.no_fp64:
         gate = parity_gate(args, b, w, rho, s, p_mixed, lam, p_fp64, t_mixed, t_fp64, time_solve)
+        # the mixed solve cut as deep as allowed, and with the finest level only cut: the switch
+        # level's trade (less gathered onto one rank against more exchanges and launches)
         dd = {"fp64": decomposed_solve(args, b, rho, p_fp64, t_fp64, cyc_fp64, "fp64"),
-              "mixed": decomposed_solve(args, b, rho, p_mixed, t_mixed, cyc_mixed, "mixed")}
+              "mixed": decomposed_solve(args, b, rho, p_mixed, t_mixed, cyc_mixed, "mixed"),
+              "mixed_switch_level_1": decomposed_solve(args, b, rho, p_mixed, t_mixed, cyc_mixed, "mixed",
+                                                       max_decomposed=1)}
     s.solve(b, p)  # restore the headline solution
 
     # with the CSF term the gradient pass also reads the CSF faces and the face coefficients

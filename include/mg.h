@@ -363,13 +363,15 @@ int mg_fp64_fma_rate(void *stream, double *sink, int blocks, int iters, double *
  * gather), a whole-grid handle runs the rest of the V-cycle, and each slab's prolongation
  * reads its coarse planes and their neighbours from there.  The norm and the mean of p are
  * sums of per-slab partial sums.  One V-cycle gives bitwise the whole-grid FP64 V-cycle.
- * The mixed-precision solve (precision MG_MIXED) is decomposed at its finest level only
- * (switch_level 1): FP32 slabs of the colour-split layout with a ghost plane per colour below
- * and above, an exchange of the colour just updated after every half sweep and after the
- * prolongation, the restriction written into the whole-grid handle's FP32 level, the rest of
- * each inner V-cycle on that handle, and the FP64 outer loop (residual, norms, update) slab by
- * slab with p's ghost planes exchanged before each residual; every cell sees the whole-grid
- * mixed solve's arithmetic, the outer loop's FP32-accumulated sums differing in grouping only.
+ * The mixed-precision solve (precision MG_MIXED) cuts its levels the same way, down to the
+ * deepest switch level its kernels allow (every cut level's nx a multiple of 16, the last cut
+ * level's slabs a multiple of 4 planes): FP32 slabs of the colour-split layout with a ghost plane
+ * per colour below and above, an exchange of the colour just updated after every half sweep and
+ * after the prolongation, the last cut level's restriction written into the whole-grid handle's
+ * FP32 level, the rest of each inner V-cycle on that handle, and the FP64 outer loop (residual,
+ * norms, update) slab by slab with p's ghost planes exchanged before each residual; every cell
+ * sees the whole-grid mixed solve's arithmetic, the outer loop's FP32-accumulated sums
+ * differing in grouping only.
  * Arrays passed in and out are whole-grid device arrays (cell layout above). */
 #define MG_DD_MAX_RANKS 64
 typedef struct mg_dd mg_dd;
@@ -389,7 +391,7 @@ int mg_dd_make_plan(int nx, int ny, int nz, int coarsest, int ranks, int max_dec
 /* Create a decomposed solver.  opts: method MG_METHOD_VCYCLE, warm_start 0, and either
  * precision MG_FP64 with inner_cycles 1, or precision MG_MIXED (inner_cycles as for mg_create)
  * with pre >= 1, post >= 1, trilinear prolongation, nx a multiple of 16 and nz a multiple of
- * 4 * ranks (max_decomposed is then 1); other fields as for mg_create.  MG_ERR_ARG otherwise.
+ * 4 * ranks; other fields as for mg_create.  MG_ERR_ARG otherwise.
  * Allocates every slab's buffers and the whole-grid handle of the switch level on the current
  * device. */
 int mg_dd_create(const mg_opts *opts, int ranks, int max_decomposed, void *stream, mg_dd **out);

@@ -1037,17 +1037,25 @@ Lay make_lay(Dims d) {
     return L;
 }
 
-// a slab (L.zlo / L.zhi): s-form only, split layout with hx % 4 == 0 (the decomposed mixed cycle)
-void launch_half32_slab(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
-                        bool from_zero) {
+// a slab (L.zlo / L.zhi): split layout with hx % 4 == 0 (the decomposed mixed cycle); s-form
+// (the finest level) or face form (the face arrays with their ghost plane above)
+template <bool SFORM>
+void half32_slab(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
+                 bool from_zero) {
     if (half_z_ok(L)) {
-        if (from_zero) run_half_z<true, true, 0, true>(s, L, h2, cf, b, x, col, Upd{});
-        else run_half_z<true, false, 0, true>(s, L, h2, cf, b, x, col, Upd{});
+        if (from_zero) run_half_z<SFORM, true, 0, true>(s, L, h2, cf, b, x, col, Upd{});
+        else run_half_z<SFORM, false, 0, true>(s, L, h2, cf, b, x, col, Upd{});
         return;
     }
     const i64 work = (i64)L.ny * L.nz * (L.hx / 4);
-    if (from_zero) k_half_vec<true, true, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
-    else k_half_vec<true, false, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
+    if (from_zero) k_half_vec<SFORM, true, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
+    else k_half_vec<SFORM, false, 0, true><<<blocks_for(work), kThreads, 0, s>>>(L, h2, cf, b, x, col, Upd{});
+}
+
+void launch_half32_slab(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const float *b, float *x, int col,
+                        bool from_zero) {
+    if (cf.s) half32_slab<true>(s, L, h2, cf, b, x, col, from_zero);
+    else half32_slab<false>(s, L, h2, cf, b, x, col, from_zero);
 }
 
 void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
@@ -1130,7 +1138,8 @@ void launch_resid_restrict32(cudaStream_t s, Lay L, Lay Lc, double ih2, const fl
     if (red_only && L.split && L.hx % 4 == 0) {
         const i64 work = (i64)Lc.ny * Lc.nz * (L.hx / 4);
         const unsigned nb = (unsigned)((work + kRrThreads - 1) / kRrThreads);
-        if (L.zlo || L.zhi) k_rr_red_vec<true, true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        if ((L.zlo || L.zhi) && sinv) k_rr_red_vec<true, true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
+        else if (L.zlo || L.zhi) k_rr_red_vec<false, true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         else if (sinv) k_rr_red_vec<true><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         else k_rr_red_vec<false><<<nb, kRrThreads, 0, s>>>(L, Lc, (float)ih2, cf, b, x, bc);
         return;

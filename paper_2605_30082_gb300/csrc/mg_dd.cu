@@ -18,14 +18,15 @@
 // so one V-cycle gives bitwise the same result for any number of slabs.  The exchange is a
 // device-to-device copy here; between GPUs it would be one send/receive per neighbour.
 //
-// The mixed-precision solve (precision MG_MIXED) decomposes the finest level only: FP32 slabs
-// in the colour-split layout with a ghost plane below and above in each colour half (mg::Lay
-// zlo / zhi), the finest level's FP32 kernels in their ghost variants, an exchange of the
-// colour just updated after every half sweep and after the prolongation, the red residuals'
-// restriction written straight into the whole-grid handle's FP32 level (the gather), the rest
-// of the inner V-cycle on that handle, and the FP64 outer loop slab by slab (the fused residual
-// kernel over each slab with its p ghost planes exchanged first; the norms and sums of p added
-// over the slabs).
+// The mixed-precision solve (precision MG_MIXED) cuts the same levels, as deep as its kernels
+// allow: FP32 slabs in the colour-split layout with a ghost plane below and above in each colour
+// half (mg::Lay zlo / zhi), s = 1/rho on the finest level and the low faces below it, the FP32
+// kernels in their ghost variants, an exchange of the colour just updated after every half
+// sweep and after the prolongation, the last cut level's red residuals restricted straight into
+// the whole-grid handle's FP32 level (the gather), the rest of the inner V-cycle on that handle,
+// and the FP64 outer loop slab by slab (the fused residual kernel over each slab with its p
+// ghost planes exchanged first; the norms and sums of p added over the slabs).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -49,10 +50,11 @@ struct Slab {
     double *fx, *fy; // low faces of the own planes
     double *fze;     // low z faces of the own planes and of the ghost above: planes + 1 planes
     double *invd, *dg;
-    // mixed precision, finest level: FP32 arrays in the slab layout `lay` (each colour half
-    // with a ghost plane below and above; the pointers at the red half's first own plane)
+    // mixed precision: FP32 arrays in the slab layout `lay` (each colour half with a ghost plane
+    // below and above; the pointers at the red half's first own plane): x, b, and s = 1/rho on
+    // the finest level or the low faces below it (fz with the face to the ghost plane above)
     mg::Lay lay;
-    float *x32, *b32, *s32;
+    float *x32, *b32, *s32, *fx32, *fy32, *fz32;
 };
 
 // The mixed solve's FP32 s = 1/rho of one slab: the whole grid's s (natural FP64) over the
@@ -68,6 +70,20 @@ __global__ void k_pack_slab_s32(mg::Lay L, int z0, int nz_total, const double *_
         if (zg < 0 || zg >= nz_total) continue;  // beyond a wall: never read
         const double v = s_whole[((mg::i64)zg * L.ny + y) * L.nx + x];
         s32[((x + y + z) & 1) * L.half + ((mg::i64)z * L.ny + y) * L.hx + (x >> 1)] = mg::d2f_rn(v);
+    }
+}
+
+// The FP32 low faces of one slab of a cut level below the finest: the slab's FP64 faces (own
+// planes; for fz also the face to the ghost plane above, `planes` = nz + 1) into its colour-split
+// layout, rounded to nearest as the whole-grid pack rounds them
+__global__ void k_pack_slab_faces(mg::Lay L, int planes, const double *__restrict__ f, float *f32) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.nx) return;
+    const int rows = L.ny * planes;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % L.ny, z = row / L.ny;
+        f32[((x + y + z) & 1) * L.half + ((mg::i64)z * L.ny + y) * L.hx + (x >> 1)] =
+            mg::d2f_rn(f[((mg::i64)z * L.ny + y) * L.nx + x]);
     }
 }
 
@@ -290,21 +306,33 @@ int vcycle(mg_dd *dd, int l, bool x_zero) {
 
 // ---- the mixed-precision cycle: FP32 slabs of the finest level ------------------------------
 
-// the whole-grid handle's FP32 level 0 seen from slab S: its arrays from the slab's first coarse
-// plane (even, so colours agree), its neighbours' planes beside it (zlo / zhi of the slab)
-mg::Lay coarse_view(const mg_dd *dd, const Slab &S, mg::i64 *off) {
+// The coarse level of cut level l for slab r, as its restriction and prolongation see it: the
+// next cut level's slab, or, below the last cut level, a view of the whole-grid handle's FP32
+// level 0 from the slab's first coarse plane (even, so colours agree) with its neighbours' planes
+// beside it (the gather and the scatter back)
+struct Coarse {
+    mg::Lay lay;
+    float *b, *x;
+};
+Coarse coarse_of(const mg_dd *dd, int l, int r) {
+    const Slab &S = dd->lv[l][r];
+    if (l + 1 < dd->ndec) {
+        const Slab &C = dd->lv[l + 1][r];
+        return {C.lay, C.b32, C.x32};
+    }
     mg::Lay v = dd->clay;
     v.nz = S.d.nz / 2;
     v.n = (mg::i64)v.nx * v.ny * v.nz;
     v.zlo = S.d.zlo;
     v.zhi = S.d.zhi;
-    *off = (mg::i64)(S.z0 / 2) * v.ny * v.hx;
-    return v;
+    const mg::i64 off = (mg::i64)(S.z0 / 2) * v.ny * v.hx;
+    return {v, dd->cb32 + off, dd->cx32 + off};
 }
 
-// colour c's first and last own planes of every slab's FP32 x into its neighbours' ghost planes
-int exchange32(mg_dd *dd, int c) {
-    std::vector<Slab> &R = dd->lv[0];
+// colour c's first and last own planes of every slab's FP32 x on cut level l into its
+// neighbours' ghost planes
+int exchange32(mg_dd *dd, int l, int c) {
+    std::vector<Slab> &R = dd->lv[l];
     const size_t plane = (size_t)R[0].lay.ny * R[0].lay.hx;
     return per_rank(dd, [&](int r, cudaStream_t st) -> int {
         float *col = R[r].x32 + (size_t)c * R[r].lay.half;
@@ -320,52 +348,58 @@ int exchange32(mg_dd *dd, int c) {
     });
 }
 
-// a half sweep of colour c on every slab, then the exchange of that colour
-int half_mixed(mg_dd *dd, int c, bool from_zero) {
-    std::vector<Slab> &R = dd->lv[0];
-    const double h2 = dd->o.h * dd->o.h;
+// h^2 of cut level l (the spacing doubles per level: an exact power-of-two scaling)
+double h2_of(const mg_dd *dd, int l) { return dd->o.h * dd->o.h * (double)(1ll << (2 * l)); }
+
+// a half sweep of colour c on every slab of cut level l, then the exchange of that colour
+int half_mixed(mg_dd *dd, int l, int c, bool from_zero) {
+    std::vector<Slab> &R = dd->lv[l];
+    const double h2 = h2_of(dd, l);
     const int rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
-        mg::launch_half32(st, R[r].lay, h2, R[r].s32, nullptr, nullptr, nullptr, R[r].b32, R[r].x32, c, from_zero);
+        mg::launch_half32(st, R[r].lay, h2, R[r].s32, R[r].fx32, R[r].fy32, R[r].fz32, R[r].b32, R[r].x32, c, from_zero);
         return MG_OK;
     });
-    return rc ? rc : exchange32(dd, c);
+    return rc ? rc : exchange32(dd, l, c);
 }
 
-// One FP32 V-cycle of the finest level, in the order of the whole-grid cycle: from x32 = 0
-// (from_zero) or from the slabs' x32; with alpha_shift, the last red half sweep adds
-// alpha x - shift to the slabs' FP64 p instead of storing x32.
-int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift, bool recording = false) {
-    std::vector<Slab> &R = dd->lv[0];
-    const double h2 = dd->o.h * dd->o.h;
+// One FP32 V-cycle from cut level l down, in the order of the whole-grid cycle: from x32 = 0
+// (from_zero) or from the slabs' x32; with alpha_shift (finest level), the last red half sweep
+// adds alpha x - shift to the slabs' FP64 p instead of storing x32.  `recording`: under a stream
+// capture (the whole-grid handle then records its levels launch by launch).
+int vcycle_mixed(mg_dd *dd, int l, bool from_zero, const double *alpha_shift, bool recording = false) {
+    std::vector<Slab> &R = dd->lv[l];
+    const double h2 = h2_of(dd, l);
     int rc;
     for (int sw = 0; sw < dd->o.pre; ++sw) {
-        if ((rc = half_mixed(dd, 0, from_zero && sw == 0))) return rc;
-        if ((rc = half_mixed(dd, 1, false))) return rc;
+        if ((rc = half_mixed(dd, l, 0, from_zero && sw == 0))) return rc;
+        if ((rc = half_mixed(dd, l, 1, false))) return rc;
     }
     // the red residuals (every black one is zero after the black sweep), restricted into the
-    // whole grid's coarse right-hand side (the gather)
+    // coarse right-hand side
     rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
-        mg::i64 off;
-        const mg::Lay cv = coarse_view(dd, R[r], &off);
-        mg::launch_resid_restrict32(st, R[r].lay, cv, 1.0 / h2, R[r].s32, nullptr, nullptr, nullptr, R[r].b32, R[r].x32,
-                                    dd->cb32 + off, true);
+        const Coarse co = coarse_of(dd, l, r);
+        mg::launch_resid_restrict32(st, R[r].lay, co.lay, 1.0 / h2, R[r].s32, R[r].fx32, R[r].fy32, R[r].fz32, R[r].b32,
+                                    R[r].x32, co.b, true);
         return MG_OK;
     });
     if (rc) return rc;
-    mg::handle_vcycle32(dd->ch, 0, recording);  // the switch level down, on the caller's stream
-    // the prolongation back: the red cells of each slab from the coarse planes beside it
+    if (l + 1 < dd->ndec) {
+        if ((rc = vcycle_mixed(dd, l + 1, true, nullptr, recording))) return rc;
+    } else {
+        mg::handle_vcycle32(dd->ch, 0, recording);  // the switch level down, on the caller's stream
+    }
+    // the prolongation back: the red cells of each slab from its coarse planes and those beside
     rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
-        mg::i64 off;
-        const mg::Lay cv = coarse_view(dd, R[r], &off);
-        mg::launch_prolong32(st, R[r].lay, cv, dd->cx32 + off, R[r].x32, MG_PROLONG_TRILINEAR, 0);
+        const Coarse co = coarse_of(dd, l, r);
+        mg::launch_prolong32(st, R[r].lay, co.lay, co.x, R[r].x32, MG_PROLONG_TRILINEAR, 0);
         return MG_OK;
     });
     if (rc) return rc;
-    if ((rc = exchange32(dd, 0))) return rc;
+    if ((rc = exchange32(dd, l, 0))) return rc;
     for (int sw = 0; sw < dd->o.post; ++sw) {
-        if ((rc = half_mixed(dd, 1, false))) return rc;
+        if ((rc = half_mixed(dd, l, 1, false))) return rc;
         if (sw + 1 < dd->o.post || !alpha_shift) {
-            if ((rc = half_mixed(dd, 0, false))) return rc;
+            if ((rc = half_mixed(dd, l, 0, false))) return rc;
             continue;
         }
         rc = per_rank(dd, [&](int r, cudaStream_t st) -> int {
@@ -378,8 +412,6 @@ int vcycle_mixed(mg_dd *dd, bool from_zero, const double *alpha_shift, bool reco
     return MG_OK;
 }
 
-// Record one V-cycle of level 0 (x_zero false) on a private stream, the whole-grid handle's
-// launches included; nothing runs.  Where recording is refused the cycles launch call by call.
 // Record f() (one cycle) on a private stream, the whole-grid handle's launches included;
 // nothing runs.  Returns the instantiated graph, or null where recording is refused (the
 // cycles then launch call by call); *launches = the kernels it holds.
@@ -430,7 +462,7 @@ void build_cycle_graph(mg_dd *dd) {
         return;
     }
     for (int k = 0; k < 2; ++k)
-        dd->mix_exec[k] = record_cycle(dd, [&] { return vcycle_mixed(dd, k == 0, nullptr, true); }, &dd->mix_launches[k]);
+        dd->mix_exec[k] = record_cycle(dd, [&] { return vcycle_mixed(dd, 0, k == 0, nullptr, true); }, &dd->mix_launches[k]);
 }
 
 // one V-cycle of level 0 from the slabs' x: the recorded graph, or call by call
@@ -563,12 +595,12 @@ int solve_mixed(mg_dd *dd, const double *b, double *p, mg_stats *st) {
             if (dd->mix_exec[g]) {
                 DD_CUDA(dd, cudaGraphLaunch(dd->mix_exec[g], s));
                 mg::count_launch((int)dd->mix_launches[g]);
-            } else if ((rc = vcycle_mixed(dd, k == 0, nullptr))) {
+            } else if ((rc = vcycle_mixed(dd, 0, k == 0, nullptr))) {
                 return rc;
             }
         }
         const double as[2] = {1.0 / scale, mu};
-        if ((rc = vcycle_mixed(dd, inner == 1, as))) return rc;
+        if ((rc = vcycle_mixed(dd, 0, inner == 1, as))) return rc;
         scale = 1.0 / rn;
         if ((rc = exchange(dd, 0))) return rc;  // p's ghost planes
         for (int r = 0; r < dd->P; ++r) {
@@ -681,9 +713,26 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
     dd->o = *o;
     dd->mixed = mixed;
     dd->s = static_cast<cudaStream_t>(stream);
-    if (mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, mixed ? 1 : max_decomposed, &dd->plan) != MG_OK) {
+    if (mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, max_decomposed, &dd->plan) != MG_OK) {
         delete dd;
         return MG_ERR_ARG;
+    }
+    if (mixed) {
+        // the mixed cycle's cut levels prolong with the red trilinear kernel (coarse rows of a
+        // multiple of 8 cells, so nx_l a multiple of 16) and the last one restricts into a view
+        // of the whole coarse level starting at an even plane (slabs of 4k planes)
+        const mg_dd_plan &pl = dd->plan;
+        int sw = pl.switch_level;
+        auto fits = [&](int k) {
+            for (int l = 0; l < k; ++l)
+                if (pl.nx[l] % 16 != 0) return false;
+            return pl.planes[k - 1] % 4 == 0;
+        };
+        while (sw > 0 && !fits(sw)) --sw;
+        if (sw == 0 || mg_dd_make_plan(o->nx, o->ny, o->nz, o->coarsest, ranks, sw, &dd->plan) != MG_OK) {
+            delete dd;
+            return MG_ERR_ARG;
+        }
     }
     dd->P = ranks;
     dd->ndec = dd->plan.switch_level;
@@ -718,14 +767,20 @@ int mg_dd_create(const mg_opts *o, int ranks, int max_decomposed, void *stream, 
                 S.lay.zhi = S.d.zhi;
                 const size_t plane = (size_t)S.lay.ny * S.lay.hx;
                 S.lay.half = (mg::i64)((S.d.nz + 2) * plane);
-                float *f[3];
-                for (float *&q : f) {
-                    q = static_cast<float *>(dd_alloc(dd, 4 * 2 * (size_t)S.lay.half));
+                auto F = [&]() {
+                    float *q = static_cast<float *>(dd_alloc(dd, 4 * 2 * (size_t)S.lay.half));
                     if (!q) ok = false;
+                    return q ? q + plane : nullptr;
+                };
+                S.x32 = F();
+                S.b32 = F();
+                if (l == 0) {
+                    S.s32 = F();
+                } else {
+                    S.fx32 = F();
+                    S.fy32 = F();
+                    S.fz32 = F();
                 }
-                S.x32 = f[0] ? f[0] + plane : nullptr;
-                S.b32 = f[1] ? f[1] + plane : nullptr;
-                S.s32 = f[2] ? f[2] + plane : nullptr;
             }
         }
     }
@@ -882,6 +937,13 @@ int mg_dd_set_density(mg_dd *dd, const double *rho) {
         for (int r = 0; r < dd->P; ++r) {
             Slab &S = dd->lv[l][r];
             mg::launch_invdiag(s, S.d, S.fx, S.fy, S.fze, S.invd, S.dg);
+            if (dd->mixed && l > 0) {  // the FP32 faces of a cut level below the finest
+                const dim3 grd((unsigned)((S.lay.nx + 127) / 128), (unsigned)std::min(S.lay.ny * (S.lay.nz + 1), 65535));
+                mg::count_launch(3);
+                k_pack_slab_faces<<<grd, 128, 0, s>>>(S.lay, S.lay.nz, S.fx, S.fx32);
+                k_pack_slab_faces<<<grd, 128, 0, s>>>(S.lay, S.lay.nz, S.fy, S.fy32);
+                k_pack_slab_faces<<<grd, 128, 0, s>>>(S.lay, S.lay.nz + 1, S.fze, S.fz32);
+            }
             mg::Dims cd = mg::make_dims(S.d.nx / 2, S.d.ny / 2, S.d.nz / 2);
             if (l + 1 < dd->ndec) {
                 Slab &C = dd->lv[l + 1][r];

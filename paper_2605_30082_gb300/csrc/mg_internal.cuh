@@ -216,10 +216,11 @@ void launch_pinv_finish(cudaStream_t s, int nc, double *M, const double *scal);
 // ---- FP32 colour-split level kernels (kernels_split.cu) ----
 // half sweep of colour col in place; sinv = 1/rho per cell (beta = (s_L + s_R)/2) when
 // non-null, else the low-face arrays; from_zero: the other colour is taken as zero.
-// On a slab (L.zlo / L.zhi; see Lay) the V-cycle kernels of the finest level take its ghost
-// planes as z neighbours: s-form, split layout with hx % 4 == 0, restriction of red residuals
-// only, trilinear prolongation of the red cells from a coarse view (Lc.zlo / Lc.zhi) whose
-// nx is a multiple of 8; other cases are not supported on slabs
+// On a slab (L.zlo / L.zhi; see Lay) the V-cycle kernels take its ghost planes as z
+// neighbours: split layout with hx % 4 == 0, s-form or face form (fz with its ghost plane
+// above: the face to the neighbour above), restriction of red residuals only, trilinear
+// prolongation of the red cells from a coarse slab or view (Lc.zlo / Lc.zhi) whose nx is a
+// multiple of 8; other cases are not supported on slabs
 void launch_half32(cudaStream_t s, Lay L, double h2, const float *sinv, const float *fx, const float *fy,
                    const float *fz, const float *b, float *x, int col, bool from_zero);
 // the last red half sweep of the finest level with the outer update fused in: the new red

@@ -191,8 +191,8 @@ def _same_as_whole_grid(sd, sw, pd, pw):
 
 @pytest.mark.parametrize("ranks,inner", [(2, 1), (4, 1), (2, 3), (4, 0)])
 def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
-    """The mixed solve with its finest level cut into slabs (FP32 slab kernels with ghost planes,
-    the coarse levels on one whole-grid handle, the FP64 outer loop slab by slab) follows the
+    """The mixed solve with its levels down to 16^3 cut into slabs (FP32 slab kernels with ghost
+    planes, the coarser levels on one whole-grid handle, the FP64 outer loop slab by slab) follows the
     whole-grid mixed solve (the same V-cycles and outer iterations; residual histories and p
     as close as the outer loop's sums allow), and it reaches the oracle's exact discrete
     solution."""
@@ -207,7 +207,8 @@ def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
     st, h = L.mg_dd_create(_mixed_opts(dims, c["h"], inner), ranks, 0)
     assert st == L.MG_OK, st
     st, plan = L.mg_dd_get_plan(h)
-    assert plan.switch_level == 1  # the mixed cycle cuts the finest level only
+    # cut down to 16^3: the prolongation into a cut level needs coarse rows of a multiple of 8 cells
+    assert plan.switch_level == 3, plan.switch_level
     assert L.mg_dd_set_density(h, rho, dims) == L.MG_OK
     pd = torch.zeros_like(b)
     sts = L.mg_stats()
@@ -220,7 +221,8 @@ def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
     assert rel(host(pd), p_ex) <= 1e-9
     _, ex, by = L.mg_dd_traffic(h)
     k = 2 * 2 + 2 * 2 + 1
-    assert ex == k and by == k * 2 * (ranks - 1) * 4 * (n // 2) * n
+    assert ex == k * plan.switch_level
+    assert by == sum(k * 2 * (ranks - 1) * 4 * (plan.nx[l] // 2) * plan.ny[l] for l in range(plan.switch_level))
     L.mg_dd_destroy(h)
     s.close()
 
