@@ -189,8 +189,8 @@ def _same_as_whole_grid(sd, sw, pd, pw):
     assert rel(host(pd), host(pw)) <= 1e-13
 
 
-@pytest.mark.parametrize("ranks,inner", [(2, 1), (4, 1), (2, 3), (4, 0)])
-def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
+@pytest.mark.parametrize("ranks,inner,max_dec", [(2, 1, 0), (4, 1, 0), (2, 3, 0), (4, 0, 0), (2, 0, 1), (4, 3, 1)])
+def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner, max_dec):
     """The mixed solve with its levels down to 16^3 cut into slabs (FP32 slab kernels with ghost
     planes, the coarser levels on one whole-grid handle, the FP64 outer loop slab by slab) follows the
     whole-grid mixed solve (the same V-cycles and outer iterations; residual histories and p
@@ -204,11 +204,12 @@ def test_dd_mixed_solve_matches_whole_grid_and_oracle(ranks, inner):
     s = Solver(dims, h=c["h"], precision="mixed", coarsest=4, rtol=1e-11, inner_cycles=inner)
     s.set_density(rho)
     pw = s.solve(b)
-    st, h = L.mg_dd_create(_mixed_opts(dims, c["h"], inner), ranks, 0)
+    st, h = L.mg_dd_create(_mixed_opts(dims, c["h"], inner), ranks, max_dec)
     assert st == L.MG_OK, st
     st, plan = L.mg_dd_get_plan(h)
-    # cut down to 16^3: the prolongation into a cut level needs coarse rows of a multiple of 8 cells
-    assert plan.switch_level == 3, plan.switch_level
+    # as deep as allowed, down to 16^3 (the prolongation into a cut level needs coarse rows of a
+    # multiple of 8 cells), or the finest level only
+    assert plan.switch_level == (max_dec or 3), plan.switch_level
     assert L.mg_dd_set_density(h, rho, dims) == L.MG_OK
     pd = torch.zeros_like(b)
     sts = L.mg_stats()
