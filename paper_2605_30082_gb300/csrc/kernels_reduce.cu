@@ -560,11 +560,18 @@ __global__ void __launch_bounds__(32 * kGradRows) k_adjoint_grad_split(
 }
 
 // The same for even nx, two cells per thread: 16-byte loads of lam and p (both 16-byte
-// aligned, as the ABI requires), the next plane's loads issued before the current plane is
-// computed, and the y-1 row's pairs taken from shared memory, where the warp of that row put
-// them (one barrier per plane, double-buffered by plane parity); only each block's first row
-// loads and splits its y-1 row itself.  Block (32, kGrad2Rows): a warp covers 64 cells of a row.
+// aligned, as the ABI requires), each plane's loads issued one plane ahead, and every value
+// split once.  Block (32, kGrad2Rows): a warp covers 64 cells of a row, the block a tile of
+// 64 cells x kGrad2Rows rows, marching kGrad2Planes planes in z.  Per plane each thread writes
+// its pairs into a shared-memory tile (double-buffered by plane parity, one barrier per plane);
+// the y-1 row of a warp is the tile row above it, the x-1 cell of a lane the neighbouring
+// lane's second cell (shuffle).  The tile's halo -- row y0 - 1 and the cells x0 - 1 of its
+// rows, 160 values -- is loaded and split by five warps, one value per lane: warps 0 and 1 lam
+// of the halo row, warps 2 and 3 p, warp 4 the halo column (lanes 0-15 lam, 16-31 p).  So no
+// lane splits a neighbour's value again, no warp waits on a halo load that was not
+// prefetched, and no warp splits more than one value beyond its own cells before the barrier.
 constexpr int kGrad2Rows = 16, kGrad2Planes = 32;
+static_assert(kGrad2Rows >= 5, "five warps of the block load the halo");
 
 __device__ __forceinline__ float4 split2(double2 v) {
     float4 r;
@@ -578,18 +585,31 @@ __device__ __forceinline__ float grad_face(float lah, float lal, float lbh, floa
     return -((lah - lbh) + (lal - lbl)) * (((pah - pbh) + (pal - pbl)) * ih2);
 }
 
+struct GradTile {
+    float4 l[2][kGrad2Rows][32], p[2][kGrad2Rows][32];  // pairs of the tile's cells
+    float4 yl[2][32], yp[2][32];                          // pairs of the halo row y0 - 1, as the tile
+    float2 xl[2][kGrad2Rows], xp[2][kGrad2Rows];          // pair of cell x0 - 1 of each row
+};
+
 __global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
     int nx, int ny, int nz, float ih2, const double *__restrict__ lam, const double *__restrict__ p,
     float *__restrict__ gx, float *__restrict__ gy, float *__restrict__ gz) {
-    __shared__ float4 sl[2][kGrad2Rows][32], sp[2][kGrad2Rows][32];
+    __shared__ GradTile T;
     const int lane = threadIdx.x, ty = threadIdx.y;
-    const int x = 2 * (blockIdx.x * 32 + lane);
-    const int y = blockIdx.y * kGrad2Rows + ty;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * kGrad2Rows;
+    const int x = x0 + 2 * lane;
+    const int y = y0 + ty;
     const int z0 = blockIdx.z * kGrad2Planes;
     const int z1 = min(z0 + kGrad2Planes, nz);
     const bool act = x < nx && y < ny;  // nx even: x + 1 < nx too
-    const bool ownrow = act && y > 0 && ty == 0;  // loads its y-1 row from global memory
     const int nxy = nx * ny;
+    // the halo value this thread loads per plane (warps 0-4), as an offset from the plane start
+    const int hx = x0 + (ty & 1) * 32 + lane, hy = y0 + (lane & 15);
+    const bool hrow = ty < 4 && y0 > 0 && hx < nx;
+    const bool hcol = ty == 4 && x0 > 0 && hy < ny;
+    const bool hld = hrow || hcol;
+    const double *hsrc = (ty == 2 || ty == 3 || (ty == 4 && lane >= 16)) ? p : lam;
+    const int hoff = hrow ? (y0 - 1) * nx + hx : (hcol ? hy * nx + x0 - 1 : 0);
     const double2 zero2 = make_double2(0.0, 0.0);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 lz = zero4, pz = zero4;  // plane z - 1
@@ -598,53 +618,57 @@ __global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
         lz = split2(*reinterpret_cast<const double2 *>(lam + c));
         pz = split2(*reinterpret_cast<const double2 *>(p + c));
     }
-    double2 Lc = zero2, Pc = zero2, Ly = zero2, Py = zero2;
+    // running offsets of this thread's cells, x faces, y faces and halo value in plane z
+    int c = z0 * nxy + y * nx + x;
+    int ax = (z0 * ny + y) * (nx + 1) + x;  // x faces: (nz, ny, nx + 1), not 8-byte aligned
+    int ay = (z0 * (ny + 1) + y) * nx + x;  // y faces: (nz, ny + 1, nx), even
+    int hc = z0 * nxy + hoff;
+    const int sx = ny * (nx + 1), sy = (ny + 1) * nx;
+    double2 Lc = zero2, Pc = zero2;
+    double Hc = 0.0;
     if (z0 < z1) {
-        const int c = z0 * nxy + y * nx + x;
         if (act) {
             Lc = *reinterpret_cast<const double2 *>(lam + c);
             Pc = *reinterpret_cast<const double2 *>(p + c);
         }
-        if (ownrow) {
-            Ly = *reinterpret_cast<const double2 *>(lam + c - nx);
-            Py = *reinterpret_cast<const double2 *>(p + c - nx);
-        }
+        if (hld) Hc = hsrc[hc];
     }
-    for (int z = z0; z < z1; ++z) {
-        const int c = z * nxy + y * nx + x;
+    for (int z = z0; z < z1; ++z, c += nxy, ax += sx, ay += sy, hc += nxy) {
         const int buf = z & 1;
-        double2 Ln = zero2, Pn = zero2, Lyn = zero2, Pyn = zero2;
+        double2 Ln = zero2, Pn = zero2;
+        double Hn = 0.0;
         if (z + 1 < z1) {
             if (act) {
                 Ln = *reinterpret_cast<const double2 *>(lam + c + nxy);
                 Pn = *reinterpret_cast<const double2 *>(p + c + nxy);
             }
-            if (ownrow) {
-                Lyn = *reinterpret_cast<const double2 *>(lam + c + nxy - nx);
-                Pyn = *reinterpret_cast<const double2 *>(p + c + nxy - nx);
-            }
+            if (hld) Hn = hsrc[hc + nxy];
         }
         const float4 l = split2(Lc), q = split2(Pc);
-        sl[buf][ty][lane] = l;
-        sp[buf][ty][lane] = q;
-        float4 ly = zero4, py = zero4;
-        if (ownrow) {
-            ly = split2(Ly);
-            py = split2(Py);
+        T.l[buf][ty][lane] = l;
+        T.p[buf][ty][lane] = q;
+        if (ty < 5) {  // warp-uniform: the halo (zeros where it is not loaded)
+            float hh, hl;
+            split_f64(Hc, hh, hl);
+            const float2 hv = make_float2(hh, hl);
+            if (ty < 4) reinterpret_cast<float2 *>(ty < 2 ? T.yl[buf] : T.yp[buf])[(ty & 1) * 32 + lane] = hv;
+            else if (lane < 16) T.xl[buf][lane] = hv;
+            else T.xp[buf][lane - 16] = hv;
         }
         __syncthreads();  // buffer `buf` was last read two planes ago, before the previous barrier
-        if (ty > 0) {
-            ly = sl[buf][ty - 1][lane];
-            py = sp[buf][ty - 1][lane];
-        }
-        // cell x - 1 is the second cell of the lane to the left (lane 0 loads it)
+        const float4 ly = ty > 0 ? T.l[buf][ty - 1][lane] : T.yl[buf][lane];
+        const float4 py = ty > 0 ? T.p[buf][ty - 1][lane] : T.yp[buf][lane];
+        // cell x - 1: the second cell of the lane to the left; lane 0 takes the halo column
+        const float2 hxl = T.xl[buf][ty], hxp = T.xp[buf][ty];
         float lxh = __shfl_up_sync(0xffffffffu, l.z, 1), lxl = __shfl_up_sync(0xffffffffu, l.w, 1);
         float pxh = __shfl_up_sync(0xffffffffu, q.z, 1), pxl = __shfl_up_sync(0xffffffffu, q.w, 1);
+        if (lane == 0) {
+            lxh = hxl.x;
+            lxl = hxl.y;
+            pxh = hxp.x;
+            pxl = hxp.y;
+        }
         if (act) {
-            if (lane == 0 && x > 0) {
-                split_f64(lam[c - 1], lxh, lxl);
-                split_f64(p[c - 1], pxh, pxl);
-            }
             float a0 = 0.f, b0 = 0.f, b1 = 0.f, e0 = 0.f, e1 = 0.f;
             if (x > 0) a0 = grad_face(lxh, lxl, l.x, l.y, pxh, pxl, q.x, q.y, ih2);
             const float a1 = grad_face(l.x, l.y, l.z, l.w, q.x, q.y, q.z, q.w, ih2);
@@ -656,9 +680,6 @@ __global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
                 e0 = grad_face(lz.x, lz.y, l.x, l.y, pz.x, pz.y, q.x, q.y, ih2);
                 e1 = grad_face(lz.z, lz.w, l.z, l.w, pz.z, pz.w, q.z, q.w, ih2);
             }
-            const int row = z * ny + y;
-            const int ax = row * (nx + 1) + x;          // x faces: (nz, ny, nx + 1), not 8-byte aligned
-            const int ay = (z * (ny + 1) + y) * nx + x;  // y faces: (nz, ny + 1, nx), even
             __stcs(gx + ax, a0);
             __stcs(gx + ax + 1, a1);
             __stcs(reinterpret_cast<float2 *>(gy + ay), make_float2(b0, b1));
@@ -671,8 +692,7 @@ __global__ void __launch_bounds__(32 * kGrad2Rows) k_adjoint_grad_split2(
         pz = q;
         Lc = Ln;
         Pc = Pn;
-        Ly = Lyn;
-        Py = Pyn;
+        Hc = Hn;
     }
 }
 
