@@ -598,6 +598,141 @@ __global__ void __launch_bounds__(64, MINB) k_half_zs(Lay L, float h2, const flo
     cp_async_wait<0>();  // only empty groups can remain; leave none behind
 }
 
+// Staged form of k_half_z for the face-form regular sweep (the levels below the finest, whose
+// coarsened faces are stored per face, and a finest level loaded from face coefficients).  A
+// thread's nine per-plane vectors -- the other colour's x in rows y -+ 1, the other colour's
+// low x faces (its cells' high x faces), its own low x, y and z faces, the other colour's low
+// y faces in row y + 1 and low z faces in plane z + 1 (its high y and z faces), its own b --
+// travel by cp.async into a ring of kZfStages planes in shared memory, one plane ahead of the
+// plane being computed, as in k_half_zs; the other colour's row y (planes z -+ 1) rolls
+// through registers, the window scalars of the warp's edge lanes are loaded one plane ahead.
+// Every thread reads back only its own copies after cp.async.wait_group (no barrier, no spin).
+// Arithmetic as k_half_z, in the same order: bitwise the same results.
+constexpr int kZfStages = 2;
+constexpr int kZfFields = 9;  // ym, yp, fo, own fx, fy, fz, fy at y + 1, fz at z + 1, own b
+constexpr size_t kZfSmem = (size_t)kZfStages * kZfFields * 64 * sizeof(float4);
+
+template <int ZC, int MINB>
+__global__ void __launch_bounds__(64, MINB) k_half_zf(Lay L, float h2, Coef32 cf, const float *__restrict__ b,
+                                                       float *xv, int col) {
+    extern __shared__ float4 stg[];  // [kZfStages][kZfFields][64 threads]
+    constexpr int D = kZfStages;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int hx = L.hx, kv = hx >> 2;
+    const int kvi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int yi = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = kvi < kv && yi < L.ny;
+    const int k0 = min(kvi, kv - 1) << 2;
+    const int y = min(yi, L.ny - 1);
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, L.nz);
+    const int lane = threadIdx.x & 31;
+    const i64 dy = hx, dz = (i64)L.ny * hx;
+    const bool hy0 = y > 0, hy1 = y < L.ny - 1;
+    const bool kl = k0 > 0, kr = k0 + 4 < hx;
+    const i64 row0 = ((i64)z0 * L.ny + y) * hx + k0;
+    const i64 opp0 = (i64)(1 - col) * L.half + row0;
+    const i64 own0 = (i64)col * L.half + row0;
+    const float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [](const float *A, i64 off) { return *reinterpret_cast<const float4 *>(A + off); };
+    auto slot = [&](int st, int f) { return stg + (st * kZfFields + f) * 64 + tid; };
+    // plane z0 + t into stage t % D (slots whose neighbour is outside the grid are not copied
+    // and never read)
+    auto issue = [&](int t) {
+        const i64 o = opp0 + (i64)t * dz, w = own0 + (i64)t * dz;
+        const int st = t % D;
+        if (hy0) cp_async16(slot(st, 0), xv + o - dy);
+        if (hy1) {
+            cp_async16(slot(st, 1), xv + o + dy);
+            cp_async16(slot(st, 6), cf.fy + o + dy);
+        }
+        cp_async16(slot(st, 2), cf.fx + o);
+        cp_async16(slot(st, 3), cf.fx + w);
+        cp_async16(slot(st, 4), cf.fy + w);
+        cp_async16(slot(st, 5), cf.fz + w);
+        if (z0 + t < L.nz - 1) cp_async16(slot(st, 7), cf.fz + o + dz);
+        cp_async16(slot(st, 8), b + w);
+    };
+    // the window scalars beyond the warp's edge lanes (lane 0: x at k0 - 1; lane 31: x and the
+    // low x face at k0 + 4)
+    auto scalars = [&](i64 o, float &xl, float &xr, float &fr) {
+        xl = xr = fr = 0.f;
+        if (lane == 0 && kl) xl = xv[o - 1];
+        if (lane == 31 && kr) {
+            xr = xv[o + 4];
+            fr = cf.fx[o + 4];
+        }
+    };
+    // other colour, row y: planes z-1, z, z+1 (rolling)
+    float4 xzm = z0 > 0 ? ld(xv, opp0 - dz) : f0, xzc = ld(xv, opp0);
+    float4 xzp = z0 + 1 < L.nz ? ld(xv, opp0 + dz) : f0;
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t) {
+        if (z0 + t < z1) issue(t);
+        cp_async_commit();  // one group per plane, empty past the chunk: the counting stays uniform
+    }
+    float cxl, cxr, cfr;
+    scalars(opp0, cxl, cxr, cfr);
+    for (int z = z0; z < z1; ++z) {
+        const int t = z - z0;
+        if (z + D - 1 < z1) issue(t + D - 1);
+        cp_async_commit();
+        const i64 opp = opp0 + (i64)t * dz, own = own0 + (i64)t * dz;
+        float nxl = 0.f, nxr = 0.f, nfr = 0.f;
+        float4 xzpp = f0;
+        if (z + 1 < z1) {
+            scalars(opp + dz, nxl, nxr, nfr);
+            if (z + 2 < L.nz) xzpp = ld(xv, opp + 2 * dz);
+        }
+        cp_async_wait<D - 1>();  // all but the D - 1 newest groups done: plane z has landed
+        const int st = t % D;
+        const bool hz1 = z < L.nz - 1;
+        const int p = (col + y + z) & 1;  // x = 2k + p
+        const bool xw1 = (p == 1 && !kr);
+        const float4 ym = hy0 ? *slot(st, 0) : f0, yp = hy1 ? *slot(st, 1) : f0;
+        const float4 fo = *slot(st, 2), a0 = *slot(st, 3), a2 = *slot(st, 4), a4 = *slot(st, 5);
+        const float4 a3 = hy1 ? *slot(st, 6) : f0, a5 = hz1 ? *slot(st, 7) : f0;
+        const float4 b4 = *slot(st, 8);
+        float fr = __shfl_down_sync(0xffffffffu, fo.x, 1);
+        if (lane == 31) fr = cfr;
+        float xl = __shfl_up_sync(0xffffffffu, xzc.w, 1), xr = __shfl_down_sync(0xffffffffu, xzc.x, 1);
+        if (lane == 0) xl = cxl;
+        if (lane == 31) xr = cxr;
+        const float fov[4] = {fo.x, fo.y, fo.z, fo.w};
+        const float a0v[4] = {a0.x, a0.y, a0.z, a0.w}, a2v[4] = {a2.x, a2.y, a2.z, a2.w};
+        const float a3v[4] = {a3.x, a3.y, a3.z, a3.w}, a4v[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float a5v[4] = {a5.x, a5.y, a5.z, a5.w};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float xo[4] = {xzc.x, xzc.y, xzc.z, xzc.w};
+        const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+        const float zmv[4] = {xzm.x, xzm.y, xzm.z, xzm.w}, zpv[4] = {xzp.x, xzp.y, xzp.z, xzp.w};
+        float out[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float w0 = a0v[v];
+            const float w1 = (v == 3 && xw1) ? 0.f : (p ? (v < 3 ? fov[v + 1] : fr) : fov[v]);
+            const float w2 = a2v[v], w3 = a3v[v], w4 = a4v[v], w5 = a5v[v];
+            const float xm = p ? xo[v] : (v ? xo[v - 1] : xl);
+            const float xp = (v == 3 && xw1) ? 0.f : (p ? (v < 3 ? xo[v + 1] : xr) : xo[v]);
+            float num = w0 * xm;
+            num += w1 * xp;
+            num += w2 * ymv[v];
+            num += w3 * ypv[v];
+            num += w4 * zmv[v];
+            num += w5 * zpv[v];
+            const float den = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
+            out[v] = __fdividef(h2 * bv[v] + num, den);
+        }
+        if (active) *reinterpret_cast<float4 *>(xv + own) = make_float4(out[0], out[1], out[2], out[3]);
+        xzm = xzc;
+        xzc = xzp;
+        xzp = xzpp;
+        cxl = nxl;
+        cxr = nxr;
+        cfr = nfr;
+    }
+    cp_async_wait<0>();  // only empty groups can remain; leave none behind
+}
+
 bool half_z_ok(const Lay &L) { return L.split && L.hx % 4 == 0 && L.hx / 4 >= 32; }
 
 // 16 planes per thread where that still gives about 4 waves of 64-thread blocks (12 resident
@@ -623,6 +758,20 @@ void run_half_z(cudaStream_t s, const Lay &L, float h2, const Coef32 &cf, const 
         }();
         (void)carveout;
         k_half_zs<16, 11, GHOST><<<dim3(gx, gy, (L.nz + 15) / 16), blk, kZsSmem, s>>>(L, h2, cf.s, b, x, col);
+        return;
+    }
+    // the face form's regular sweeps, staged, where the grid gives at least four waves of
+    // 4-plane blocks (11 blocks x 18 KB of staging per SM, as k_half_zs)
+    if (!SFORM && !FROM_ZERO && UPDATE == 0 && !GHOST && (i64)gx * gy * ((L.nz + 3) / 4) >= 4 * sms * 11) {
+        static const bool carveout = [] {
+            // a preference only: the launch is valid either way
+            if (cudaFuncSetAttribute(k_half_zf<4, 11>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                (void)cudaGetLastError();
+            return true;
+        }();
+        (void)carveout;
+        k_half_zf<4, 11><<<dim3(gx, gy, (L.nz + 3) / 4), blk, kZfSmem, s>>>(L, h2, cf, b, x, col);
         return;
     }
     if ((i64)gx * gy * ((L.nz + 15) / 16) >= 4 * sms * 12)

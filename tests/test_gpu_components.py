@@ -179,6 +179,25 @@ def test_staged_half_sweep_matches_oracle_ragged_rows():
         assert rel(host(xs), O.rbgs(faces, b, x, s.h, sweeps, order)) < TOL[torch.float32]
 
 
+def test_staged_face_form_half_sweep_matches_oracle_ragged_rows():
+    """Face-form regular half sweeps (the levels below the finest, and a finest level loaded
+    from face coefficients) are staged in shared memory where the grid gives at least
+    4 x 152 x 11 blocks of 4 planes.  320 cells per row give 40 four-cell vectors per colour:
+    two rows per 64-thread block and a second block with 8 of its 32 lanes active per row;
+    192 rows and 160 planes make 7680 blocks."""
+    dims = (320, 192, 160)
+    s, M = make(dims, "mixed", coeffs="faces")
+    nx, ny, nz = dims
+    faces = tuple(f.astype(np.float32).astype(np.float64) for f in M.level_faces(0))
+    x = rnd((nz, ny, nx), 33).astype(np.float32)
+    b = rnd((nz, ny, nx), 34).astype(np.float32)
+    xg, bg = dev(x, torch.float32), dev(b, torch.float32)
+    for sweeps, order in ((1, 0), (1, 1), (2, 0)):
+        xs = xg.clone()
+        assert L.mg_smooth(s._h, 0, xs, bg, sweeps, order) == 0
+        assert rel(host(xs), O.rbgs(faces, b, x, s.h, sweeps, order)) < TOL[torch.float32]
+
+
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("prolong", ["trilinear", "constant"])
